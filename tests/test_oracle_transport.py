@@ -1,0 +1,233 @@
+"""Pins of the oracle's spatial operators (Sec. 3.2): CWENO3, the kinetic
+transport L(f) and the Euler divergence Phi(U)."""
+
+import numpy as np
+import pytest
+from numpy.polynomial import Polynomial as Poly
+
+import oracle as O
+
+
+def test_cweno_linear_and_constant_data_exact():
+    """Every sub-polynomial reproduces a line, so any weights give the exact
+    face values of linear data; constants are kept."""
+    rng = np.random.default_rng(0)
+    a, b = rng.normal(size=(2, 50))
+    for eps_w in (1e-6, 1.0, 1e-30):
+        L, R = O.cweno3_faces(a - b, a, a + b, eps_w)
+        assert np.allclose(L, a - 0.5 * b, atol=1e-14)
+        assert np.allclose(R, a + 0.5 * b, atol=1e-14)
+
+
+def test_cweno_linear_weights_give_optimal_parabola():
+    """With eps_w -> infinity the weights are the linear ones and the
+    reconstruction is P_opt, exact at the faces for cell averages of any
+    quadratic (this fixes P_opt and the definition of P_0)."""
+    rng = np.random.default_rng(1)
+    c = rng.normal(size=(3, 20))
+    p = [Poly(c[:, k]) for k in range(20)]
+
+    def avg(P, lo, hi):
+        I = P.integ()
+        return (I(hi) - I(lo)) / (hi - lo)
+
+    qm = np.array([avg(P, -1.5, -0.5) for P in p])
+    q0 = np.array([avg(P, -0.5, 0.5) for P in p])
+    qp = np.array([avg(P, 0.5, 1.5) for P in p])
+    L, R = O.cweno3_faces(qm, q0, qp, 1e40)
+    assert np.allclose(L, [P(-0.5) for P in p], atol=1e-12)
+    assert np.allclose(R, [P(0.5) for P in p], atol=1e-12)
+
+
+def test_cweno_indicators_are_jiang_shu_integrals():
+    """IS_k = sum_l int_{-1/2}^{1/2} (d^l P_k/ds^l)^2 ds for P_L, P_R and
+    P_0 = (P_opt - P_L/4 - P_R/4)/(1/2), evaluated by polynomial calculus."""
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        qm, q0, qp = rng.normal(size=3)
+        PL = Poly([q0, q0 - qm])
+        PR = Poly([q0, qp - q0])
+        D = qp - 2 * q0 + qm
+        Popt = Poly([q0 - D / 24, (qp - qm) / 2, D / 2])
+        P0 = (Popt - 0.25 * PL - 0.25 * PR) / 0.5
+
+        def js(P):
+            tot = 0.0
+            for l in (1, 2):
+                d = P.deriv(l) if P.degree() >= l else Poly([0.0])
+                I = (d * d).integ()
+                tot += I(0.5) - I(-0.5)
+            return tot
+
+        IS0, ISL, ISR = O.cweno3_indicators(qm, q0, qp)
+        assert np.isclose(IS0, js(P0), rtol=1e-12, atol=1e-14)
+        assert np.isclose(ISL, js(PL), rtol=1e-12, atol=1e-14)
+        assert np.isclose(ISR, js(PR), rtol=1e-12, atol=1e-14)
+
+
+def test_cweno_picks_smooth_substencil():
+    """With eps_w ~ 0 a constant left (right) sub-stencil takes all the weight:
+    IS_L = (q0 - qm)^2 (IS_R = (qp - q0)^2) is what vanishes."""
+    L, R = O.cweno3_faces(np.array(1.0), np.array(1.0), np.array(5.0), 1e-100)
+    assert np.isclose(L, 1.0) and np.isclose(R, 1.0)
+    L, R = O.cweno3_faces(np.array(5.0), np.array(1.0), np.array(1.0), 1e-100)
+    assert np.isclose(L, 1.0) and np.isclose(R, 1.0)
+
+
+def _cell_avg_sin(xc, h, k=1):
+    # average of sin(2 pi k x) over [xc - h/2, xc + h/2]
+    return np.sin(2 * np.pi * k * xc) * np.sin(np.pi * k * h) / (np.pi * k * h)
+
+
+def test_cweno_third_order_on_smooth_data():
+    """Face values of smooth data converge at (about) third order in L1."""
+    errs = []
+    for n in (40, 80, 160):
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+        q = 1.5 + _cell_avg_sin(xc, h)
+        qe = O.pad_cells(q, 0, "periodic")
+        L, R = O.cweno3_faces(qe[1:n + 1], qe[2:n + 2], qe[3:n + 3], 1e-6)
+        exact_R = 1.5 + np.sin(2 * np.pi * (xc + h / 2))
+        errs.append(np.mean(np.abs(R - exact_R)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[-1] > 2.5, (errs, orders)
+
+
+def test_kinetic_transport_consistency_and_order():
+    """L(f) approximates v . grad f in both directions and for both signs of v:
+    for cell averages of a smooth periodic profile the error of L against the
+    exact face-difference quotient falls at second order in L1 (third-order
+    face values; CWENO3 with a fixed eps_w loses one order at smooth extrema,
+    which shows in the max norm)."""
+    nv, vmax = 4, 1.0
+    v, w = O.velocity_grid(nv, vmax)
+    errs = []
+    for n in (32, 64):
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+        ax = _cell_avg_sin(xc, h)
+        ay = _cell_avg_sin(xc, h, 2)
+        f = np.broadcast_to((2.0 + ax[None, :] * ay[:, None])[:, :, None, None], (n, n, nv, nv)).copy()
+        L = O.kinetic_transport(f, v, h, h, "periodic", "periodic", 1e-6)
+        # exact: v_x d/dx + v_y d/dy of the cell average
+        dfx = (np.sin(2 * np.pi * (xc + h / 2)) - np.sin(2 * np.pi * (xc - h / 2))) / h
+        gx = dfx[None, :] * ay[:, None]
+        gy = ax[None, :] * (np.sin(4 * np.pi * (xc + h / 2)) - np.sin(4 * np.pi * (xc - h / 2)))[:, None] / h
+        exact = v[None, None, None, :] * gx[:, :, None, None] + v[None, None, :, None] * gy[:, :, None, None]
+        errs.append(np.mean(np.abs(L - exact)))
+    assert np.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_free_transport_matches_exact_shift():
+    """nu -> 0 (eps huge): the kinetic step is pure free transport; after time t
+    the cell averages equal those of f0(x - v t), with an L1 error falling at
+    (at least) second order -- this fixes the upwind direction of the flux."""
+    nv, vmax = 4, 1.0
+    v, w = O.velocity_grid(nv, vmax)
+    errs = []
+    t_end = 0.25
+    for n in (16, 32):
+        prob = O.Problem(nx=n, ny=n, nv=nv, vmax=vmax, switch="frozen")
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+
+        def prof(sx, sy):
+            return 2.0 + _cell_avg_sin(xc - sx, h)[None, :] * _cell_avg_sin(xc - sy, h)[:, None]
+
+        f0 = np.empty((n, n, nv, nv))
+        for a in range(nv):
+            for b in range(nv):
+                f0[:, :, a, b] = prof(0, 0) * (1.0 + 0.1 * a + 0.05 * b)
+        U = np.moveaxis(O.cons_from_moments(O.moments(f0, v, w)), -1, 0)
+        st = O.State(f=f0, U=U.copy(), kin=np.ones((n, n), bool), eps=np.full((n, n), 1e14))
+        steps = 4 * n // 8
+        dt = t_end / steps
+        for _ in range(steps):
+            st = O.advance(prob, st, dt, O.ARS233)
+        err = 0.0
+        for a in range(nv):
+            for b in range(nv):
+                ex = prof(v[b] * t_end, v[a] * t_end) * (1.0 + 0.1 * a + 0.05 * b)
+                err += np.mean(np.abs(st.f[:, :, a, b] - ex)) / nv ** 2
+        errs.append(err)
+    assert errs[1] < 0.02
+    assert np.log2(errs[0] / errs[1]) > 1.6, errs
+
+
+def test_euler_constant_state_is_steady():
+    U = np.empty((4, 6, 7))
+    U[0], U[1], U[2], U[3] = 1.3, 0.4, -0.2, 2.0
+    for bc in ("periodic", "outflow"):
+        P = O.euler_phi(U, 0.1, 0.2, bc, bc, 1e-6)
+        assert np.max(np.abs(P)) < 1e-13
+
+
+def exact_riemann_density(rhoL, uL, pL, rhoR, uR, pR, gamma, xi):
+    """Textbook exact solution of the 1-D Euler Riemann problem (ideal gas),
+    density sampled at xi = x/t (two-rarefaction/shock wave curves)."""
+    from scipy.optimize import brentq
+    cL, cR = np.sqrt(gamma * pL / rhoL), np.sqrt(gamma * pR / rhoR)
+
+    def fK(p, rho, pk, ck):
+        if p > pk:
+            A = 2.0 / ((gamma + 1) * rho)
+            B = (gamma - 1) / (gamma + 1) * pk
+            return (p - pk) * np.sqrt(A / (p + B))
+        return 2 * ck / (gamma - 1) * ((p / pk) ** ((gamma - 1) / (2 * gamma)) - 1)
+
+    g = lambda p: fK(p, rhoL, pL, cL) + fK(p, rhoR, pR, cR) + uR - uL
+    ps = brentq(g, 1e-10, 100.0, xtol=1e-14)
+    us = 0.5 * (uL + uR) + 0.5 * (fK(ps, rhoR, pR, cR) - fK(ps, rhoL, pL, cL))
+    gm = (gamma - 1) / (gamma + 1)
+    out = np.empty_like(xi)
+    for k, s in enumerate(xi):
+        if s <= us:  # left of contact
+            if ps > pL:
+                SL = uL - cL * np.sqrt((gamma + 1) / (2 * gamma) * ps / pL + (gamma - 1) / (2 * gamma))
+                out[k] = rhoL if s < SL else rhoL * ((ps / pL + gm) / (gm * ps / pL + 1))
+            else:
+                csL = cL * (ps / pL) ** ((gamma - 1) / (2 * gamma))
+                if s < uL - cL:
+                    out[k] = rhoL
+                elif s > us - csL:
+                    out[k] = rhoL * (ps / pL) ** (1 / gamma)
+                else:
+                    out[k] = rhoL * (2 / (gamma + 1) + gm / cL * (uL - s)) ** (2 / (gamma - 1))
+        else:
+            if ps > pR:
+                SR = uR + cR * np.sqrt((gamma + 1) / (2 * gamma) * ps / pR + (gamma - 1) / (2 * gamma))
+                out[k] = rhoR if s > SR else rhoR * ((ps / pR + gm) / (gm * ps / pR + 1))
+            else:
+                csR = cR * (ps / pR) ** ((gamma - 1) / (2 * gamma))
+                if s > uR + cR:
+                    out[k] = rhoR
+                elif s < us + csR:
+                    out[k] = rhoR * (ps / pR) ** (1 / gamma)
+                else:
+                    out[k] = rhoR * (2 / (gamma + 1) - gm / cR * (uR - s)) ** (2 / (gamma - 1))
+    return out
+
+
+def test_euler_sod_converges_to_exact_riemann_solution():
+    """Test 2 setting (Sec. 4.1.2) on the Euler part alone: Sod data along y,
+    (rho, u, p) = (1, 0, 1) | (1/8, 0, 1/32), gamma = 2 (d_v = 2), compared
+    with the exact Riemann solution at t = 0.15; the L1 error decreases under
+    refinement."""
+    errs = []
+    for n in (100, 200):
+        prob = O.Problem(nx=1, ny=n, x0=0, x1=0.1, y0=0, y1=1, bc_x="periodic", bc_y="outflow",
+                         nv=4, vmax=8.0, switch="frozen")
+        y = (np.arange(n) + 0.5) / n
+        rho = np.where(y <= 0.5, 1.0, 0.125)[:, None]
+        p = np.where(y <= 0.5, 1.0, 1.0 / 32)[:, None]
+        st = O.init_state(prob, rho, 0 * rho, 0 * rho, p / rho, np.full_like(rho, 1e-6),
+                          kin=np.zeros_like(rho, bool))
+        t_end = 0.15
+        steps = int(np.ceil(t_end / (0.4 / n / 2.0)))
+        for _ in range(steps):
+            st = O.advance(prob, st, t_end / steps, O.ARS233)
+        r = O.macro(st)[0][:, 0]
+        ex = exact_riemann_density(1.0, 0.0, 1.0, 0.125, 0.0, 1.0 / 32, 2.0, (y - 0.5) / t_end)
+        errs.append(np.mean(np.abs(r - ex)))
+    assert errs[1] < errs[0] and errs[1] < 0.01, errs

@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs shaped like the paper's 2-D tests.
+
+This module only draws input fields and names problem parameters.  It holds
+none of the method's arithmetic (no moments, no Maxwellians, no fluxes), so it
+can feed both the CUDA library and the CPU oracle without coupling them.
+
+Every generator returns a plain dict:
+  grid   -- nx, ny, x0, x1, y0, y1, bc_x, bc_y ('periodic' | 'outflow')
+  vmesh  -- nv, vmax
+  params -- beta, tau, eta_factor, delta, cweno_eps, switch, coupling
+  scheme -- 'ars233' | 'imex_euler'
+  dt, steps
+  fields -- rho, ux, uy, T, eps (float64 [ny, nx]) and kin (bool [ny, nx])
+
+The paper's workloads are analytic initial conditions (Test 1-6, Sec. 4), not
+datasets; these stand in for them at the sizes of the benchmark configurations.
+"""
+
+import numpy as np
+
+PARAMS = dict(beta=-0.5, tau=1.0, eta_factor=1.0, delta=1e-3, cweno_eps=1e-6,
+              switch="frozen", coupling="stage")
+
+
+def _centres(nx, ny, x0, x1, y0, y1):
+    x = x0 + (np.arange(nx) + 0.5) * (x1 - x0) / nx
+    y = y0 + (np.arange(ny) + 0.5) * (y1 - y0) / ny
+    return np.meshgrid(x, y)
+
+
+def _dt(cfl, nx, ny, x0, x1, y0, y1, vmax):
+    """dt = CFL min(dx, dy) / v_max, the time-step rule of Tests 2-6."""
+    return cfl * min((x1 - x0) / nx, (y1 - y0) / ny) / vmax
+
+
+def sine_periodic(nx=32, ny=32, nv=16, vmax=6.0, eps=1e-2, steps=10, cfl=0.5,
+                  scheme="imex_euler"):
+    """Plain ES-BGK, all kinetic, periodic [0,1]^2:
+    rho = 1 + 0.2 sin(2 pi x) sin(2 pi y), u = 0, T = 1, uniform eps."""
+    X, Y = _centres(nx, ny, 0, 1, 0, 1)
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)
+    z = np.zeros_like(rho)
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="periodic", bc_y="periodic"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS), scheme=scheme,
+        dt=_dt(cfl, nx, ny, 0, 1, 0, 1, vmax), steps=steps,
+        fields=dict(rho=rho, ux=z.copy(), uy=z.copy(), T=np.ones_like(rho),
+                    eps=np.full_like(rho, eps), kin=np.ones(rho.shape, bool)))
+
+
+def riemann_quadrants(nx=128, ny=128, nv=32, vmax=8.0, seed=0, steps=200, cfl=0.5,
+                      t_range=(0.25, 3.0), scheme="ars233", initial="fluid"):
+    """Coupled ES-BGK/Euler four-quadrant 2-D Riemann data on [0,1]^2, outflow.
+
+    Per quadrant rho, p ~ U[0.1, 1.5] and |u| ~ U[0, 0.7] at a uniform angle,
+    redrawn until T = p/rho lies in t_range so that the velocity grid resolves
+    the Maxwellians.  log10 eps = -2.5 + 1.5 sin(2 pi x) sin(2 pi y), a smooth
+    field between 1e-4 and 1e-1.  Plain switch with eta = eps, delta = 1e-3.
+    initial='fluid' starts all cells macroscopic, as the Sod test of Sec. 4.
+    """
+    rng = np.random.default_rng(seed)
+    X, Y = _centres(nx, ny, 0, 1, 0, 1)
+    rho = np.empty_like(X)
+    ux = np.empty_like(X)
+    uy = np.empty_like(X)
+    T = np.empty_like(X)
+    for qx in (0, 1):
+        for qy in (0, 1):
+            while True:
+                r, p = rng.uniform(0.1, 1.5, size=2)
+                if t_range[0] <= p / r <= t_range[1]:
+                    break
+            mag = rng.uniform(0.0, 0.7)
+            ang = rng.uniform(0.0, 2 * np.pi)
+            m = ((X >= 0.5) == bool(qx)) & ((Y >= 0.5) == bool(qy))
+            rho[m], T[m] = r, p / r
+            ux[m], uy[m] = mag * np.cos(ang), mag * np.sin(ang)
+    eps = 10.0 ** (-2.5 + 1.5 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y))
+    kin = np.zeros(X.shape, bool) if initial == "fluid" else np.ones(X.shape, bool)
+    params = dict(PARAMS, switch="plain")
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="outflow", bc_y="outflow"),
+        vmesh=dict(nv=nv, vmax=vmax), params=params, scheme=scheme,
+        dt=_dt(cfl, nx, ny, 0, 1, 0, 1, vmax), steps=steps,
+        fields=dict(rho=rho, ux=ux, uy=uy, T=T, eps=eps, kin=kin))
+
+
+def gaussian_blob(nx=256, ny=256, nv=48, vmax=8.0, eps=1e-3, steps=100, cfl=0.5,
+                  amp=0.5, width=0.1, u0=(0.3, 0.0), T0=1.0, scheme="ars233"):
+    """Precision form: periodic [0,1]^2, all kinetic,
+    rho = 1 + amp exp(-|x - (1/2,1/2)|^2 / width^2), u = u0, T = T0."""
+    X, Y = _centres(nx, ny, 0, 1, 0, 1)
+    rho = 1.0 + amp * np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / width ** 2)
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="periodic", bc_y="periodic"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS), scheme=scheme,
+        dt=_dt(cfl, nx, ny, 0, 1, 0, 1, vmax), steps=steps,
+        fields=dict(rho=rho, ux=np.full_like(rho, u0[0]), uy=np.full_like(rho, u0[1]),
+                    T=np.full_like(rho, T0), eps=np.full_like(rho, eps),
+                    kin=np.ones(rho.shape, bool)))
+
+
+def order_test(n=90, nv=32, vmax=5.0, L=6.0, eps=1e-2, seed=0, kin_fraction=0.5,
+               coupling="stage"):
+    """Test 1 (Sec. 4.1.1): [0,6]^2 periodic, rho = 1 + 0.1 exp(-3 d^2),
+    T = 0.3 (1 + 0.1 exp(-3 d^2)), u = 0, d the distance to the centre, and a
+    random regime map frozen for the whole run."""
+    rng = np.random.default_rng(seed)
+    X, Y = _centres(n, n, 0, L, 0, L)
+    d2 = (X - L / 2) ** 2 + (Y - L / 2) ** 2
+    bump = 0.1 * np.exp(-3.0 * d2)
+    rho = 1.0 + bump
+    T = 0.3 * (1.0 + bump)
+    z = np.zeros_like(rho)
+    kin = rng.uniform(size=rho.shape) < kin_fraction
+    return dict(
+        grid=dict(nx=n, ny=n, x0=0.0, x1=L, y0=0.0, y1=L, bc_x="periodic", bc_y="periodic"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS, coupling=coupling),
+        scheme="ars233", dt=None, steps=None,
+        fields=dict(rho=rho, ux=z.copy(), uy=z.copy(), T=T, eps=np.full_like(rho, eps), kin=kin))
+
+
+def random_cells(n, nv, vmax, seed=0, anisotropy=0.3):
+    """Random positive per-cell distributions (n, nv, nv): a Gaussian-like
+    bump with random centre, widths and tilt times a random positive factor.
+    Used for per-cell kernel checks (collision, moments)."""
+    rng = np.random.default_rng(seed)
+    dv = 2.0 * vmax / nv
+    v = -vmax + (np.arange(nv) + 0.5) * dv
+    VX, VY = np.meshgrid(v, v)
+    out = np.empty((n, nv, nv))
+    for c in range(n):
+        cx, cy = rng.uniform(-0.5, 0.5, size=2)
+        sx, sy = rng.uniform(0.7, 1.4, size=2)
+        tilt = rng.uniform(-anisotropy, anisotropy)
+        q = ((VX - cx) / sx) ** 2 + ((VY - cy) / sy) ** 2 + 2 * tilt * (VX - cx) * (VY - cy) / (sx * sy)
+        out[c] = rng.uniform(0.5, 1.5) * np.exp(-0.5 * q) * (1 + 0.2 * rng.uniform(size=(nv, nv)))
+    return out
+
+
+def batched_cases(n_cases=64, seed0=0, sizes=None, nvs=None, steps=100):
+    """Batched form: independent periodic cases of uneven sizes.
+
+    Case c (seed = seed0 + c): N_x = N_y from {64, 80, ..., 256}, N_v from
+    {16, 18, ..., 40}, v_max = 8, eps log-uniform in [1e-4, 1e-1], rho and T
+    random smooth fields (4 Fourier modes, wavenumber <= 3) mapped affinely
+    into [0.5, 1.5] and [0.5, 2], u = 0, plain switch, ARS(2,3,3).
+    """
+    sizes = list(range(64, 257, 16)) if sizes is None else list(sizes)
+    nvs = list(range(16, 41, 2)) if nvs is None else list(nvs)
+    cases = []
+    for c in range(n_cases):
+        rng = np.random.default_rng(seed0 + c)
+        n = int(rng.choice(sizes))
+        nv = int(rng.choice(nvs))
+        X, Y = _centres(n, n, 0, 1, 0, 1)
+
+        def smooth():
+            acc = np.zeros_like(X)
+            for _ in range(4):
+                kx, ky = rng.integers(0, 4, size=2)
+                ph = rng.uniform(0, 2 * np.pi)
+                acc += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * X + ky * Y) + ph)
+            lo, hi = acc.min(), acc.max()
+            return (acc - lo) / (hi - lo) if hi > lo else np.zeros_like(acc)
+
+        rho = 0.5 + smooth()
+        T = 0.5 + 1.5 * smooth()
+        eps = 10.0 ** rng.uniform(-4, -1)
+        z = np.zeros_like(rho)
+        cases.append(dict(
+            grid=dict(nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="periodic", bc_y="periodic"),
+            vmesh=dict(nv=nv, vmax=8.0), params=dict(PARAMS, switch="plain"), scheme="ars233",
+            dt=_dt(0.5, n, n, 0, 1, 0, 1, 8.0), steps=steps,
+            fields=dict(rho=rho, ux=z.copy(), uy=z.copy(), T=T, eps=np.full_like(rho, eps),
+                        kin=np.ones(rho.shape, bool))))
+    return cases
