@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the ES-BGK kinetic stage update (coupled IMEX domain decomposition).
+
+Workload (default): the coupled ES-BGK/Euler configuration -- 128 x 128 cells on
+[0,1]^2 (outflow), 32 x 32 velocities on [-8,8]^2, seeded four-quadrant Riemann
+data, eps(x) between 1e-4 and 1e-1, plain switch, ARS(2,3,3), f stored in FP32.
+A step is one full step of Algorithm 1 (regime update, three stages with
+coupling, final combination).  Metric: kinetic (cell x velocity) stage updates
+per second = sum over steps of K_kinetic * N_v^2 * (transport evaluations).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload riemann|blob|sine] [--prec fp32|fp64|bf16]
+Under torchrun every rank runs an independent replica (seed = rank): weak
+scaling, no collective on the data path.  Prints one JSON line on rank 0.
+"""
+
+import os
+
+# the CPU oracle legs are timed single-threaded; say so in "cores"
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "kinetic (cell x velocity) stage updates/s"
+UNIT = "updates/s"
+# accesses of f-sized arrays per element per step, and transport evaluations
+# per step (running-accumulator form of the IMEX step)
+ACCESSES = {"ars233": (12, 3), "imex_euler": (2, 1)}
+ELEM = {"fp64": 8, "fp32": 4, "bf16": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "bf16": "bf16-storage/f32"}
+
+
+def make_workload(name, seed):
+    if name == "riemann":
+        return W.riemann_quadrants(seed=seed)
+    if name == "blob":
+        return W.gaussian_blob()
+    if name == "sine":
+        return W.sine_periodic()
+    raise SystemExit("unknown workload " + name)
+
+
+def describe(wl, name, prec):
+    g, v, p = wl["grid"], wl["vmesh"], wl["params"]
+    return {"workload": "%s %dx%d cells, %dx%d velocities on [-%g,%g]^2, %s, %s switch, %s storage" % (
+        {"riemann": "four-quadrant Riemann ES-BGK/Euler", "blob": "Gaussian blob all-kinetic",
+         "sine": "sine-periodic all-kinetic"}[name], g["nx"], g["ny"], v["nv"], v["nv"], v["vmax"], v["vmax"],
+        wl["scheme"], p["switch"], prec),
+        "nx": g["nx"], "ny": g["ny"], "nv": v["nv"], "scheme": wl["scheme"], "prec": prec,
+        "switch": p["switch"], "dt": wl["dt"]}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+
+def oracle_sample(name, steps, warmup=0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the same
+    configuration on a 32 x 32 window of cells (same velocity grid, scheme,
+    switch and data recipe).  Returns (updates/s, description, per-step s)."""
+    import oracle as O
+    if name == "riemann":
+        wl = W.riemann_quadrants(nx=32, ny=32, seed=0)
+    elif name == "blob":
+        wl = W.gaussian_blob(nx=16, ny=16)
+    else:
+        wl = W.sine_periodic()
+    P = O.Problem(**wl["grid"], **wl["vmesh"], **wl["params"])
+    tab = {"ars233": O.ARS233, "imex_euler": O.IMEX_EULER}[wl["scheme"]]
+    nL = ACCESSES[wl["scheme"]][1]
+    st = O.init_state(P, **wl["fields"])
+    for _ in range(warmup):
+        st = O.step(P, st, wl["dt"], tab)
+    upd, per = 0, []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st = O.step(P, st, wl["dt"], tab)
+        per.append(time.perf_counter() - t0)
+        upd += int(st.kin.sum()) * P.nv * P.nv * nL
+    g, v = wl["grid"], wl["vmesh"]
+    desc = "FP64 numpy oracle, %d steps of the same configuration on %dx%d cells (%dx%d velocities), " \
+           "single-threaded" % (steps, g["nx"], g["ny"], v["nv"], v["nv"])
+    return upd / sum(per), desc, per
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    val, desc, per = oracle_sample(args.workload, args.steps, warmup=args.warmup)
+    wl = make_workload(args.workload, 0)
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": describe(wl, args.workload, "fp64"), "impl": "reference",
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_03586_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(m["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def stored_traffic(prec, workload):
+    """DRAM bytes per kinetic element-evaluation of the stage kernel from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d["entries"]["%s/%s" % (workload, prec)]
+        if e["source_hash"] != source_hash():
+            return None
+        return float(e["dram_bytes_per_element_eval"])
+    except Exception:
+        return None
+
+
+def ours_arm(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2512_03586_gb300 as G
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = make_workload(args.workload, rank)
+    f = wl["fields"]
+    s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=args.prec, device=dev)
+    s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    tab = G.make_tableau(wl["scheme"])
+    dt = wl["dt"]
+    nvv = wl["vmesh"]["nv"] ** 2
+    acc, nL = ACCESSES[wl["scheme"]]
+    ebytes = ELEM[args.prec]
+    for _ in range(args.warmup):
+        s.step(dt, tab)
+    s.sync()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    # --- timed region: K steps, L2 flushed before each (outside the events)
+    c0 = s.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.step(dt, tab)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    s.sync()
+    c1 = s.counters()
+    updates = (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv
+    if world > 1:
+        t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_max, updates_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, updates_all = ms, float(updates)
+    value = updates_all / (ms_max * 1e-3)
+
+    # --- per-kernel device times (separate pass; events around each launch)
+    k2 = max(3, min(args.steps, 20))
+    s.timing(True)
+    s.timing_read()
+    cb = s.counters()
+    for k in range(k2):
+        flush.fill_(float(k))
+        s.step(dt, tab)
+    tk = s.timing_read()
+    s.timing(False)
+    ca = s.counters()
+    evals = ca["kinetic_cell_updates"] - cb["kinetic_cell_updates"]
+    fills = ca["buffer_fills"] - cb["buffer_fills"]
+    st_ms = tk["stage"][0] + tk["final"][0]
+    st_n = tk["stage"][1] + tk["final"][1]
+    algo_bytes = evals * nvv * (acc / nL) * ebytes + fills * nvv * ebytes
+    achieved = algo_bytes / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
+    peak, peak_src = measured_peak()
+    tr = stored_traffic(args.prec, args.workload)
+    launches_per_step = (tk["l1"][1] + tk["flags"][1] + 2 * tk["compact"][1] + tk["prep"][1] + tk["stage"][1]
+                         + tk["final"][1]) / k2
+    step_ms_kernels = sum(v[0] for v in tk.values()) / k2
+
+    # --- end to end through the C ABI with pinned host buffers
+    nc = s.nc
+    pin = {k: torch.empty(nc, dtype=torch.float64).pin_memory().numpy() for k in ("rho", "ux", "uy", "T", "eps")}
+    mom = s.moments()
+    for q, k in enumerate(("rho", "ux", "uy", "T")):
+        pin[k][:] = mom[q].reshape(-1)
+    pin["eps"][:] = f["eps"].reshape(-1)
+    kin = torch.empty(nc, dtype=torch.uint8).pin_memory().numpy()
+    kin[:] = s.flags().reshape(-1)
+    outp = torch.empty((4, nc), dtype=torch.float64).pin_memory().numpy()
+    k3 = max(3, min(args.steps, 10))
+    e0 = s.counters()["kinetic_cell_updates"]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k3):
+        s.set_state(pin["rho"], pin["ux"], pin["uy"], pin["T"], pin["eps"], kin)
+        s.step(dt, tab)
+        s.moments(out=outp)
+    t_e2e = time.perf_counter() - t0
+    e_upd = (s.counters()["kinetic_cell_updates"] - e0) * nvv
+
+    kin_frac = c1["kinetic_cells"] / nc
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cv, cdesc, _ = oracle_sample(args.workload, args.cpu_steps)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
+
+    cfg = describe(wl, args.workload, args.prec)
+    cfg.update({"l2": "flushed (256 MB write) before every timed step, outside the step's events",
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "kinetic_fraction_end": kin_frac, "kernel_launches_per_step": launches_per_step})
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic", "config": cfg,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": (achieved / peak) if achieved else None,
+                        "traffic": (tr * evals * nvv / st_n) if (tr is not None and st_n) else None,
+                        "kernel": "stage_kernel (fused IMEX stage + final combination)",
+                        "algorithmic_bytes_per_launch": algo_bytes / st_n if st_n else None,
+                        "avg_launch_ms": st_ms / st_n if st_n else None, "peak_source": peak_src,
+                        "bytes_model": "%d f-array accesses per element per step / %d transport evaluations x %d B,"
+                                       " plus one write per buffer-cell element reconstructed" % (acc, nL, ebytes)},
+           "kernel_ms_per_step": {k: v[0] / k2 for k, v in tk.items()},
+           "kernel_sum_ms_per_step": step_ms_kernels,
+           "e2e": {"value": e_upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * nc * 8 + nc,
+                   "d2h_bytes_per_step": 4 * nc * 8,
+                   "note": "each step: esbgk_set_state from pinned host arrays (restart from the macroscopic "
+                           "state and regime map), esbgk_step, esbgk_get_moments to pinned host arrays"},
+           "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * esbgk.h -- C ABI of the GB300 (sm_103a) library for the coupled IMEX
+ * domain-decomposition method for the ES-BGK model (Caparello & Tenna,
+ * arXiv 2512.03586).
+ *
+ * One context advances one 2-D problem: N_x x N_y cells, each either kinetic
+ * (a discrete distribution f over N_v x N_v velocities) or fluid (Euler
+ * conserved variables U = (rho, rho u_x, rho u_y, E)).  One step is
+ * Algorithm 1 of the paper: regime update (Sec. 3.1.2), then the s stages of
+ * an IMEX Runge-Kutta scheme (Eqs. RKEI1-RKEI2 for f, RKEuler for U) with the
+ * coupling of Sec. 3.3 at every stage, then the final combination.
+ *
+ * Conventions (every function):
+ *  - Return value: ESBGK_OK (0) or a negative esbgk_status.  Errors are sticky:
+ *    after an error every call but esbgk_last_error/esbgk_destroy returns it
+ *    until esbgk_set_state succeeds.
+ *  - Host arrays are caller-owned, C-contiguous float64 (uint8 for flags),
+ *    cell index c = j * N_x + i (j along y).  f is [c][v_y index][v_x index].
+ *    They are copied in or out inside the call; calls that return data wait
+ *    for the context's stream.
+ *  - Device memory: the library allocates none.  The caller passes one device
+ *    workspace of esbgk_workspace_bytes() bytes (e.g. a torch uint8 tensor)
+ *    and keeps it alive until esbgk_destroy.
+ *  - All device work goes to the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  A context is not thread-safe.
+ *  - Velocity nodes (Sec. 3.2): v_k = -v_max + (k + 1/2) dv, dv = 2 v_max/N_v,
+ *    quadrature weight dv^2 (midpoint rule).
+ */
+#ifndef ESBGK_H
+#define ESBGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esbgk_ctx esbgk_ctx;
+
+typedef enum {
+  ESBGK_OK = 0,
+  ESBGK_E_ARG = -1,            /* invalid argument (sizes, tableau, dt, NULL)        */
+  ESBGK_E_WORKSPACE = -2,      /* workspace too small or misaligned (< 256 B)        */
+  ESBGK_E_CUDA = -3,           /* a CUDA runtime call failed; see esbgk_last_error   */
+  ESBGK_E_NONREALIZABLE = -4,  /* rho <= 0, T <= 0, det(temperature tensor) <= 0 or a
+                                  singular moment system in some cell                */
+  ESBGK_E_TIMEOUT = -5,        /* reserved: a bounded device wait expired           */
+  ESBGK_E_STATE = -6           /* call out of order (e.g. step before set_state)    */
+} esbgk_status;
+
+typedef enum { ESBGK_FP64 = 0, ESBGK_FP32 = 1, ESBGK_BF16 = 2 } esbgk_prec;
+typedef enum { ESBGK_BC_PERIODIC = 0, ESBGK_BC_OUTFLOW = 1 } esbgk_bc;
+typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1 } esbgk_switch;
+typedef enum { ESBGK_COUPLE_STAGE = 0, ESBGK_COUPLE_STEP = 1 } esbgk_coupling;
+
+/* Cartesian grid of Sec. 3.2: N_x x N_y cells on [x0,x1] x [y0,y1]; two ghost
+ * cells per side, periodic or outflow (copy of the edge cell). */
+typedef struct {
+  int32_t nx, ny;
+  double x0, x1, y0, y1;
+  int32_t bc_x, bc_y; /* esbgk_bc */
+} esbgk_grid;
+
+/* Velocity grid of Sec. 3.2: N_v points per direction on [-v_max, v_max]. */
+typedef struct {
+  int32_t nv;
+  double vmax;
+} esbgk_vmesh;
+
+/* Model and switch parameters.
+ *  beta       ES-BGK parameter (Sec. 2): Pr = 1/(1 - beta), beta in [-1/2, 1).
+ *  tau        collision rate nu = tau / eps(x) (tau constant).
+ *  eta_factor eta = eta_factor * eps(x) in the criterion of Eq. crit:CompEuler.
+ *  delta      threshold of Eq. eqKintoFluid1 (absolute L1 deviation).
+ *  cweno_eps  epsilon of the CWENO3 nonlinear weights (Sec. 3.2).
+ *  sw         esbgk_switch: FROZEN keeps the regime map, PLAIN applies
+ *             Sec. 3.1.2 before every step.
+ *  coupling   esbgk_coupling: STAGE couples at every stage (Algorithm 1),
+ *             STEP only at step end (the LOC-hybrid of Sec. 3.5).
+ *  prec       esbgk_prec of f storage and per-element arithmetic: FP64; FP32;
+ *             BF16 storage with FP32 arithmetic.  Per-cell tensor solves,
+ *             U and the totals are always FP64. */
+typedef struct {
+  double beta, tau, eta_factor, delta, cweno_eps;
+  int32_t sw, coupling, prec;
+} esbgk_params;
+
+/* IMEX tableaux (Sec. 3.4), 2 <= s <= 4 stages: explicit (At, bt) for the
+ * transport and the Euler system (Abar = At, bbar = bt), implicit (A, b) for
+ * the relaxation.  Entry (i, j) of a matrix is At[i*4 + j] (row stride 4
+ * whatever s).  At must be strictly lower triangular, A lower triangular with
+ * A[i][i] >= 0; at most three running accumulators may be needed (always true
+ * when the first stage is explicit, as in ARS schemes). */
+typedef struct {
+  int32_t s;
+  double At[16], bt[4], A[16], b[4];
+} esbgk_tableau;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int esbgk_version(void);
+
+/* Bytes of device workspace needed for this problem; 0 on invalid input. */
+size_t esbgk_workspace_bytes(const esbgk_grid* grid, const esbgk_vmesh* vmesh,
+                             const esbgk_params* params);
+
+/* Create a context.  `workspace` is device memory (>= 256-byte aligned) of at
+ * least esbgk_workspace_bytes() bytes, owned by the caller.  `stream` is a
+ * cudaStream_t or NULL.  On success *out receives the context (host-allocated;
+ * free with esbgk_destroy). */
+int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_params* params,
+                 void* workspace, size_t workspace_bytes, void* stream, esbgk_ctx** out);
+
+/* Release the host context (the workspace stays the caller's). NULL is a no-op. */
+void esbgk_destroy(esbgk_ctx* ctx);
+
+/* Set the macroscopic state (Sec. 3.3): rho, u_x, u_y, T and the Knudsen field
+ * eps, each [N_c] float64, and the regime map kinetic[N_c] (1 = kinetic;
+ * NULL = all kinetic).  Kinetic cells get f = the discrete Maxwellian of
+ * (rho, u, T) (Eq. Coupling_FluKin), as every test of Sec. 4 starts.  Clears a
+ * sticky error.  Returns E_ARG for rho <= 0, T <= 0 or eps < 0 anywhere. */
+int esbgk_set_state(esbgk_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    const double* T, const double* eps, const uint8_t* kinetic);
+
+/* Overwrite f of every cell from host float64 [N_c][N_v][N_v] (resume from a
+ * checkpoint; values of fluid cells are kept but unused) and set U := moments
+ * of f in kinetic cells (Eq. Coupling_KinFlu). */
+int esbgk_set_f(esbgk_ctx* ctx, const double* f);
+
+/* Copy f of every cell to host float64 [N_c][N_v][N_v] (fluid cells: stale). */
+int esbgk_get_f(esbgk_ctx* ctx, double* f);
+
+/* Regime update of Algorithm 1 from the current state (Eqs. crit:CompEuler,
+ * eqKintoFluid1): lambda_A = max |eig(I - S_1)| with the S_1 of Sec. 3.1.1
+ * (central differences of u and T), the L1 deviation of f from its Maxwellian
+ * in kinetic cells; new flag = lambda_A > eta  or  (kinetic and L1 > delta).
+ * Cells that turn kinetic get f := Maxwellian(U) at the next advance. */
+int esbgk_regime_update(esbgk_ctx* ctx);
+
+/* Replace the regime map (kinetic[N_c], 1 = kinetic) before the next advance,
+ * e.g. to impose a reference map; conversions are taken relative to the map
+ * of the previous step. */
+int esbgk_set_flags(esbgk_ctx* ctx, const uint8_t* kinetic);
+
+/* Copy the current regime map to host kinetic[N_c]. */
+int esbgk_get_flags(esbgk_ctx* ctx, uint8_t* kinetic);
+
+/* Indicators of the last regime update: lamA[N_c] and L1[N_c] (L1 = 0 in
+ * cells that were fluid).  Either pointer may be NULL. */
+int esbgk_get_indicators(esbgk_ctx* ctx, double* lamA, double* L1);
+
+/* Advance one step with the current regime map (Algorithm 1 without the
+ * regime update): stages of Eqs. RKEuler/RKEI1 with per-stage coupling
+ * (Remark rem_coupling), final combination Eqs. RKEuler_2/RKEI2.  dt > 0. */
+int esbgk_advance(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
+
+/* One full step of Algorithm 1: esbgk_regime_update (PLAIN switch only) then
+ * esbgk_advance.  Enqueued on the stream; does not wait. */
+int esbgk_step(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
+
+/* Macroscopic fields of every cell (moments of f in kinetic cells, the Euler
+ * solution elsewhere), each [N_c] float64; any pointer may be NULL. */
+int esbgk_get_moments(esbgk_ctx* ctx, double* rho, double* ux, double* uy, double* T);
+
+/* Conserved variables U[4][N_c] (rho, rho u_x, rho u_y, E). */
+int esbgk_get_cons(esbgk_ctx* ctx, double* U);
+
+/* Global mass, x- and y-momentum and energy: sum over cells of U dx dy. */
+int esbgk_totals(esbgk_ctx* ctx, double out[4]);
+
+/* Work counters since create: kinetic cell-stage updates (each counts N_v^2
+ * element updates; one per transport evaluation of a kinetic cell), steps,
+ * the kinetic cells of the current map, and buffer-cell reconstructions
+ * f := Maxwellian(U) done inside the stages.  Any pointer may be NULL. */
+int esbgk_counters(esbgk_ctx* ctx, long long* kinetic_cell_updates, long long* steps,
+                   long long* kinetic_cells, long long* buffer_fills);
+
+/* Kernel classes reported by esbgk_timing_read. */
+enum {
+  ESBGK_K_L1 = 0,      /* L1 deviation of kinetic cells (regime update)        */
+  ESBGK_K_FLAGS = 1,   /* criteria and new regime map                          */
+  ESBGK_K_COMPACT = 2, /* categorisation and compaction of the map             */
+  ESBGK_K_PREP = 3,    /* start-of-step coupling (buffer and converted cells)  */
+  ESBGK_K_STAGE = 4,   /* fused IMEX stage kernels                             */
+  ESBGK_K_FINAL = 5,   /* final combination (same kernel as the stages)        */
+  ESBGK_K_OTHER = 6,
+  ESBGK_K_COUNT = 7
+};
+
+/* Per-kernel timing: when enabled, every kernel the library launches on the
+ * context's stream is bracketed by CUDA events on that stream.  Host event
+ * objects only; no device memory. */
+int esbgk_timing(esbgk_ctx* ctx, int enable);
+
+/* Wait for the stream and return, per kernel class, the summed device time in
+ * milliseconds (ms[ESBGK_K_COUNT]) and the number of launches
+ * (launches[ESBGK_K_COUNT]) recorded since the last read; then reset.  Either
+ * pointer may be NULL; n is the capacity of both arrays. */
+int esbgk_timing_read(esbgk_ctx* ctx, double* ms, long long* launches, int32_t n);
+
+/* Wait for the stream and report a pending device error. */
+int esbgk_sync(esbgk_ctx* ctx);
+
+/* Message of the last error (NUL-terminated, truncated to n) and, for
+ * ESBGK_E_NONREALIZABLE, the first offending cell (else -1). */
+int esbgk_last_error(esbgk_ctx* ctx, char* buf, size_t n, long long* bad_cell);
+
+/* Per-cell collision check entry (device pointers, no context): for n cells of
+ * f*[n][N_v][N_v] (storage type of `prec`) and h[n] (float64) solve the
+ * implicit relaxation f = f* + h (G_hat[f] - f) of Eq. RKEI1 through the
+ * conserved moments and write f[n][N_v][N_v] and G_hat (same type).  This is
+ * the device code the stage kernel uses.  Enqueued on `stream` (does not
+ * wait); a cell whose state is not realizable (rho <= 0, T <= 0, singular
+ * moment system) gets NaN in both outputs. */
+int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax,
+                      double beta, int32_t prec, void* f_out, void* g_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESBGK_H */

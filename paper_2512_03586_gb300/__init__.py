@@ -1,0 +1,246 @@
+"""GB300 (sm_103a) library for the coupled IMEX domain-decomposition method of
+the ES-BGK model (Caparello & Tenna, arXiv 2512.03586).
+
+The compute path is libesbgk.so (hand-written CUDA behind the C ABI of
+include/esbgk.h).  This package only marshals arguments: PyTorch provides the
+device workspace and the stream, numpy the host arrays.  Every entry point
+loads libesbgk.so on first use and raises ImportError when it has not been
+built -- there is no CPU fallback.
+"""
+
+import ctypes
+import importlib
+
+import numpy as np
+
+
+def _lib():
+    """The ctypes binding of libesbgk.so; raises ImportError when the library
+    has not been built (no fallback)."""
+    return importlib.import_module(__name__ + "._abi")
+
+
+class Error(RuntimeError):
+    """A negative esbgk_status returned by the library."""
+
+    NAMES = {0: "OK", -1: "E_ARG", -2: "E_WORKSPACE", -3: "E_CUDA", -4: "E_NONREALIZABLE",
+             -5: "E_TIMEOUT", -6: "E_STATE"}
+
+    def __init__(self, code, msg="", bad_cell=-1):
+        self.code = code
+        self.bad_cell = bad_cell
+        super().__init__("%s (%d): %s" % (self.NAMES.get(code, "?"), code, msg))
+
+
+BC = {"periodic": 0, "outflow": 1}
+SWITCH = {"frozen": 0, "plain": 1}
+COUPLING = {"stage": 0, "step": 1}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+__all__ = ["Solver", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
+
+_ALPHA = (3.0 + 3.0 ** 0.5) / 6.0
+#: ARS(2,3,3) (Sec. 3.4): explicit (At, bt), implicit (A, b), alpha = (3+sqrt 3)/6.
+ARS233 = dict(
+    At=[[0.0, 0.0, 0.0], [_ALPHA, 0.0, 0.0], [_ALPHA - 1.0, 2.0 - 2.0 * _ALPHA, 0.0]],
+    bt=[0.0, 0.5, 0.5],
+    A=[[0.0, 0.0, 0.0], [0.0, _ALPHA, 0.0], [0.0, 1.0 - 2.0 * _ALPHA, _ALPHA]],
+    b=[0.0, 0.5, 0.5])
+#: First-order IMEX (Filbet-Jin) in ARS(1,1,1) form: f^{n+1} = relax(f^n - dt L(f^n)).
+IMEX_EULER = dict(At=[[0.0, 0.0], [1.0, 0.0]], bt=[1.0, 0.0], A=[[0.0, 0.0], [0.0, 1.0]], b=[0.0, 1.0])
+TABLEAUX = {"ars233": ARS233, "imex_euler": IMEX_EULER}
+
+
+def make_tableau(t):
+    """esbgk_tableau from a name ('ars233', 'imex_euler') or a dict At, bt, A, b."""
+    if isinstance(t, str):
+        t = TABLEAUX[t]
+    At, A = np.asarray(t["At"], float), np.asarray(t["A"], float)
+    bt, b = np.asarray(t["bt"], float), np.asarray(t["b"], float)
+    s = len(b)
+    out = _lib().Tableau()
+    out.s = s
+    for i in range(s):
+        out.bt[i] = bt[i]
+        out.b[i] = b[i]
+        for j in range(s):
+            out.At[i * 4 + j] = At[i, j]
+            out.A[i * 4 + j] = A[i, j]
+    return out
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class Solver:
+    """One problem on one GPU: wraps esbgk_create / esbgk_* on a torch workspace.
+
+    grid: nx, ny, x0, x1, y0, y1, bc_x, bc_y ('periodic' | 'outflow')
+    vmesh: nv, vmax
+    params: beta, tau, eta_factor, delta, cweno_eps, switch ('frozen' | 'plain'),
+            coupling ('stage' | 'step'); prec: 'fp64' | 'fp32' | 'bf16'.
+    """
+
+    def __init__(self, grid, vmesh, params, prec="fp64", device=None, stream=None):
+        import torch
+        _abi = _lib()
+        self._abi = _abi
+        self.torch = torch
+        self.grid = _abi.Grid(int(grid["nx"]), int(grid["ny"]), float(grid.get("x0", 0.0)), float(grid.get("x1", 1.0)),
+                         float(grid.get("y0", 0.0)), float(grid.get("y1", 1.0)), BC[grid.get("bc_x", "periodic")],
+                         BC[grid.get("bc_y", "periodic")])
+        self.vmesh = _abi.VMesh(int(vmesh["nv"]), float(vmesh["vmax"]))
+        p = params
+        self.params = _abi.Params(float(p.get("beta", -0.5)), float(p.get("tau", 1.0)), float(p.get("eta_factor", 1.0)),
+                             float(p.get("delta", 1e-3)), float(p.get("cweno_eps", 1e-6)),
+                             SWITCH[p.get("switch", "frozen")], COUPLING[p.get("coupling", "stage")], PREC[prec])
+        self.nx, self.ny, self.nv = self.grid.nx, self.grid.ny, self.vmesh.nv
+        self.nc = self.nx * self.ny
+        nbytes = _abi.esbgk_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.vmesh), ctypes.byref(self.params))
+        if nbytes == 0:
+            raise Error(-1, "invalid grid/velocity mesh/parameters")
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            r = _abi.esbgk_create(ctypes.byref(self.grid), ctypes.byref(self.vmesh), ctypes.byref(self.params),
+                                  ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx))
+        if r != 0:
+            raise Error(r, "esbgk_create")
+        self.workspace_bytes = nbytes
+
+    # -- helpers ------------------------------------------------------------
+    def _check(self, r, what):
+        if r != 0:
+            buf = ctypes.create_string_buffer(512)
+            bad = ctypes.c_longlong(-1)
+            self._abi.esbgk_last_error(self._ctx, buf, 512, ctypes.byref(bad))
+            raise Error(r, "%s: %s" % (what, buf.value.decode(errors="replace")), bad.value)
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._abi.esbgk_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ----------------------------------------------------------------
+    def set_state(self, rho, ux, uy, T, eps, kin=None):
+        n = self.nc
+        arrs = [_f64(a, n) for a in (rho, ux, uy, T, eps)]
+        k = None if kin is None else np.ascontiguousarray(np.asarray(kin).reshape(-1), dtype=np.uint8)
+        r = self._abi.esbgk_set_state(self._ctx, *[_dptr(a) for a in arrs], None if k is None else _u8ptr(k))
+        self._check(r, "set_state")
+
+    def set_f(self, f):
+        f = _f64(f, self.nc * self.nv * self.nv)
+        self._check(self._abi.esbgk_set_f(self._ctx, _dptr(f)), "set_f")
+
+    def f(self):
+        out = np.empty((self.ny, self.nx, self.nv, self.nv))
+        self._check(self._abi.esbgk_get_f(self._ctx, _dptr(out)), "get_f")
+        return out
+
+    def regime_update(self):
+        self._check(self._abi.esbgk_regime_update(self._ctx), "regime_update")
+
+    def set_flags(self, kin):
+        k = np.ascontiguousarray(np.asarray(kin).reshape(-1), dtype=np.uint8)
+        self._check(self._abi.esbgk_set_flags(self._ctx, _u8ptr(k)), "set_flags")
+
+    def flags(self):
+        out = np.empty((self.ny, self.nx), np.uint8)
+        self._check(self._abi.esbgk_get_flags(self._ctx, _u8ptr(out)), "get_flags")
+        return out.astype(bool)
+
+    def indicators(self):
+        lam = np.empty((self.ny, self.nx))
+        l1 = np.empty((self.ny, self.nx))
+        self._check(self._abi.esbgk_get_indicators(self._ctx, _dptr(lam), _dptr(l1)), "get_indicators")
+        return lam, l1
+
+    def advance(self, dt, tableau="ars233"):
+        t = tableau if isinstance(tableau, self._abi.Tableau) else make_tableau(tableau)
+        self._check(self._abi.esbgk_advance(self._ctx, float(dt), ctypes.byref(t)), "advance")
+
+    def step(self, dt, tableau="ars233"):
+        t = tableau if isinstance(tableau, self._abi.Tableau) else make_tableau(tableau)
+        self._check(self._abi.esbgk_step(self._ctx, float(dt), ctypes.byref(t)), "step")
+
+    def moments(self, out=None):
+        """(rho, u_x, u_y, T) as a (4, ny, nx) float64 array (written into `out`
+        when given: C-contiguous float64, e.g. pinned host memory)."""
+        if out is None:
+            out = np.empty((4, self.ny, self.nx))
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 4 * self.nc
+        o = out.reshape(4, -1)
+        self._check(self._abi.esbgk_get_moments(self._ctx, *[_dptr(o[q]) for q in range(4)]), "get_moments")
+        return out
+
+    def cons(self):
+        out = np.empty((4, self.ny, self.nx))
+        self._check(self._abi.esbgk_get_cons(self._ctx, _dptr(out)), "get_cons")
+        return out
+
+    def totals(self):
+        out = np.empty(4)
+        self._check(self._abi.esbgk_totals(self._ctx, _dptr(out)), "totals")
+        return out
+
+    def counters(self):
+        u, s, k, b = (ctypes.c_longlong() for _ in range(4))
+        self._check(self._abi.esbgk_counters(self._ctx, ctypes.byref(u), ctypes.byref(s), ctypes.byref(k),
+                                             ctypes.byref(b)), "counters")
+        return dict(kinetic_cell_updates=u.value, steps=s.value, kinetic_cells=k.value, buffer_fills=b.value)
+
+    def timing(self, enable=True):
+        """Bracket every library kernel with CUDA events on the stream."""
+        self._check(self._abi.esbgk_timing(self._ctx, int(bool(enable))), "timing")
+
+    def timing_read(self):
+        """{kernel class: (milliseconds, launches)} since the last read."""
+        n = len(self._abi.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(self._abi.esbgk_timing_read(self._ctx, ms, cnt, n), "timing_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self._abi.KERNEL_CLASSES)}
+
+    def sync(self):
+        self._check(self._abi.esbgk_sync(self._ctx), "sync")
+
+
+def relax_cells(fstar, h, vmax, beta=-0.5, prec="fp64", stream=None):
+    """esbgk_relax_cells on torch device tensors: fstar (n, nv, nv) of the
+    storage dtype of `prec`, h (n,) float64.  Returns (f, G_hat) tensors."""
+    import torch
+    _abi = _lib()
+    n, nv, nv2 = fstar.shape
+    assert nv == nv2 and fstar.is_cuda and fstar.is_contiguous()
+    h = h.to(torch.float64).contiguous()
+    f = torch.empty_like(fstar)
+    g = torch.empty_like(fstar)
+    st = stream if stream is not None else torch.cuda.current_stream(fstar.device)
+    r = _abi.esbgk_relax_cells(ctypes.c_void_p(fstar.data_ptr()), ctypes.cast(h.data_ptr(), _abi.D), n, nv,
+                               float(vmax), float(beta), PREC[prec], ctypes.c_void_p(f.data_ptr()),
+                               ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise Error(r, "esbgk_relax_cells")
+    return f, g

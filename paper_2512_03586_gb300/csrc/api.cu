@@ -1,0 +1,782 @@
+// api.cu -- host runtime behind the C ABI of include/esbgk.h: context,
+// workspace carving, the step driver of Algorithm 1 and the host copies.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "esbgk.h"
+#include "launch.h"
+
+using namespace esbgk;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kVersion = 100;  // 0.1.0
+
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+const Launchers* launchers_for(int prec) {
+  switch (prec) {
+    case ESBGK_FP64: return &kLaunchF64;
+    case ESBGK_FP32: return &kLaunchF32;
+    case ESBGK_BF16: return &kLaunchBF16;
+    default: return nullptr;
+  }
+}
+
+// Byte offsets of every array inside the caller's workspace.
+struct Layout {
+  size_t F[3], ACC[3], Un, Us[2], Phi, eps, lamA, L1, stage5, red, tot;
+  size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr;
+  size_t total;
+};
+
+constexpr int kRedBlocks = 1024;
+
+Layout make_layout(int nc, int nvv, size_t elem) {
+  Layout L{};
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = p;
+    p += up(bytes);
+    return at;
+  };
+  const size_t fsz = (size_t)nc * nvv * elem, dsz = (size_t)nc * sizeof(double);
+  for (int q = 0; q < 3; ++q) L.F[q] = take(fsz);
+  for (int q = 0; q < 3; ++q) L.ACC[q] = take(fsz);
+  L.Un = take(4 * dsz);
+  L.Us[0] = take(4 * dsz);
+  L.Us[1] = take(4 * dsz);
+  L.Phi = take(kMaxStages * 4 * dsz);
+  L.eps = take(dsz);
+  L.lamA = take(dsz);
+  L.L1 = take(dsz);
+  L.stage5 = take(5 * dsz);
+  L.red = take(kRedBlocks * 4 * sizeof(double));
+  L.tot = take(4 * sizeof(double));
+  L.flags = take(nc);
+  L.flags_prev = take(nc);
+  L.cat = take(nc);
+  L.klist = take((size_t)nc * sizeof(int));
+  L.blist = take((size_t)nc * sizeof(int));
+  L.flist = take((size_t)nc * sizeof(int));
+  L.clist = take((size_t)nc * sizeof(int));
+  L.counts = take(4 * sizeof(int));
+  L.err = take(sizeof(DevErr));
+  L.ctr = take(2 * sizeof(long long));
+  L.total = p;
+  return L;
+}
+
+bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params* p) {
+  if (!g || !v || !p) return false;
+  if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > (1LL << 30)) return false;
+  if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return false;
+  if ((g->bc_x != ESBGK_BC_PERIODIC && g->bc_x != ESBGK_BC_OUTFLOW) ||
+      (g->bc_y != ESBGK_BC_PERIODIC && g->bc_y != ESBGK_BC_OUTFLOW))
+    return false;
+  if (v->nv < 2 || v->nv > 64 || !(v->vmax > 0)) return false;
+  if (!(p->beta >= -0.5 && p->beta < 1.0) || !(p->tau > 0) || !(p->cweno_eps > 0)) return false;
+  if (!(p->eta_factor >= 0) || !(p->delta >= 0)) return false;
+  if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN) return false;
+  if (p->coupling != ESBGK_COUPLE_STAGE && p->coupling != ESBGK_COUPLE_STEP) return false;
+  return launchers_for(p->prec) != nullptr;
+}
+
+Geo make_geo(const esbgk_grid* g, const esbgk_vmesh* v) {
+  Geo G{};
+  G.nx = g->nx;
+  G.ny = g->ny;
+  G.nc = g->nx * g->ny;
+  G.nv = v->nv;
+  G.nvv = v->nv * v->nv;
+  G.bcx = g->bc_x;
+  G.bcy = g->bc_y;
+  G.dx = (g->x1 - g->x0) / g->nx;
+  G.dy = (g->y1 - g->y0) / g->ny;
+  G.vmax = v->vmax;
+  G.dv = 2.0 * v->vmax / v->nv;
+  G.w = G.dv * G.dv;
+  return G;
+}
+
+}  // namespace
+
+struct esbgk_ctx {
+  Geo g;
+  Model m;
+  int prec, sw, coupling;
+  const Launchers* L;
+  cudaStream_t stream;
+  int grid_stage, grid_red;
+  unsigned char* ws;
+  void* F[3];
+  void* ACC[3];
+  double *Un, *Us[2], *Phi, *eps, *lamA, *L1, *stage5, *red, *tot;
+  uint8_t *flags, *flags_prev, *cat;
+  int *klist, *blist, *flist, *clist, *counts;
+  DevErr* err;
+  long long* ctr;
+  int cur;
+  bool have_state, conv_pending;
+  long long steps;
+  int status;
+  long long bad_cell;
+  std::string msg;
+  // per-kernel timing (host event objects only)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct Rec {
+    int cat;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  double t_ms[ESBGK_K_COUNT] = {0};
+  long long t_n[ESBGK_K_COUNT] = {0};
+
+  ~esbgk_ctx() {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : ev_free) cudaEventDestroy(e);
+  }
+
+  View view() const {
+    View V{};
+    V.g = g;
+    V.m = m;
+    V.eps = eps;
+    V.flags = flags;
+    V.klist = klist;
+    V.blist = blist;
+    V.flist = flist;
+    V.clist = clist;
+    V.counts = counts;
+    V.err = err;
+    return V;
+  }
+};
+
+namespace {
+
+int fail(esbgk_ctx* X, int code, const std::string& why) {
+  if (X) {
+    X->status = code;
+    X->msg = why;
+  }
+  return code;
+}
+
+int cuda_check(esbgk_ctx* X, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return ESBGK_OK;
+  return fail(X, ESBGK_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int after_launch(esbgk_ctx* X, const char* where) { return cuda_check(X, cudaGetLastError(), where); }
+
+cudaEvent_t take_event(esbgk_ctx* X) {
+  if (!X->ev_free.empty()) {
+    cudaEvent_t e = X->ev_free.back();
+    X->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one kernel launch with events on the context's stream when timing
+// is enabled.
+struct Timed {
+  esbgk_ctx* X;
+  int cat;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(esbgk_ctx* X_, int cat_) : X(X_), cat(cat_) {
+    if (X->timing && (a = take_event(X)) && (b = take_event(X))) cudaEventRecord(a, X->stream);
+  }
+  ~Timed() {
+    if (a && b) {
+      cudaEventRecord(b, X->stream);
+      X->recs.push_back({cat, a, b});
+    } else {
+      if (a) X->ev_free.push_back(a);
+      if (b) X->ev_free.push_back(b);
+    }
+  }
+};
+
+// Wait for the stream, then turn a device error word into a status.
+int sync_and_check(esbgk_ctx* X) {
+  int r = cuda_check(X, cudaStreamSynchronize(X->stream), "cudaStreamSynchronize");
+  if (r) return r;
+  DevErr e{};
+  r = cuda_check(X, cudaMemcpy(&e, X->err, sizeof(e), cudaMemcpyDeviceToHost), "read error word");
+  if (r) return r;
+  if (e.code != 0) {
+    X->bad_cell = e.cell;
+    char buf[160];
+    snprintf(buf, sizeof buf, "non-realizable state (rho, T, det of the temperature tensor or moment system) in cell %lld",
+             (long long)e.cell);
+    return fail(X, ESBGK_E_NONREALIZABLE, buf);
+  }
+  return ESBGK_OK;
+}
+
+int compact(esbgk_ctx* X) {
+  const View V = X->view();
+  {
+    Timed t(X, ESBGK_K_COMPACT);
+    launch_categorize(V, X->flags, X->flags_prev, X->cat, X->stream);
+    launch_compact(X->cat, X->g.nc, X->klist, X->blist, X->flist, X->clist, X->counts, X->stream);
+  }
+  return after_launch(X, "compaction");
+}
+
+int regime_update(esbgk_ctx* X) {
+  const View V = X->view();
+  {
+    Timed t(X, ESBGK_K_L1);
+    X->L->l1(X->F[X->cur], X->L1, V, X->grid_stage, X->stream);
+  }
+  int r = after_launch(X, "l1 kernel");
+  if (r) return r;
+  {
+    Timed t(X, ESBGK_K_FLAGS);
+    launch_flags(V, X->Un, X->L1, X->L1, X->lamA, X->flags, X->stream);
+  }
+  if ((r = after_launch(X, "flags kernel"))) return r;
+  if ((r = compact(X))) return r;
+  X->conv_pending = true;
+  return ESBGK_OK;
+}
+
+double T_(const esbgk_tableau* t, int i, int j) { return t->At[i * 4 + j]; }
+double I_(const esbgk_tableau* t, int i, int j) { return t->A[i * 4 + j]; }
+
+bool valid_tableau(const esbgk_tableau* t) {
+  if (!t || t->s < 2 || t->s > kMaxStages) return false;
+  const int s = t->s;
+  for (int i = 0; i < s; ++i) {
+    if (!std::isfinite(t->bt[i]) || !std::isfinite(t->b[i])) return false;
+    for (int j = 0; j < s; ++j) {
+      if (!std::isfinite(T_(t, i, j)) || !std::isfinite(I_(t, i, j))) return false;
+      if (j >= i && T_(t, i, j) != 0.0) return false;
+      if (j > i && I_(t, i, j) != 0.0) return false;
+    }
+    if (I_(t, i, i) < 0.0) return false;
+  }
+  return true;
+}
+
+// One step of Algorithm 1 with the current regime map.  Stage i (0-based)
+// kernels consume L(f^(i-1)) and fold every explicit and implicit term into
+// running accumulators of the later stages and of the final combination, so
+// that no L_j or Q_j is ever stored: per element and ARS(2,3,3) step this
+// reads f^n, f^(2), D_3, D_fin, f^(3), D_fin' and writes f^(2), D_3, D_fin,
+// f^(3), D_fin', f^{n+1} (12 accesses for 3 transport evaluations).
+int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
+  const int s = T->s;
+  bool shortcut = T->bt[s - 1] == 0.0;
+  for (int j = 0; j < s && shortcut; ++j)
+    shortcut = T->b[j] == I_(T, s - 1, j) && T->bt[j] == T_(T, s - 1, j);
+  auto needQ = [&](int i) {
+    bool q = !shortcut && T->b[i] != 0.0;
+    for (int k = i + 1; k < s; ++k) q = q || I_(T, k, i) != 0.0;
+    return q;
+  };
+  const bool trivial0 = I_(T, 0, 0) == 0.0 && !needQ(0);
+  const int i0 = trivial0 ? 1 : 0;
+  const int ntarget = (s - 1 - i0) + (shortcut ? 0 : 1);
+  if (ntarget > 3) return fail(X, ESBGK_E_ARG, "tableau needs more than 3 running accumulators");
+  auto slot = [&](int k) { return k - (i0 + 1); };  // k == s means the final combination
+  const int slot_fin = s - 1 - i0;
+
+  const View V = X->view();
+  int other[2], n = 0;
+  for (int q = 0; q < 3; ++q)
+    if (q != X->cur) other[n++] = q;
+  void* Fc = X->F[X->cur];
+
+  // start of step: coupling into f^n (buffer cells, converted cells), U^(0)
+  PrepArgs P{};
+  P.f = Fc;
+  P.U = X->Un;
+  P.list1 = X->blist;
+  P.count1 = X->counts + 1;
+  P.list2 = X->conv_pending ? X->clist : nullptr;
+  P.count2 = X->conv_pending ? X->counts + 3 : nullptr;
+  P.copy_to = trivial0 ? X->Us[0] : nullptr;
+  P.flags_prev = X->flags_prev;
+  if (!trivial0) {
+    // flags_prev still has to be refreshed: reuse the copy path into Us[1]
+    P.copy_to = X->Us[1];
+  }
+  {
+    Timed t(X, ESBGK_K_PREP);
+    X->L->prep(P, V, X->grid_stage, X->stream);
+  }
+  int r = after_launch(X, "prep kernel");
+  if (r) return r;
+  X->conv_pending = false;
+
+  int prev_buf = X->cur;
+  for (int i = i0; i < s; ++i) {
+    const bool first = i == i0, last = i == s - 1;
+    StageArgs A{};
+    A.f_src = i == 0 ? nullptr : X->F[prev_buf];
+    A.star_base = first ? Fc : X->ACC[slot(i)];
+    A.star_cL = i == 0 ? 0.0 : -dt * T_(T, i, i - 1);
+    A.h_coef = dt * I_(T, i, i);
+    A.need_q = needQ(i) ? 1 : 0;
+    const int outbuf = other[(i - i0) & 1];
+    A.f_out = X->F[outbuf];
+    int na = 0;
+    for (int k = i + 1; k <= s; ++k) {
+      if (k == s && shortcut) break;
+      const int sl = k == s ? slot_fin : slot(k);
+      const double tl = k == s ? T->bt[i - (i > 0)] : T_(T, k, i > 0 ? i - 1 : 0);
+      A.acc_cL[na] = i == 0 ? 0.0 : -dt * tl;
+      A.acc_cQ[na] = dt * (k == s ? T->b[i] : I_(T, k, i));
+      A.acc_in[na] = first ? Fc : X->ACC[sl];
+      A.acc_out[na] = X->ACC[sl];
+      ++na;
+    }
+    A.nacc = na;
+    A.Un = X->Un;
+    A.U_prev = i == 0 ? X->Un : X->Us[(i - 1) & 1];
+    A.U_out = (last && shortcut) ? X->Un : X->Us[i & 1];
+    A.Phi = X->Phi;
+    A.phi_store = i == 0 ? -1 : i - 1;
+    A.nphi = i;
+    for (int j = 0; j < i; ++j) A.phi_coef[j] = dt * T_(T, i, j);
+    A.hoc = X->coupling == ESBGK_COUPLE_STAGE ? 1 : 0;
+    A.fill = (last && shortcut) ? 0 : 1;
+    A.kin_u_moments = (A.hoc || (last && shortcut)) ? 1 : 0;
+    A.ctr = X->ctr;
+    {
+      Timed t(X, ESBGK_K_STAGE);
+      X->L->stage(A, V, X->grid_stage, X->stream);
+    }
+    if ((r = after_launch(X, "stage kernel"))) return r;
+    prev_buf = outbuf;
+  }
+  if (!shortcut) {
+    StageArgs A{};
+    A.f_src = X->F[prev_buf];
+    A.star_base = X->ACC[slot_fin];
+    A.star_cL = -dt * T->bt[s - 1];
+    A.h_coef = 0.0;
+    A.need_q = 0;
+    A.f_out = Fc;
+    A.nacc = 0;
+    A.Un = X->Un;
+    A.U_prev = X->Us[(s - 1) & 1];
+    A.U_out = X->Un;
+    A.Phi = X->Phi;
+    A.phi_store = s - 1;
+    A.nphi = s;
+    for (int j = 0; j < s; ++j) A.phi_coef[j] = dt * T->bt[j];
+    A.hoc = 1;
+    A.fill = 0;
+    A.kin_u_moments = 1;
+    A.ctr = X->ctr;
+    {
+      Timed t(X, ESBGK_K_FINAL);
+      X->L->stage(A, V, X->grid_stage, X->stream);
+    }
+    if ((r = after_launch(X, "final kernel"))) return r;
+  } else {
+    X->cur = prev_buf;
+  }
+  X->steps += 1;
+  return ESBGK_OK;
+}
+
+template <typename S>
+void to_storage(const double* in, S* out, size_t n);
+template <>
+void to_storage<double>(const double* in, double* out, size_t n) {
+  memcpy(out, in, n * sizeof(double));
+}
+template <>
+void to_storage<float>(const double* in, float* out, size_t n) {
+  for (size_t q = 0; q < n; ++q) out[q] = (float)in[q];
+}
+template <>
+void to_storage<__nv_bfloat16>(const double* in, __nv_bfloat16* out, size_t n) {
+  for (size_t q = 0; q < n; ++q) out[q] = __float2bfloat16_rn((float)in[q]);
+}
+template <typename S>
+void from_storage(const S* in, double* out, size_t n);
+template <>
+void from_storage<double>(const double* in, double* out, size_t n) {
+  memcpy(out, in, n * sizeof(double));
+}
+template <>
+void from_storage<float>(const float* in, double* out, size_t n) {
+  for (size_t q = 0; q < n; ++q) out[q] = in[q];
+}
+template <>
+void from_storage<__nv_bfloat16>(const __nv_bfloat16* in, double* out, size_t n) {
+  for (size_t q = 0; q < n; ++q) out[q] = __bfloat162float(in[q]);
+}
+
+#define GUARD(X)                                         \
+  do {                                                   \
+    if (!(X)) return ESBGK_E_ARG;                        \
+    if ((X)->status) return (X)->status;                 \
+  } while (0)
+#define NEED_STATE(X)                                                        \
+  do {                                                                       \
+    if (!(X)->have_state) return fail((X), ESBGK_E_STATE, "no state set"); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int esbgk_version(void) { return kVersion; }
+
+size_t esbgk_workspace_bytes(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_params* params) {
+  if (!valid_inputs(grid, vmesh, params)) return 0;
+  return make_layout(grid->nx * grid->ny, vmesh->nv * vmesh->nv, launchers_for(params->prec)->elem).total;
+}
+
+int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_params* params, void* workspace,
+                 size_t workspace_bytes, void* stream, esbgk_ctx** out) {
+  if (!out) return ESBGK_E_ARG;
+  *out = nullptr;
+  if (!valid_inputs(grid, vmesh, params) || !workspace) return ESBGK_E_ARG;
+  const Launchers* L = launchers_for(params->prec);
+  const Geo g = make_geo(grid, vmesh);
+  const Layout lay = make_layout(g.nc, g.nvv, L->elem);
+  if (workspace_bytes < lay.total || ((uintptr_t)workspace % kAlign) != 0) return ESBGK_E_WORKSPACE;
+  esbgk_ctx* X = new (std::nothrow) esbgk_ctx();
+  if (!X) return ESBGK_E_ARG;
+  X->g = g;
+  X->m.beta = params->beta;
+  X->m.tau = params->tau;
+  X->m.eps_w = params->cweno_eps;
+  X->m.eta_factor = params->eta_factor;
+  X->m.delta = params->delta;
+  X->prec = params->prec;
+  X->sw = params->sw;
+  X->coupling = params->coupling;
+  X->L = L;
+  X->stream = (cudaStream_t)stream;
+  unsigned char* w = (unsigned char*)workspace;
+  X->ws = w;
+  for (int q = 0; q < 3; ++q) {
+    X->F[q] = w + lay.F[q];
+    X->ACC[q] = w + lay.ACC[q];
+  }
+  X->Un = (double*)(w + lay.Un);
+  X->Us[0] = (double*)(w + lay.Us[0]);
+  X->Us[1] = (double*)(w + lay.Us[1]);
+  X->Phi = (double*)(w + lay.Phi);
+  X->eps = (double*)(w + lay.eps);
+  X->lamA = (double*)(w + lay.lamA);
+  X->L1 = (double*)(w + lay.L1);
+  X->stage5 = (double*)(w + lay.stage5);
+  X->red = (double*)(w + lay.red);
+  X->tot = (double*)(w + lay.tot);
+  X->flags = w + lay.flags;
+  X->flags_prev = w + lay.flags_prev;
+  X->cat = w + lay.cat;
+  X->klist = (int*)(w + lay.klist);
+  X->blist = (int*)(w + lay.blist);
+  X->flist = (int*)(w + lay.flist);
+  X->clist = (int*)(w + lay.clist);
+  X->counts = (int*)(w + lay.counts);
+  X->err = (DevErr*)(w + lay.err);
+  X->ctr = (long long*)(w + lay.ctr);
+  X->cur = 0;
+  X->bad_cell = -1;
+  int dev = 0, nsm = 0;
+  int r = cuda_check(X, cudaGetDevice(&dev), "cudaGetDevice");
+  if (!r) r = cuda_check(X, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  if (!r) r = cuda_check(X, L->setup(g), "kernel attributes");
+  if (r) {
+    delete X;
+    return r;
+  }
+  X->grid_stage = nsm * L->blocks_per_sm(g);
+  X->grid_red = nsm < kRedBlocks ? nsm : kRedBlocks;
+  r = cuda_check(X, cudaMemsetAsync(X->err, 0, sizeof(DevErr), X->stream), "clear error word");
+  if (!r) r = cuda_check(X, cudaMemsetAsync(X->ctr, 0, 2 * sizeof(long long), X->stream), "clear counters");
+  if (!r) r = cuda_check(X, cudaMemsetAsync(X->Phi, 0, lay.stage5 - lay.Phi, X->stream), "clear arrays");
+  // f of cells that are never kinetic is never written: start it at zero
+  if (!r) r = cuda_check(X, cudaMemsetAsync(w + lay.F[0], 0, lay.Un - lay.F[0], X->stream), "clear f arrays");
+  if (r) {
+    delete X;
+    return r;
+  }
+  *out = X;
+  return ESBGK_OK;
+}
+
+void esbgk_destroy(esbgk_ctx* ctx) { delete ctx; }
+
+int esbgk_set_state(esbgk_ctx* X, const double* rho, const double* ux, const double* uy, const double* T,
+                    const double* eps, const uint8_t* kinetic) {
+  if (!X || !rho || !ux || !uy || !T || !eps) return ESBGK_E_ARG;
+  const int nc = X->g.nc;
+  for (int c = 0; c < nc; ++c) {
+    if (!(rho[c] > 0) || !(T[c] > 0) || !(eps[c] >= 0) || !std::isfinite(ux[c]) || !std::isfinite(uy[c]) ||
+        !std::isfinite(rho[c]) || !std::isfinite(T[c]) || !std::isfinite(eps[c]))
+      return fail(X, ESBGK_E_ARG, "set_state: need rho > 0, T > 0, eps >= 0, finite values");
+  }
+  X->status = ESBGK_OK;
+  X->msg.clear();
+  X->bad_cell = -1;
+  const double* src[5] = {rho, ux, uy, T, eps};
+  int r = ESBGK_OK;
+  for (int q = 0; q < 5 && !r; ++q)
+    r = cuda_check(X, cudaMemcpyAsync(X->stage5 + (size_t)q * nc, src[q], nc * sizeof(double), cudaMemcpyHostToDevice,
+                                      X->stream),
+                   "set_state copy");
+  if (!r && kinetic)
+    r = cuda_check(X, cudaMemcpyAsync(X->cat, kinetic, nc, cudaMemcpyHostToDevice, X->stream), "flags copy");
+  if (!r) r = cuda_check(X, cudaMemsetAsync(X->err, 0, sizeof(DevErr), X->stream), "clear error word");
+  if (r) return r;
+  launch_init_state(X->stage5, kinetic ? X->cat : nullptr, X->Un, X->eps, X->flags, X->flags_prev, nc, X->stream);
+  if ((r = after_launch(X, "init kernel"))) return r;
+  if ((r = compact(X))) return r;
+  // f = M_hat[U] in kinetic cells
+  PrepArgs P{};
+  P.f = X->F[X->cur];
+  P.U = X->Un;
+  P.list1 = X->klist;
+  P.count1 = X->counts;
+  X->L->prep(P, X->view(), X->grid_stage, X->stream);
+  if ((r = after_launch(X, "initial Maxwellian"))) return r;
+  X->have_state = true;
+  X->conv_pending = false;
+  return ESBGK_OK;
+}
+
+int esbgk_set_f(esbgk_ctx* X, const double* f) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!f) return ESBGK_E_ARG;
+  const size_t n = (size_t)X->g.nc * X->g.nvv;
+  std::vector<unsigned char> buf(n * X->L->elem);
+  switch (X->prec) {
+    case ESBGK_FP64: to_storage<double>(f, (double*)buf.data(), n); break;
+    case ESBGK_FP32: to_storage<float>(f, (float*)buf.data(), n); break;
+    default: to_storage<__nv_bfloat16>(f, (__nv_bfloat16*)buf.data(), n); break;
+  }
+  int r = cuda_check(X, cudaMemcpyAsync(X->F[X->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, X->stream),
+                     "set_f copy");
+  if (r) return r;
+  X->L->moments(X->F[X->cur], X->Un, X->view(), X->grid_stage, X->stream);
+  if ((r = after_launch(X, "moments kernel"))) return r;
+  return cuda_check(X, cudaStreamSynchronize(X->stream), "set_f sync");
+}
+
+int esbgk_get_f(esbgk_ctx* X, double* f) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!f) return ESBGK_E_ARG;
+  const size_t n = (size_t)X->g.nc * X->g.nvv;
+  std::vector<unsigned char> buf(n * X->L->elem);
+  int r = cuda_check(X, cudaMemcpyAsync(buf.data(), X->F[X->cur], buf.size(), cudaMemcpyDeviceToHost, X->stream),
+                     "get_f copy");
+  if (!r) r = sync_and_check(X);
+  if (r) return r;
+  switch (X->prec) {
+    case ESBGK_FP64: from_storage<double>((double*)buf.data(), f, n); break;
+    case ESBGK_FP32: from_storage<float>((float*)buf.data(), f, n); break;
+    default: from_storage<__nv_bfloat16>((__nv_bfloat16*)buf.data(), f, n); break;
+  }
+  return ESBGK_OK;
+}
+
+int esbgk_regime_update(esbgk_ctx* X) {
+  GUARD(X);
+  NEED_STATE(X);
+  return regime_update(X);
+}
+
+int esbgk_set_flags(esbgk_ctx* X, const uint8_t* kinetic) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!kinetic) return ESBGK_E_ARG;
+  std::vector<uint8_t> k(X->g.nc);
+  for (int c = 0; c < X->g.nc; ++c) k[c] = kinetic[c] ? 1 : 0;
+  int r = cuda_check(X, cudaMemcpyAsync(X->flags, k.data(), k.size(), cudaMemcpyHostToDevice, X->stream),
+                     "set_flags copy");
+  if (!r) r = compact(X);
+  if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_flags sync");
+  if (!r) X->conv_pending = true;
+  return r;
+}
+
+int esbgk_get_flags(esbgk_ctx* X, uint8_t* kinetic) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!kinetic) return ESBGK_E_ARG;
+  int r = cuda_check(X, cudaMemcpyAsync(kinetic, X->flags, X->g.nc, cudaMemcpyDeviceToHost, X->stream), "get_flags");
+  return r ? r : sync_and_check(X);
+}
+
+int esbgk_get_indicators(esbgk_ctx* X, double* lamA, double* L1) {
+  GUARD(X);
+  NEED_STATE(X);
+  const size_t b = (size_t)X->g.nc * sizeof(double);
+  int r = ESBGK_OK;
+  if (lamA) r = cuda_check(X, cudaMemcpyAsync(lamA, X->lamA, b, cudaMemcpyDeviceToHost, X->stream), "lamA copy");
+  if (!r && L1) r = cuda_check(X, cudaMemcpyAsync(L1, X->L1, b, cudaMemcpyDeviceToHost, X->stream), "L1 copy");
+  return r ? r : sync_and_check(X);
+}
+
+int esbgk_advance(esbgk_ctx* X, double dt, const esbgk_tableau* tab) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!(dt > 0) || !std::isfinite(dt) || !valid_tableau(tab)) return fail(X, ESBGK_E_ARG, "advance: bad dt or tableau");
+  return advance(X, dt, tab);
+}
+
+int esbgk_step(esbgk_ctx* X, double dt, const esbgk_tableau* tab) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!(dt > 0) || !std::isfinite(dt) || !valid_tableau(tab)) return fail(X, ESBGK_E_ARG, "step: bad dt or tableau");
+  if (X->sw == ESBGK_SWITCH_PLAIN) {
+    const int r = regime_update(X);
+    if (r) return r;
+  }
+  return advance(X, dt, tab);
+}
+
+int esbgk_get_moments(esbgk_ctx* X, double* rho, double* ux, double* uy, double* T) {
+  GUARD(X);
+  NEED_STATE(X);
+  const int nc = X->g.nc;
+  launch_prim(X->Un, X->stage5, nc, X->stream);
+  int r = after_launch(X, "prim kernel");
+  double* dst[4] = {rho, ux, uy, T};
+  for (int q = 0; q < 4 && !r; ++q)
+    if (dst[q])
+      r = cuda_check(X, cudaMemcpyAsync(dst[q], X->stage5 + (size_t)q * nc, nc * sizeof(double), cudaMemcpyDeviceToHost,
+                                        X->stream),
+                     "get_moments copy");
+  return r ? r : sync_and_check(X);
+}
+
+int esbgk_get_cons(esbgk_ctx* X, double* U) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!U) return ESBGK_E_ARG;
+  int r = cuda_check(X, cudaMemcpyAsync(U, X->Un, 4 * (size_t)X->g.nc * sizeof(double), cudaMemcpyDeviceToHost,
+                                        X->stream),
+                     "get_cons copy");
+  return r ? r : sync_and_check(X);
+}
+
+int esbgk_totals(esbgk_ctx* X, double out[4]) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!out) return ESBGK_E_ARG;
+  launch_totals(X->Un, X->g.nc, X->red, X->tot, X->g.dx * X->g.dy, X->grid_red, X->stream);
+  int r = after_launch(X, "totals kernels");
+  if (!r) r = cuda_check(X, cudaMemcpyAsync(out, X->tot, 4 * sizeof(double), cudaMemcpyDeviceToHost, X->stream),
+                         "totals copy");
+  return r ? r : sync_and_check(X);
+}
+
+int esbgk_counters(esbgk_ctx* X, long long* updates, long long* steps, long long* kinetic_cells,
+                   long long* buffer_fills) {
+  GUARD(X);
+  long long c[2] = {0, 0};
+  int k[4] = {0, 0, 0, 0};
+  int r = cuda_check(X, cudaMemcpyAsync(c, X->ctr, sizeof c, cudaMemcpyDeviceToHost, X->stream), "counter copy");
+  if (!r) r = cuda_check(X, cudaMemcpyAsync(k, X->counts, sizeof k, cudaMemcpyDeviceToHost, X->stream), "counts copy");
+  if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "counters sync");
+  if (r) return r;
+  if (updates) *updates = c[0];
+  if (steps) *steps = X->steps;
+  if (kinetic_cells) *kinetic_cells = k[0];
+  if (buffer_fills) *buffer_fills = c[1];
+  return ESBGK_OK;
+}
+
+int esbgk_timing(esbgk_ctx* X, int enable) {
+  GUARD(X);
+  X->timing = enable != 0;
+  return ESBGK_OK;
+}
+
+int esbgk_timing_read(esbgk_ctx* X, double* ms, long long* launches, int32_t n) {
+  GUARD(X);
+  int r = cuda_check(X, cudaStreamSynchronize(X->stream), "timing sync");
+  if (r) return r;
+  for (auto& q : X->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
+      X->t_ms[q.cat] += t;
+      X->t_n[q.cat] += 1;
+    }
+    X->ev_free.push_back(q.a);
+    X->ev_free.push_back(q.b);
+  }
+  X->recs.clear();
+  for (int q = 0; q < ESBGK_K_COUNT && q < n; ++q) {
+    if (ms) ms[q] = X->t_ms[q];
+    if (launches) launches[q] = X->t_n[q];
+  }
+  for (int q = 0; q < ESBGK_K_COUNT; ++q) {
+    X->t_ms[q] = 0;
+    X->t_n[q] = 0;
+  }
+  return ESBGK_OK;
+}
+
+int esbgk_sync(esbgk_ctx* X) {
+  GUARD(X);
+  return sync_and_check(X);
+}
+
+int esbgk_last_error(esbgk_ctx* X, char* buf, size_t n, long long* bad_cell) {
+  if (!X) return ESBGK_E_ARG;
+  if (buf && n) {
+    strncpy(buf, X->msg.c_str(), n - 1);
+    buf[n - 1] = 0;
+  }
+  if (bad_cell) *bad_cell = X->status == ESBGK_E_NONREALIZABLE ? X->bad_cell : -1;
+  return X->status;
+}
+
+int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax, double beta,
+                      int32_t prec, void* f_out, void* g_out, void* stream) {
+  const Launchers* L = launchers_for(prec);
+  if (!L || !fstar || !h || !f_out || !g_out || n < 0 || nv < 2 || nv > 64 || !(vmax > 0) ||
+      !(beta >= -0.5 && beta < 1.0))
+    return ESBGK_E_ARG;
+  if (n == 0) return ESBGK_OK;
+  Geo g{};
+  g.nx = n;
+  g.ny = 1;
+  g.nc = n;
+  g.nv = nv;
+  g.nvv = nv * nv;
+  g.vmax = vmax;
+  g.dv = 2.0 * vmax / nv;
+  g.w = g.dv * g.dv;
+  g.dx = g.dy = 1.0;
+  if (L->setup(g) != cudaSuccess) return ESBGK_E_CUDA;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return ESBGK_E_CUDA;
+  const int grid = n < nsm * 8 ? n : nsm * 8;
+  L->relax_cells(fstar, h, n, g, beta, f_out, g_out, grid, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? ESBGK_OK : ESBGK_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// common.cuh -- shared device definitions of the ES-BGK library (sm_103a).
+//
+// Layouts (device, all inside the caller's workspace):
+//   f  : storage type S, [cell c = j*nx + i][vy][vx]  -- velocity-contiguous,
+//        one cell's N_v^2 values are one coalesced run.
+//   U  : float64 [4][nc]  (rho, rho u_x, rho u_y, E), structure of arrays.
+//   Phi: float64 [stage][4][nc], the Euler divergences of earlier stages.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define ESBGK_DEV __device__ __forceinline__
+
+namespace esbgk {
+
+constexpr int kThreads = 256;            // threads of every per-cell CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxStages = 4;
+constexpr double kPi = 3.14159265358979323846;
+
+// Geometry of one problem (Sec. 3.2).
+struct Geo {
+  int nx, ny, nc;      // cells per axis, cells
+  int nv, nvv;         // velocity nodes per axis, nv*nv
+  int bcx, bcy;        // 0 periodic, 1 outflow
+  double dx, dy;       // cell sizes
+  double vmax, dv, w;  // velocity bound, step, quadrature weight dv^2
+};
+
+// Model constants (Sec. 2, 3.1).
+struct Model {
+  double beta, tau, eps_w, eta_factor, delta;
+};
+
+// Device error word: first error wins.
+struct DevErr {
+  int code;
+  int pad;
+  long long cell;
+};
+
+enum : int { kErrNone = 0, kErrNonRealizable = 1 };
+
+ESBGK_DEV void report_error(DevErr* e, int code, long long cell) {
+  if (e && atomicCAS(&e->code, 0, code) == 0) e->cell = cell;
+}
+
+// Storage <-> arithmetic type mapping.
+template <typename S> struct Real;
+template <> struct Real<double> { using T = double; };
+template <> struct Real<float> { using T = float; };
+template <> struct Real<__nv_bfloat16> { using T = float; };
+
+ESBGK_DEV double ld(const double* p) { return __ldg(p); }
+ESBGK_DEV float ld(const float* p) { return __ldg(p); }
+ESBGK_DEV float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+ESBGK_DEV void st(double* p, double v) { *p = v; }
+ESBGK_DEV void st(float* p, float v) { *p = v; }
+ESBGK_DEV void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// plain (coherent) loads for arrays written earlier in the same kernel by the
+// same thread (accumulators updated in place)
+ESBGK_DEV double ldc(const double* p) { return *p; }
+ESBGK_DEV float ldc(const float* p) { return *p; }
+ESBGK_DEV float ldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+ESBGK_DEV double fdiv(double a, double b) { return a / b; }
+ESBGK_DEV float fdiv(float a, float b) { return __fdividef(a, b); }
+
+// 2^x.  FP32: the hardware approximation (ex2.approx, max rel. error ~2^-22).
+ESBGK_DEV float exp2r(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+ESBGK_DEV double exp2r(double x) { return exp2(x); }
+
+// Index of cell i + d along an axis of n cells under boundary condition bc
+// (0 periodic, 1 outflow: ghost cells copy the edge cell).
+ESBGK_DEV int nb(int i, int n, int bc) {
+  if (bc == 0) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// CWENO3 (Levy-Puppo-Russo) value at the face of the middle cell that faces
+// `c`, from cell averages a | b | c.  P_L, P_R are the one-sided lines,
+// P_0 = (P_opt - P_L/4 - P_R/4)/(1/2); the face value of
+// sum_k alpha_k P_k / sum_k alpha_k with alpha_k = d_k/(eps + IS_k)^2 is
+// evaluated with a single division by multiplying every alpha through by
+// (eps+IS_0)^2 (eps+IS_L)^2 (eps+IS_R)^2.
+template <typename R>
+ESBGK_DEV R cweno_face(R a, R b, R c, R epsw) {
+  const R dl = b - a, dr = c - b, d1 = c - a;
+  const R D = dr - dl;
+  const R PL = b + R(0.5) * dl;
+  const R PR = b + R(0.5) * dr;
+  const R P0 = b + D * R(1.0 / 6.0) + R(0.25) * d1;
+  const R IS0 = R(13.0 / 3.0) * D * D + R(0.25) * d1 * d1;
+  R sL = epsw + dl * dl;
+  sL *= sL;
+  R sR = epsw + dr * dr;
+  sR *= sR;
+  R s0 = epsw + IS0;
+  s0 *= s0;
+  const R a0 = R(0.5) * sL * sR;
+  const R aL = R(0.25) * s0 * sR;
+  const R aR = R(0.25) * s0 * sL;
+  return fdiv(a0 * P0 + aL * PL + aR * PR, a0 + aL + aR);
+}
+
+template <typename R>
+ESBGK_DEV R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of N per-thread values (kThreads threads).  Result lands in
+// out[0..N) (shared memory, float64) after the call; red is shared scratch of
+// kWarps*N doubles.  Warp sums run in the arithmetic type R, the cross-warp
+// sum in float64.
+template <int N, typename R>
+ESBGK_DEV void block_sum(R (&v)[N], double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    R s = warp_sum(v[n]);
+    if (lane == 0) red[warp * N + n] = (double)s;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < N) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += red[w * N + lane];
+    out[lane] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace esbgk

@@ -1,0 +1,223 @@
+// kernels_common.cu -- precision-independent kernels: state set-up, regime
+// criteria, compaction of the regime map, macroscopic read-out and totals.
+#include "launch.h"
+
+namespace esbgk {
+
+// U = (rho, rho u, 1/2 rho |u|^2 + rho T) from (rho, u, T) (Sec. 2, d_v = 2).
+__global__ void init_state_kernel(const double* __restrict__ prim, const uint8_t* __restrict__ kin_in,
+                                  double* Un, double* eps, uint8_t* flags, uint8_t* flags_prev, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double rho = prim[c], ux = prim[nc + c], uy = prim[2 * (size_t)nc + c], T = prim[3 * (size_t)nc + c];
+  Un[c] = rho;
+  Un[nc + c] = rho * ux;
+  Un[2 * (size_t)nc + c] = rho * uy;
+  Un[3 * (size_t)nc + c] = 0.5 * rho * (ux * ux + uy * uy) + rho * T;
+  eps[c] = prim[4 * (size_t)nc + c];
+  const uint8_t k = kin_in ? (kin_in[c] ? 1 : 0) : 1;
+  flags[c] = k;
+  flags_prev[c] = k;
+}
+
+void launch_init_state(const double* prim, const uint8_t* kin_in, double* Un, double* eps, uint8_t* flags,
+                       uint8_t* flags_prev, int nc, cudaStream_t s) {
+  init_state_kernel<<<(nc + 255) / 256, 256, 0, s>>>(prim, kin_in, Un, eps, flags, flags_prev, nc);
+}
+
+// Regime criteria of Sec. 3.1.2 for one cell.  X = I - S_1 with
+//   S_1 = I - eps D(u) mu/(rho T) - 2/3 (eps kappa/(rho T^{3/2}))^2 grad T grad T^T,
+//   mu/(rho T) = 1/(tau (1-beta)),  kappa/(rho T^{3/2}) = 5/2 /(tau sqrt T),
+//   D = grad u + grad u^T - 2/3 div u I;
+// lambda_A = max |eig X| = |tr X|/2 + sqrt(((X_xx - X_yy)/2)^2 + X_xy^2).
+// Gradients: central differences of cell-centre u and T, ghost cells by BC.
+// New flag (Eqs. crit:CompEuler, eqKintoFluid1):
+//   lambda_A > eta   or   (kinetic and ||f - M||_1 > delta).
+__global__ void flags_kernel(View V, const double* __restrict__ Un, const double* __restrict__ L1in,
+                             double* L1out, double* lamA, uint8_t* flags_out) {
+  const Geo& g = V.g;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nc) return;
+  const int i = c % g.nx, j = c / g.nx;
+  const size_t nc = g.nc;
+  auto prim = [&](int cc, double& ux, double& uy, double& T) {
+    const double rho = Un[cc], mx = Un[nc + cc], my = Un[2 * nc + cc], E = Un[3 * nc + cc];
+    ux = mx / rho;
+    uy = my / rho;
+    T = (E - 0.5 * rho * (ux * ux + uy * uy)) / rho;
+  };
+  double uxE, uyE, TE, uxW, uyW, TW, uxN, uyN, TN, uxS, uyS, TS, ux0, uy0, T0;
+  prim(j * g.nx + nb(i + 1, g.nx, g.bcx), uxE, uyE, TE);
+  prim(j * g.nx + nb(i - 1, g.nx, g.bcx), uxW, uyW, TW);
+  prim(nb(j + 1, g.ny, g.bcy) * g.nx + i, uxN, uyN, TN);
+  prim(nb(j - 1, g.ny, g.bcy) * g.nx + i, uxS, uyS, TS);
+  prim(c, ux0, uy0, T0);
+  const double i2dx = 0.5 / g.dx, i2dy = 0.5 / g.dy;
+  const double dudx = (uxE - uxW) * i2dx, dudy = (uxN - uxS) * i2dy;
+  const double dvdx = (uyE - uyW) * i2dx, dvdy = (uyN - uyS) * i2dy;
+  const double dTdx = (TE - TW) * i2dx, dTdy = (TN - TS) * i2dy;
+  const double div = dudx + dvdy;
+  const double Dxx = 2.0 * dudx - (2.0 / 3.0) * div;
+  const double Dyy = 2.0 * dvdy - (2.0 / 3.0) * div;
+  const double Dxy = dudy + dvdx;
+  const double eps = V.eps[c];
+  const double c1 = eps / (V.m.tau * (1.0 - V.m.beta));
+  const double kk = 2.5 * eps / (V.m.tau * sqrt(T0));
+  const double c2 = (2.0 / 3.0) * kk * kk;
+  const double Xxx = c1 * Dxx + c2 * dTdx * dTdx;
+  const double Xxy = c1 * Dxy + c2 * dTdx * dTdy;
+  const double Xyy = c1 * Dyy + c2 * dTdy * dTdy;
+  const double mean = 0.5 * (Xxx + Xyy), half = 0.5 * (Xxx - Xyy);
+  const double lam = fabs(mean) + sqrt(half * half + Xxy * Xxy);
+  const uint8_t kin = V.flags[c];
+  const double l1 = kin ? L1in[c] : 0.0;
+  lamA[c] = lam;
+  L1out[c] = l1;
+  flags_out[c] = (lam > V.m.eta_factor * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
+}
+
+void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
+                  uint8_t* flags_out, cudaStream_t s) {
+  flags_kernel<<<(V.g.nc + 255) / 256, 256, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+}
+
+// Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
+// cross stencil of a kinetic cell, Remark rem_coupling), 2 other fluid; bit 2
+// (value 4) marks a kinetic cell that was fluid in the previous step.
+__global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
+                                  uint8_t* cat) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nc) return;
+  if (flags[c]) {
+    cat[c] = prev[c] ? 0 : 4;
+    return;
+  }
+  const int i = c % g.nx, j = c / g.nx;
+  bool hit = false;
+  const int d[4] = {-2, -1, 1, 2};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hit |= flags[j * g.nx + nb(i + d[q], g.nx, g.bcx)] != 0;
+    hit |= flags[nb(j + d[q], g.ny, g.bcy) * g.nx + i] != 0;
+  }
+  cat[c] = hit ? 1 : 2;
+}
+
+void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
+                       cudaStream_t s) {
+  categorize_kernel<<<(V.g.nc + 255) / 256, 256, 0, s>>>(V.g, flags, flags_prev, cat);
+}
+
+// Deterministic stream compaction of the categories into the lists of
+// kinetic, buffer, fluid and converted cells (ascending cell order), one CTA.
+constexpr int kScanThreads = 1024;
+
+__device__ int block_exclusive_scan(int v, int* sm, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kScanThreads / 32 ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sm[32 + lane] = w;
+  }
+  __syncthreads();
+  total = sm[32 + 31];
+  const int before = warp > 0 ? sm[32 + warp - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint8_t* __restrict__ cat, int nc, int* klist,
+                                                               int* blist, int* flist, int* clist, int* counts) {
+  __shared__ int sm[64];
+  const int chunk = (nc + kScanThreads - 1) / kScanThreads;
+  const int lo = threadIdx.x * chunk;
+  const int hi = min(nc, lo + chunk);
+  int n[4] = {0, 0, 0, 0};
+  for (int c = lo; c < hi; ++c) {
+    const int t = cat[c];
+    n[0] += (t & 3) == 0;
+    n[1] += t == 1;
+    n[2] += t == 2;
+    n[3] += t == 4;
+  }
+  int off[4], tot[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) off[q] = block_exclusive_scan(n[q], sm, tot[q]);
+  for (int c = lo; c < hi; ++c) {
+    const int t = cat[c];
+    if ((t & 3) == 0) klist[off[0]++] = c;
+    if (t == 1) blist[off[1]++] = c;
+    if (t == 2) flist[off[2]++] = c;
+    if (t == 4) clist[off[3]++] = c;
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) counts[q] = tot[q];
+  }
+}
+
+void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* flist, int* clist, int* counts,
+                    cudaStream_t s) {
+  compact_kernel<<<1, kScanThreads, 0, s>>>(cat, nc, klist, blist, flist, clist, counts);
+}
+
+// (rho, u_x, u_y, T) from U.
+__global__ void prim_kernel(const double* __restrict__ Un, double* out, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double rho = Un[c], ux = Un[nc + c] / rho, uy = Un[2 * (size_t)nc + c] / rho;
+  out[c] = rho;
+  out[nc + c] = ux;
+  out[2 * (size_t)nc + c] = uy;
+  out[3 * (size_t)nc + c] = (Un[3 * (size_t)nc + c] - 0.5 * rho * (ux * ux + uy * uy)) / rho;
+}
+
+void launch_prim(const double* Un, double* out, int nc, cudaStream_t s) {
+  prim_kernel<<<(nc + 255) / 256, 256, 0, s>>>(Un, out, nc);
+}
+
+// Global totals: fixed-order two-level sum of U over cells, times dx dy.
+__global__ void totals_partial_kernel(const double* __restrict__ Un, int nc, double* partial) {
+  __shared__ double red[4][256];
+  double s[4] = {0, 0, 0, 0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += Un[(size_t)q * nc + c];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) partial[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void totals_final_kernel(const double* __restrict__ partial, int nb, double* out, double dxdy) {
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[b * 4 + threadIdx.x];
+    out[threadIdx.x] = s * dxdy;
+  }
+}
+
+void launch_totals(const double* Un, int nc, double* partial, double* out, double dxdy, int grid, cudaStream_t s) {
+  totals_partial_kernel<<<grid, 256, 0, s>>>(Un, nc, partial);
+  totals_final_kernel<<<1, 32, 0, s>>>(partial, grid, out, dxdy);
+}
+
+}  // namespace esbgk

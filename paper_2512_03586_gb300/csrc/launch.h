@@ -1,0 +1,104 @@
+// launch.h -- argument blocks shared by the host runtime and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace esbgk {
+
+// Read-mostly view of a problem's device state.
+struct View {
+  Geo g;
+  Model m;
+  const double* eps;       // [nc] Knudsen number
+  const uint8_t* flags;    // [nc] 1 = kinetic
+  const int* klist;        // kinetic cells
+  const int* blist;        // buffer cells (fluid, inside a kinetic stencil)
+  const int* flist;        // other fluid cells
+  const int* clist;        // cells that turned kinetic since the last step
+  const int* counts;       // [4] nK, nB, nF, nC
+  DevErr* err;
+};
+
+// One stage (or the final combination) of the IMEX step; see the stage
+// kernel.  For kinetic cells:
+//   L     = L(f_src)                              (none when f_src == null)
+//   f*    = star_base + star_cL * L
+//   f     = relax(f*, h = h_coef * nu)            (h_coef > 0), else f*
+//   Q     = nu (G_hat - f)                        (h_coef > 0 or need_q)
+//   acc_out[t] = acc_in[t] + acc_cL[t] L + acc_cQ[t] Q
+//   f_out = f;  U_out = moments(f*) if kin_u_moments else U^n
+// For fluid cells: Phi[phi_store] = Phi(U_prev) (phi_store >= 0), then
+//   U_out = U^n - sum_{j < nphi} phi_coef[j] Phi[j]; buffer cells also get
+//   f_out = M_hat[U_out] (hoc) or M_hat[U^n] when `fill`.
+struct StageArgs {
+  const void* f_src;
+  const void* star_base;
+  double star_cL;
+  double h_coef;
+  int need_q;
+  void* f_out;
+  int nacc;
+  const void* acc_in[3];
+  void* acc_out[3];
+  double acc_cL[3], acc_cQ[3];
+  const double* Un;
+  const double* U_prev;
+  double* U_out;
+  double* Phi;
+  int phi_store;
+  int nphi;
+  double phi_coef[4];
+  int hoc;
+  int fill;
+  int kin_u_moments;
+  long long* ctr;
+};
+
+// Start-of-step preparation: f := M_hat[U] in the cells of list1 and list2;
+// copy_to := U (all cells) and flags_prev := flags when those are non-null.
+struct PrepArgs {
+  void* f;
+  const double* U;
+  const int* list1;
+  const int* count1;
+  const int* list2;
+  const int* count2;
+  double* copy_to;
+  uint8_t* flags_prev;
+};
+
+// Per-storage-type launchers (one table per precision).
+struct Launchers {
+  size_t elem;
+  cudaError_t (*setup)(const Geo&);
+  int (*blocks_per_sm)(const Geo&);
+  void (*stage)(const StageArgs&, const View&, int grid, cudaStream_t);
+  void (*prep)(const PrepArgs&, const View&, int grid, cudaStream_t);
+  void (*l1)(const void* f, double* L1, const View&, int grid, cudaStream_t);
+  void (*relax_cells)(const void* fs, const double* h, int n, const Geo&, double beta, void* fo, void* go,
+                      int grid, cudaStream_t);
+  void (*moments)(const void* f, double* U, const View&, int grid, cudaStream_t);
+};
+
+extern const Launchers kLaunchF64;
+extern const Launchers kLaunchF32;
+extern const Launchers kLaunchBF16;
+
+// Precision-independent kernels (kernels_common.cu).
+void launch_init_state(const double* prim /*[5][nc] rho ux uy T eps*/, const uint8_t* kin_in, double* Un,
+                       double* eps, uint8_t* flags, uint8_t* flags_prev, int nc, cudaStream_t s);
+void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
+                  uint8_t* flags_out, cudaStream_t s);
+void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
+                       cudaStream_t s);
+void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* flist, int* clist, int* counts,
+                    cudaStream_t s);
+void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
+void launch_totals(const double* Un, int nc, double* partial /*[grid][4]*/, double* out, double dxdy, int grid,
+                   cudaStream_t s);
+
+}  // namespace esbgk

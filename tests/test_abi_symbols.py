@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/esbgk.h declares; host-only entry points behave (no GPU needed)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "esbgk.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(esbgk_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2512_03586_gb300 import build as B
+    return B.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    names = declared_functions()
+    assert "esbgk_step" in names and "esbgk_relax_cells" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (esbgk_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_python_binding_declares_every_symbol(libpath):
+    from paper_2512_03586_gb300 import _abi
+    assert sorted(_abi.DECLARED) == declared_functions()
+
+
+def test_host_only_entry_points(libpath):
+    from paper_2512_03586_gb300 import _abi
+    assert _abi.esbgk_version() >= 100
+    g = _abi.Grid(128, 128, 0.0, 1.0, 0.0, 1.0, 1, 1)
+    v = _abi.VMesh(32, 8.0)
+    p = _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, _abi.FP32)
+    nb = _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p))
+    # six f arrays of nc * nv^2 floats plus O(nc) per-cell arrays
+    f_bytes = 128 * 128 * 32 * 32 * 4
+    assert 6 * f_bytes <= nb <= 6 * f_bytes + 400 * 128 * 128 + (1 << 20)
+    p64 = _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, _abi.FP64)
+    assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(v), ctypes.byref(p64)) > nb
+    for bad in (_abi.Grid(0, 4, 0, 1, 0, 1, 0, 0), _abi.Grid(4, 4, 1, 0, 0, 1, 0, 0), _abi.Grid(4, 4, 0, 1, 0, 1, 7, 0)):
+        assert _abi.esbgk_workspace_bytes(ctypes.byref(bad), ctypes.byref(v), ctypes.byref(p)) == 0
+    for badp in (_abi.Params(-0.6, 1.0, 1.0, 1e-3, 1e-6, 1, 0, 1), _abi.Params(-0.5, 0.0, 1.0, 1e-3, 1e-6, 1, 0, 1),
+                 _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, 9)):
+        assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(v), ctypes.byref(badp)) == 0
+    assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(_abi.VMesh(65, 8.0)), ctypes.byref(p)) == 0
+    # NULL arguments are rejected before any device call
+    out = ctypes.c_void_p()
+    assert _abi.esbgk_create(None, None, None, None, 0, None, ctypes.byref(out)) == _abi.E_ARG
+    assert _abi.esbgk_step(None, 1e-3, None) == _abi.E_ARG
+    assert _abi.esbgk_relax_cells(None, None, 1, 8, 1.0, -0.5, 0, None, None, None) == _abi.E_ARG
+    _abi.esbgk_destroy(None)
+
+
+def test_oracle_and_library_share_no_code():
+    """The CPU oracle and the CUDA path are independent: neither imports the other."""
+    pkg = os.path.join(ROOT, "paper_2512_03586_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", txt, re.M), f
+                assert "oracle/" not in txt, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2512_03586_gb300" not in txt, f
