@@ -46,7 +46,9 @@ typedef enum {
   ESBGK_E_NONREALIZABLE = -4,  /* rho <= 0, T <= 0, det(temperature tensor) <= 0 or a
                                   singular moment system in some cell                */
   ESBGK_E_TIMEOUT = -5,        /* reserved: a bounded device wait expired           */
-  ESBGK_E_STATE = -6           /* call out of order (e.g. step before set_state)    */
+  ESBGK_E_STATE = -6,          /* call out of order (e.g. step before set_state)    */
+  ESBGK_E_TOO_LARGE = -7       /* problem exceeds the fixed scratch of
+                                  esbgk_kinetic_steps_noalloc                        */
 } esbgk_status;
 
 typedef enum { ESBGK_FP64 = 0, ESBGK_FP32 = 1, ESBGK_BF16 = 2 } esbgk_prec;
@@ -214,6 +216,41 @@ int esbgk_last_error(esbgk_ctx* ctx, char* buf, size_t n, long long* bad_cell);
  * moment system) gets NaN in both outputs. */
 int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax,
                       double beta, int32_t prec, void* f_out, void* g_out, void* stream);
+
+/* Allocation-free stepping of an all-kinetic problem.  (The paper has no
+ * counterpart: this is a service for callers.)
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocating library
+ * routine -- work launched while a CUDA stream is being captured into a graph,
+ * a host that owns every device allocation through its own pool or budget, or
+ * a real-time loop that may not touch the allocator.  Every other entry point
+ * needs a caller-provided workspace (esbgk_create); this one needs none.
+ *
+ * It advances f by `nsteps` IMEX steps (dt, tab) with every cell kinetic and
+ * the regime frozen (params->sw and params->coupling are validated but make no
+ * difference when no cell is fluid), exactly as esbgk_create + esbgk_set_f +
+ * esbgk_step would.  The caller passes, in device memory:
+ *   f    in/out [N_c][N_v][N_v], storage type of params->prec (f^n in,
+ *        f^{n+nsteps} out);
+ *   eps  in [N_c] float64, the Knudsen number;
+ *   U    out [4][N_c] float64, the conserved moments of the final f.
+ * Intermediate stage and accumulator arrays live in one static device array of
+ * 32 MiB that the library keeps on every GPU it is loaded on until the process
+ * exits.  The problem fits when
+ *   5 * N_c * N_v^2 * (8, 4 or 2 bytes for FP64, FP32, BF16)
+ *     + 68 * N_c + 3 KiB  <=  32 MiB  (each array rounded up to 256 bytes);
+ * larger problems are rejected with ESBGK_E_TOO_LARGE before any device work.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.
+ * All calls share the one array, which keeps the last call's contents (the
+ * call clears what must start at zero): calls that may overlap on the GPU --
+ * on different streams, or from several host threads -- race and must be
+ * serialised by the caller.  The call waits for `stream` at the end and
+ * returns ESBGK_E_NONREALIZABLE if some cell became non-realizable, E_ARG on
+ * invalid input, E_CUDA on a failed CUDA call. */
+int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_vmesh* vmesh,
+                                const esbgk_params* params, double dt, const esbgk_tableau* tab,
+                                int32_t nsteps, const double* eps, void* f, double* U, void* stream);
 
 #ifdef __cplusplus
 }

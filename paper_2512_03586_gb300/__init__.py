@@ -24,7 +24,7 @@ class Error(RuntimeError):
     """A negative esbgk_status returned by the library."""
 
     NAMES = {0: "OK", -1: "E_ARG", -2: "E_WORKSPACE", -3: "E_CUDA", -4: "E_NONREALIZABLE",
-             -5: "E_TIMEOUT", -6: "E_STATE"}
+             -5: "E_TIMEOUT", -6: "E_STATE", -7: "E_TOO_LARGE"}
 
     def __init__(self, code, msg="", bad_cell=-1):
         self.code = code

@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libesbgk.so")
 
 OK = 0
-E_ARG, E_WORKSPACE, E_CUDA, E_NONREALIZABLE, E_TIMEOUT, E_STATE = -1, -2, -3, -4, -5, -6
+E_ARG, E_WORKSPACE, E_CUDA, E_NONREALIZABLE, E_TIMEOUT, E_STATE, E_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_WORKSPACE", -3: "E_CUDA", -4: "E_NONREALIZABLE",
-                -5: "E_TIMEOUT", -6: "E_STATE"}
+                -5: "E_TIMEOUT", -6: "E_STATE", -7: "E_TOO_LARGE"}
 FP64, FP32, BF16 = 0, 1, 2
 BC = {"periodic": 0, "outflow": 1}
 SWITCH = {"frozen": 0, "plain": 1}
@@ -92,6 +92,8 @@ _SIGS = {
     "esbgk_last_error": (I, [P, ctypes.c_char_p, ctypes.c_size_t, LL]),
     "esbgk_relax_cells": (I, [P, D, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                               ctypes.c_int32, P, P, P]),
+    "esbgk_kinetic_steps_noalloc": (I, [ctypes.POINTER(Grid), ctypes.POINTER(VMesh), ctypes.POINTER(Params),
+                                        ctypes.c_double, ctypes.POINTER(Tableau), ctypes.c_int32, D, P, D, P]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -780,3 +781,135 @@ int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (esbgk_kinetic_steps_noalloc).  Its stage and
+// accumulator arrays live in this file-scope device array instead of a
+// caller workspace; see the header for who needs this and the size rule.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 32ull << 20;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name only stands in for the symbol; the address must come from
+// cudaGetSymbolAddress with the device current.
+unsigned char* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+cudaError_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+// Every cell kinetic: klist = 0..nc-1, no buffer/fluid/converted cells; clear
+// the error word and the counters.
+__global__ void noalloc_init_kernel(int* klist, int* counts, DevErr* err, long long* ctr, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) klist[c] = c;
+  if (c == 0) {
+    counts[0] = nc;
+    counts[1] = counts[2] = counts[3] = 0;
+    err->code = 0;
+    err->cell = -1;
+    ctr[0] = ctr[1] = 0;
+  }
+}
+
+}  // namespace
+
+extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_vmesh* vmesh,
+                                           const esbgk_params* params, double dt, const esbgk_tableau* tab,
+                                           int32_t nsteps, const double* eps, void* f, double* U, void* stream) {
+  if (!valid_inputs(grid, vmesh, params) || !eps || !f || !U || nsteps < 0 || !(dt > 0) || !std::isfinite(dt) ||
+      !valid_tableau(tab))
+    return ESBGK_E_ARG;
+  const Launchers* L = launchers_for(params->prec);
+  const Geo g = make_geo(grid, vmesh);
+  const size_t fsz = (size_t)g.nc * g.nvv * L->elem, dsz = (size_t)g.nc * sizeof(double);
+  const size_t off_f1 = 0, off_f2 = up(fsz), off_acc = 2 * up(fsz);
+  const size_t off_us0 = 5 * up(fsz), off_us1 = off_us0 + up(4 * dsz);
+  const size_t off_kl = off_us1 + up(4 * dsz);
+  const size_t off_cnt = off_kl + up((size_t)g.nc * sizeof(int));
+  const size_t off_err = off_cnt + up(4 * sizeof(int));
+  const size_t off_ctr = off_err + up(sizeof(DevErr));
+  const size_t need = off_ctr + up(2 * sizeof(long long));
+  if (need > kNoallocScratchBytes) return ESBGK_E_TOO_LARGE;
+  unsigned char* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return ESBGK_E_CUDA;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || L->setup(g) != cudaSuccess)
+    return ESBGK_E_CUDA;
+
+  // a context on the stack whose arrays are the caller's f, eps, U and the
+  // static scratch (no host heap, no device allocation)
+  esbgk_ctx X;
+  X.g = g;
+  X.m.beta = params->beta;
+  X.m.tau = params->tau;
+  X.m.eps_w = params->cweno_eps;
+  X.m.eta_factor = params->eta_factor;
+  X.m.delta = params->delta;
+  X.prec = params->prec;
+  X.sw = ESBGK_SWITCH_FROZEN;
+  X.coupling = ESBGK_COUPLE_STAGE;
+  X.L = L;
+  X.stream = (cudaStream_t)stream;
+  X.grid_stage = nsm * L->blocks_per_sm(g);
+  X.grid_red = 1;
+  X.ws = base;
+  X.F[0] = f;
+  X.F[1] = base + off_f1;
+  X.F[2] = base + off_f2;
+  for (int q = 0; q < 3; ++q) X.ACC[q] = base + off_acc + q * up(fsz);
+  X.Un = U;
+  X.Us[0] = (double*)(base + off_us0);
+  X.Us[1] = (double*)(base + off_us1);
+  X.Phi = X.Us[0];  // only fluid cells touch Phi; there are none
+  X.eps = (double*)eps;
+  X.lamA = X.L1 = X.stage5 = X.red = X.tot = nullptr;
+  X.flags = X.flags_prev = X.cat = nullptr;
+  X.klist = X.blist = X.flist = X.clist = (int*)(base + off_kl);
+  X.counts = (int*)(base + off_cnt);
+  X.err = (DevErr*)(base + off_err);
+  X.ctr = (long long*)(base + off_ctr);
+  X.cur = 0;
+  X.have_state = true;
+  X.conv_pending = false;
+  X.steps = 0;
+  X.status = ESBGK_OK;
+  X.bad_cell = -1;
+
+  noalloc_init_kernel<<<(g.nc + 255) / 256, 256, 0, X.stream>>>(X.klist, X.counts, X.err, X.ctr, g.nc);
+  if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
+  if (nsteps == 0) {
+    L->moments(f, U, X.view(), X.grid_stage, X.stream);
+    if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    const int r = advance(&X, dt, tab);
+    if (r) return r;
+  }
+  if (X.cur != 0 &&
+      cudaMemcpyAsync(f, X.F[X.cur], fsz, cudaMemcpyDeviceToDevice, X.stream) != cudaSuccess)
+    return ESBGK_E_CUDA;
+  DevErr e{};
+  if (cudaMemcpyAsync(&e, X.err, sizeof e, cudaMemcpyDeviceToHost, X.stream) != cudaSuccess ||
+      cudaStreamSynchronize(X.stream) != cudaSuccess)
+    return ESBGK_E_CUDA;
+  return e.code ? ESBGK_E_NONREALIZABLE : ESBGK_OK;
+}
