@@ -243,7 +243,7 @@ int regime_update(esbgk_ctx* X) {
   const View V = X->view();
   {
     Timed t(X, ESBGK_K_L1);
-    X->L->l1(X->F[X->cur], X->L1, V, X->grid_stage, X->stream);
+    X->L->l1(X->F[X->cur], X->Un, X->L1, V, X->grid_stage, X->stream);
   }
   int r = after_launch(X, "l1 kernel");
   if (r) return r;

@@ -69,6 +69,15 @@ ESBGK_DEV float ldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 ESBGK_DEV double fdiv(double a, double b) { return a / b; }
 ESBGK_DEV float fdiv(float a, float b) { return __fdividef(a, b); }
 
+// Precision-explicit |x|, sqrt and max: a float argument must never be
+// promoted to double (on GB300 the FP64 pipe is narrow).
+ESBGK_DEV float rabs(float x) { return fabsf(x); }
+ESBGK_DEV double rabs(double x) { return fabs(x); }
+ESBGK_DEV float rsqrt_(float x) { return sqrtf(x); }
+ESBGK_DEV double rsqrt_(double x) { return sqrt(x); }
+ESBGK_DEV float rmax(float a, float b) { return fmaxf(a, b); }
+ESBGK_DEV double rmax(double a, double b) { return fmax(a, b); }
+
 // 2^x.  FP32: the hardware approximation (ex2.approx, max rel. error ~2^-22).
 ESBGK_DEV float exp2r(float x) {
   float y;

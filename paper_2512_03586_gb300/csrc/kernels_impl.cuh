@@ -2,8 +2,16 @@
 //
 // Included by one translation unit per storage type S (double, float,
 // __nv_bfloat16), each of which instantiates the launchers declared in
-// launch.h.  All per-element arithmetic runs in R = Real<S>::T; per-cell tensor
-// solves and U run in float64.
+// launch.h.  Per-element arithmetic runs in R = Real<S>::T.
+//
+// Work decomposition: one warp owns one cell.  Its 32 lanes stride over the
+// N_v^2 velocities (lane l always handles nodes l, l+32, ...), so every
+// velocity reduction is a warp butterfly (no CTA barrier) and the per-cell
+// solves run redundantly in all lanes (no broadcast).  A CTA holds
+// kCellWarps independent cells; per-warp shared memory keeps f* of the cell
+// between the passes.  A persistent grid walks the compacted work
+// list: kinetic cells, then buffer cells, then chunks of 32 fluid cells (one
+// lane per cell).
 #pragma once
 
 #include "common.cuh"
@@ -11,151 +19,140 @@
 
 namespace esbgk {
 
-// ---------------------------------------------------------------------------
-// Per-CTA shared state of one cell.
-struct CellShared {
-  double red[kWarps * 15];
-  double tot[16];
-  double rho, ux, uy, T;          // moments of the cell
-  double ixx, ixy, iyy;           // inverse temperature tensor
-  double pref, isT;               // rho/(2 pi sqrt det Tt), 1/sqrt(T)
-  double h, nu;                   // implicit coefficient dt a_ii nu, nu = tau/eps
-  double a[6];                    // moment-projection coefficients
-  double U[4];                    // conserved variables (fluid/buffer cells)
-  int ok;
-};
+constexpr int kCellWarps = 4;                  // cells (warps) per CTA at most
+constexpr int kCellThreads = kCellWarps * 32;  // threads per CTA at most
+constexpr double kLog2e = 1.4426950408889634;
 
-// Monomial index of xi_x^p xi_y^q (p + q <= 4) in the 15 projection sums.
+// Monomial index of xi_x^p xi_y^q (p + q <= 4) among the 15 projection sums.
 __host__ __device__ constexpr int mono(int p, int q) { return (p + q) * (p + q + 1) / 2 + q; }
 
-// Exponents of the quadratic basis psi = (1, x, y, x^2, xy, y^2).
-static __device__ __constant__ int kPsiP[6] = {0, 1, 0, 2, 1, 0};
-static __device__ __constant__ int kPsiQ[6] = {0, 0, 1, 0, 1, 2};
+// Per-cell parameters of the discrete Gaussian, identical in every lane.
+template <typename R>
+struct CellPar {
+  R ux, uy;          // mean velocity
+  R qxx, qxy, qyy;   // exponent -log2(e)/2 (v-u)^T Tt^{-1} (v-u) = qxx cx^2 + qxy cx cy + qyy cy^2
+  R pref;            // rho / (2 pi sqrt(det Tt))
+  R isT;             // 1/sqrt(T), scale of xi = (v-u)/sqrt(T)
+  R t[6];            // projection targets (rho, 0, 0, rho Tt/T)
+  R a[6];            // projection coefficients
+};
 
-// Per-cell temperature tensor and Gaussian parameters (thread 0 only).
-// From the moments m = (rho, m_x, m_y, S_xx, S_xy, S_yy) (already multiplied by
-// w): u = m/rho, Theta = S/rho - u u, T = tr(Theta)/2 (hypothesis H3, Sec. 2).
-// If relax: Theta <- (Theta + k T I)/(1 + k), k = h (1 - beta), the exact
-// stress moment of the implicit stage.  Tt = (1 - beta) T I + beta Theta.
+// Velocity node iterator of one lane: nodes k = lane, lane+32, ... with
+// (kx, ky) = (k mod N_v, k div N_v) and the node velocities
+// (vx, vy) = v0 + (kx, ky) dv, advanced without divisions or int->float
+// conversions (on GB300 conversions run on the narrow FP64 pipe).  fx, fy
+// hold kx, ky as exact small integers in R, so vx, vy are bit-identical to
+// v0 + R(kx) dv.
+template <typename R>
+struct NodeIter {
+  int k, kx, dkx, nv;
+  R fx, fy, fdkx, fdky, fnv, v0, dv;
+  ESBGK_DEV NodeIter(int lane, int nv_, R v0_, R dv_)
+      : k(lane), kx(lane % nv_), dkx(32 % nv_), nv(nv_), fx(R(lane % nv_)), fy(R(lane / nv_)),
+        fdkx(R(32 % nv_)), fdky(R(32 / nv_)), fnv(R(nv_)), v0(v0_), dv(dv_) {}
+  ESBGK_DEV R vx() const { return v0 + fx * dv; }
+  ESBGK_DEV R vy() const { return v0 + fy * dv; }
+  ESBGK_DEV void next() {
+    k += 32;
+    kx += dkx;
+    fx += fdkx;
+    fy += fdky;
+    if (kx >= nv) {
+      kx -= nv;
+      fx -= fnv;
+      fy += R(1);
+    }
+  }
+};
+
+// Temperature tensor from the moments of a cell (hypothesis H3 and Sec. 2).
+// m are the raw sums over nodes of f, c f, c (x) c f with c = v - u0 about a
+// reference velocity u0 (this keeps Theta = S'/rho - (u-u0)(u-u0) free of
+// cancellation); w is the quadrature weight.
+//   rho = w m0, u = u0 + w m1/rho, Theta, T = tr(Theta)/2;
+//   relax: Theta <- (Theta + k T I)/(1 + k), k = h (1 - beta) -- the exact
+//          stress moment of the implicit stage;
+//   Tt = (1 - beta) T I + beta Theta; its determinant in float64.
 // Returns false for a non-realizable state.
-static __device__ bool cell_tensor(CellShared& sh, const double* m, double beta, double h, bool relax) {
-  const double rho = m[0];
-  if (!(rho > 0.0)) return false;
-  const double ux = m[1] / rho, uy = m[2] / rho;
-  double txx = m[3] / rho - ux * ux, txy = m[4] / rho - ux * uy, tyy = m[5] / rho - uy * uy;
-  const double T = 0.5 * (txx + tyy);
-  if (!(T > 0.0)) return false;
+template <typename R>
+ESBGK_DEV bool es_params(const R (&m)[6], R u0x, R u0y, R w, R beta, R h, bool relax, CellPar<R>& P) {
+  const R rho = w * m[0];
+  if (!(rho > R(0))) return false;
+  const R ir = R(1) / rho;
+  const R dux = w * m[1] * ir, duy = w * m[2] * ir;
+  R txx = w * m[3] * ir - dux * dux, txy = w * m[4] * ir - dux * duy, tyy = w * m[5] * ir - duy * duy;
+  const R T = R(0.5) * (txx + tyy);
+  if (!(T > R(0))) return false;
   if (relax) {
-    const double k = h * (1.0 - beta);
-    const double inv = 1.0 / (1.0 + k);
+    const R k = h * (R(1) - beta);
+    const R inv = R(1) / (R(1) + k);
     txx = (txx + k * T) * inv;
     txy = txy * inv;
     tyy = (tyy + k * T) * inv;
   }
-  const double Txx = (1.0 - beta) * T + beta * txx;
-  const double Txy = beta * txy;
-  const double Tyy = (1.0 - beta) * T + beta * tyy;
-  const double det = Txx * Tyy - Txy * Txy;
+  const R Txx = (R(1) - beta) * T + beta * txx;
+  const R Txy = beta * txy;
+  const R Tyy = (R(1) - beta) * T + beta * tyy;
+  const double det = fma((double)Txx, (double)Tyy, -(double)Txy * (double)Txy);
   if (!(det > 0.0)) return false;
-  sh.rho = rho;
-  sh.ux = ux;
-  sh.uy = uy;
-  sh.T = T;
-  sh.ixx = Tyy / det;
-  sh.ixy = -Txy / det;
-  sh.iyy = Txx / det;
-  sh.pref = rho / (2.0 * kPi * sqrt(det));
-  sh.isT = 1.0 / sqrt(T);
-  // targets t of the projection (density, zero mean in xi, stress Tt/T)
-  sh.a[0] = rho;
-  sh.a[1] = 0.0;
-  sh.a[2] = 0.0;
-  sh.a[3] = rho * Txx / T;
-  sh.a[4] = rho * Txy / T;
-  sh.a[5] = rho * Tyy / T;
+  const R idet = R(1.0 / det);
+  P.ux = u0x + dux;
+  P.uy = u0y + duy;
+  P.qxx = R(-0.5 * kLog2e) * Tyy * idet;
+  P.qxy = R(kLog2e) * Txy * idet;
+  P.qyy = R(-0.5 * kLog2e) * Txx * idet;
+  P.pref = rho * R(0.5 / kPi) / rsqrt_(R(det));
+  P.isT = R(1) / rsqrt_(T);
+  const R rT = rho / T;
+  P.t[0] = rho;
+  P.t[1] = R(0);
+  P.t[2] = R(0);
+  P.t[3] = rT * Txx;
+  P.t[4] = rT * Txy;
+  P.t[5] = rT * Tyy;
   return true;
 }
 
-// Same parameters for the Maxwellian of (rho, u, T): Tt = T I.
-static __device__ bool cell_maxwell(CellShared& sh, double rho, double ux, double uy, double T) {
-  if (!(rho > 0.0) || !(T > 0.0)) return false;
-  sh.rho = rho;
-  sh.ux = ux;
-  sh.uy = uy;
-  sh.T = T;
-  sh.ixx = 1.0 / T;
-  sh.ixy = 0.0;
-  sh.iyy = 1.0 / T;
-  sh.pref = rho / (2.0 * kPi * T);
-  sh.isT = 1.0 / sqrt(T);
-  sh.a[0] = rho;
-  sh.a[1] = 0.0;
-  sh.a[2] = 0.0;
-  sh.a[3] = rho;
-  sh.a[4] = 0.0;
-  sh.a[5] = rho;
-  return true;
-}
-
-// 6x6 symmetric positive definite solve by Cholesky, in place on b.
-static __device__ bool chol6(double (&H)[6][6], double (&b)[6]) {
-  double L[6][6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    double s = H[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-    if (!(s > 0.0)) return false;
-    const double d = sqrt(s);
-    L[j][j] = d;
-    const double id = 1.0 / d;
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      double t = H[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t * id;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double t = b[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) t -= L[i][k] * b[k];
-    b[i] = t / L[i][i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    double t = b[i];
-#pragma unroll
-    for (int k = i + 1; k < 6; ++k) t -= L[k][i] * b[k];
-    b[i] = t / L[i][i];
-  }
-  return true;
-}
-
-// Discrete Gaussian with exact moments (the projected ES Gaussian): evaluate
-// G_k = pref exp(-(v_k-u)^T Tt^{-1} (v_k-u)/2) into Gs[k], reduce the 15
-// moments w sum G xi^p eta^q (xi = (v-u)/sqrt T), and solve H a = t - r for the
-// coefficients of G_hat = G (1 + a . psi).  Needs sh filled by cell_tensor or
-// cell_maxwell (sh.a holds the targets t on entry).  Sets sh.ok = 0 on a
-// singular system.  All threads of the CTA must call it.
+// Parameters of the Maxwellian of (rho, u, T): Tt = T I.
 template <typename R>
-__device__ void gauss_project(const Geo& g, CellShared& sh, R* Gs) {
-  const R L2E = R(1.4426950408889634);
-  const R ux = (R)sh.ux, uy = (R)sh.uy;
-  const R qxx = (R)(-0.5 * sh.ixx) * L2E, qxy = (R)(-sh.ixy) * L2E, qyy = (R)(-0.5 * sh.iyy) * L2E;
-  const R pref = (R)sh.pref, isT = (R)sh.isT;
+ESBGK_DEV bool maxwell_params(double rho, double ux, double uy, double T, CellPar<R>& P) {
+  if (!(rho > 0.0) || !(T > 0.0)) return false;
+  P.ux = R(ux);
+  P.uy = R(uy);
+  P.qxx = R(-0.5 * kLog2e / T);
+  P.qxy = R(0);
+  P.qyy = P.qxx;
+  P.pref = R(rho * 0.5 / (kPi * T));
+  P.isT = R(1.0 / sqrt(T));
+  P.t[0] = R(rho);
+  P.t[1] = P.t[2] = R(0);
+  P.t[3] = R(rho);
+  P.t[4] = R(0);
+  P.t[5] = R(rho);
+  return true;
+}
+
+template <typename R>
+ESBGK_DEV R gauss_at(const CellPar<R>& P, R cx, R cy) {
+  return P.pref * exp2r(P.qxx * cx * cx + P.qxy * cx * cy + P.qyy * cy * cy);
+}
+
+// Projection of the discrete Gaussian onto exact moments (whole warp): the 15
+// sums w sum G xi^p eta^q over the nodes, then H a = t - r with
+// H_mn = w sum G psi_m psi_n, r_m = w sum G psi_m, psi = (1, x, y, x^2, xy, y^2).
+// After this G_hat = G (1 + a . psi) has w sum psi G_hat = t.
+template <typename R>
+ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
   R s[15];
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
-  for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-    const int kx = k % g.nv, ky = k / g.nv;
-    const R cx = v0 + R(kx) * dv - ux, cy = v0 + R(ky) * dv - uy;
-    const R G = pref * exp2r(qxx * cx * cx + qxy * cx * cy + qyy * cy * cy);
-    Gs[k] = G;
-    const R x = cx * isT, y = cy * isT;
+  NodeIter<R> it(lane, g.nv, v0, dv);
+#pragma unroll 2
+  for (; it.k < g.nvv; it.next()) {
+    const R cx = it.vx() - P.ux, cy = it.vy() - P.uy;
+    const R G = gauss_at(P, cx, cy);
+    const R x = cx * P.isT, y = cy * P.isT;
     const R Gx = G * x, Gy = G * y;
     const R Gxx = Gx * x, Gxy = Gx * y, Gyy = Gy * y;
     s[0] += G;
@@ -174,67 +171,76 @@ __device__ void gauss_project(const Geo& g, CellShared& sh, R* Gs) {
     s[13] += Gxy * y * y;
     s[14] += Gyy * y * y;
   }
-  block_sum<15>(s, sh.red, sh.tot);
-  if (threadIdx.x == 0) {
-    const double w = g.w;
-    double H[6][6], rhs[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
+  for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * (R)g.w;
+  // H a = t - r by Gaussian elimination spread over lanes 0..5 (lane m holds
+  // row m and its right-hand side; H is symmetric positive definite, so no
+  // pivoting), pivot rows broadcast by shuffles.
+  constexpr int PP[6] = {0, 1, 0, 2, 1, 0};
+  constexpr int PQ[6] = {0, 0, 1, 0, 1, 2};
+  const int row = lane < 6 ? lane : 5;
+  R h[7];
 #pragma unroll
-      for (int n = 0; n < 6; ++n) H[m][n] = w * sh.tot[mono(kPsiP[m] + kPsiP[n], kPsiQ[m] + kPsiQ[n])];
-      rhs[m] = sh.a[m] - w * sh.tot[mono(kPsiP[m], kPsiQ[m])];
-    }
-    const bool ok = chol6(H, rhs);
+  for (int n = 0; n < 6; ++n) {
+    R v = R(0);
 #pragma unroll
-    for (int m = 0; m < 6; ++m) sh.a[m] = ok ? rhs[m] : 0.0;
-    sh.ok = ok ? sh.ok : 0;
+    for (int m = 0; m < 6; ++m)
+      if (row == m) v = s[mono(PP[m] + PP[n], PQ[m] + PQ[n])];
+    h[n] = v;
   }
-  __syncthreads();
+  {
+    R v = R(0);
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+      if (row == m) v = P.t[m] - s[mono(PP[m], PQ[m])];
+    h[6] = v;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    R piv[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) piv[n] = __shfl_sync(0xffffffffu, h[n], p);
+    ok = ok && piv[p] > R(0);
+    const R fct = row > p ? h[p] / piv[p] : R(0);
+#pragma unroll
+    for (int n = 0; n < 7; ++n) h[n] -= fct * piv[n];
+  }
+  // back substitution: a_p = (b_p - sum_{n>p} U_pn a_n) / U_pp
+#pragma unroll
+  for (int p = 5; p >= 0; --p) {
+    R acc = h[6];
+#pragma unroll
+    for (int n = p + 1; n < 6; ++n) acc -= h[n] * P.a[n];
+    const R ap = __shfl_sync(0xffffffffu, acc / h[p], p);
+    P.a[p] = ap;
+  }
+  return ok;
 }
 
-// G_hat at node k from the stored G_k.
+// G_hat at node (cx, cy) = v - u.
 template <typename R>
-ESBGK_DEV R ghat_at(const Geo& g, const CellShared& sh, const R* a, R G, int k) {
-  const int kx = k % g.nv, ky = k / g.nv;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv, isT = (R)sh.isT;
-  const R x = (v0 + R(kx) * dv - (R)sh.ux) * isT, y = (v0 + R(ky) * dv - (R)sh.uy) * isT;
-  return G * (R(1) + a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y);
+ESBGK_DEV R ghat(const CellPar<R>& P, R cx, R cy) {
+  const R G = gauss_at(P, cx, cy);
+  const R x = cx * P.isT, y = cy * P.isT;
+  return G * (R(1) + P.a[0] + P.a[1] * x + P.a[2] * y + P.a[3] * x * x + P.a[4] * x * y + P.a[5] * y * y);
 }
 
 // Element offsets of the two-cell cross stencil of cell c (BC mapped):
-// o[0..3] = i-2, i-1, i+1, i+2 along x, o[4..7] the same along y.
-ESBGK_DEV void stencil_offsets(const Geo& g, int c, size_t (&o)[8]) {
+// o[0..3] = i-2, i-1, i+1, i+2 along x, o[4..7] the same along y.  Offsets
+// are 32-bit: the library limits N_c N_v^2 to below 2^31 elements.
+ESBGK_DEV void stencil_offsets(const Geo& g, int c, unsigned (&o)[8]) {
   const int i = c % g.nx, j = c / g.nx;
   const int d[4] = {-2, -1, 1, 2};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    o[q] = ((size_t)j * g.nx + nb(i + d[q], g.nx, g.bcx)) * g.nvv;
-    o[4 + q] = ((size_t)nb(j + d[q], g.ny, g.bcy) * g.nx + i) * g.nvv;
+    o[q] = (unsigned)(j * g.nx + nb(i + d[q], g.nx, g.bcx)) * (unsigned)g.nvv;
+    o[4 + q] = (unsigned)(nb(j + d[q], g.ny, g.bcy) * g.nx + i) * (unsigned)g.nvv;
   }
 }
 
-// L(f) at node k of cell c: upwind (Lax-Friedrichs with |v_k|) flux of CWENO3
-// face values along x and y.  up/dn/far are the upwind, downwind and far
-// upwind neighbours for the sign of v, so no branch diverges within a warp;
-// L_x = |v_x| (F(face away from upwind) - F(face toward upwind)) / dx.
-template <typename S, typename R>
-ESBGK_DEV R transport_at(const S* __restrict__ f, size_t o0, const size_t (&o)[8], int k, R vx, R vy,
-                         R idx, R idy, R epsw, R& q0) {
-  q0 = ld(f + o0 + k);
-  const bool px = vx > R(0), py = vy > R(0);
-  const R ux = ld(f + (px ? o[1] : o[2]) + k);
-  const R dx = ld(f + (px ? o[2] : o[1]) + k);
-  const R fx = ld(f + (px ? o[0] : o[3]) + k);
-  const R uy = ld(f + (py ? o[5] : o[6]) + k);
-  const R dy = ld(f + (py ? o[6] : o[5]) + k);
-  const R fy = ld(f + (py ? o[4] : o[7]) + k);
-  const R Lx = fabs(vx) * (cweno_face(ux, q0, dx, epsw) - cweno_face(fx, ux, q0, epsw)) * idx;
-  const R Ly = fabs(vy) * (cweno_face(uy, q0, dy, epsw) - cweno_face(fy, uy, q0, epsw)) * idy;
-  return Lx + Ly;
-}
-
 // ---------------------------------------------------------------------------
-// Euler part (fluid cells), one thread per cell.
+// Euler part (fluid cells), one lane per cell.
 
 // Physical flux of Eq. Euler_Compact along d (0 = x, 1 = y), gamma = 2, and the
 // local wave speed |u_d| + sqrt(gamma P/rho).
@@ -247,13 +253,13 @@ ESBGK_DEV void euler_phys(const R (&U)[4], int d, R (&F)[4], R& a) {
   F[1] = U[1] * un + (d == 0 ? P : R(0));
   F[2] = U[2] * un + (d == 1 ? P : R(0));
   F[3] = un * (U[3] + P);
-  a = fabs(un) + sqrt(R(2) * P / rho);
+  a = rabs(un) + rsqrt_(R(2) * P / rho);
 }
 
 // Phi(U)(c): CWENO3 face states per component, local Lax-Friedrichs flux at
 // the four faces of the cell, divergence (Eq. semidiscrete Euler).
 template <typename R>
-__device__ void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c, R epsw, R (&phi)[4]) {
+ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c, R epsw, R (&phi)[4]) {
   const int i = c % g.nx, j = c / g.nx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) phi[q] = R(0);
@@ -281,7 +287,7 @@ __device__ void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c
     euler_phys(Rm, d, FRm, aRm);
     euler_phys(Lp, d, FLp, aLp);
     euler_phys(Rp, d, FRp, aRp);
-    const R am = fmax(aLm, aRm), ap = fmax(aLp, aRp);
+    const R am = rmax(aLm, aRm), ap = rmax(aLp, aRp);
     const R ih = R(1) / (R)(d == 0 ? g.dx : g.dy);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -295,7 +301,7 @@ __device__ void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c
 // U^(i)(c) = U^n(c) - sum_j coef_j Phi_j(c) for a fluid cell, after storing
 // Phi_{i-1}(c) when requested (Eqs. RKEuler, RKEuler_2).
 template <typename R>
-__device__ void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)[4]) {
+ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)[4]) {
   const size_t nc = V.g.nc;
   if (A.phi_store >= 0) {
     R phi[4];
@@ -320,162 +326,335 @@ ESBGK_DEV void prim_of(const double (&U)[4], double& rho, double& ux, double& uy
   T = (U[3] - 0.5 * rho * (ux * ux + uy * uy)) / rho;
 }
 
+// Reference velocity for the moment sums of cell c: the mean velocity held
+// in U (0 when U is not usable).
+template <typename R>
+ESBGK_DEV void ref_velocity(const double* U, size_t nc, int c, R& u0x, R& u0y) {
+  u0x = R(0);
+  u0y = R(0);
+  if (!U) return;
+  const double rho = U[c];
+  if (rho > 0.0) {
+    u0x = R(U[nc + c] / rho);
+    u0y = R(U[2 * nc + c] / rho);
+  }
+}
+
+// Conserved variables (float64) from the raw moment sums about u0.
+template <typename R>
+ESBGK_DEV void cons_from_sums(const R (&m)[6], R u0x, R u0y, double w, double (&U)[4]) {
+  const double m0 = w * (double)m[0], m1 = w * (double)m[1], m2 = w * (double)m[2];
+  const double ux = u0x, uy = u0y;
+  U[0] = m0;
+  U[1] = m1 + ux * m0;
+  U[2] = m2 + uy * m0;
+  U[3] = 0.5 * w * ((double)m[3] + (double)m[5]) + ux * m1 + uy * m2 + 0.5 * (ux * ux + uy * uy) * m0;
+}
+
 // ---------------------------------------------------------------------------
-// Kinetic cell of a stage (or of the final combination).
-template <typename S>
-__device__ void kinetic_cell(const StageArgs& A, const View& V, int c, CellShared& sh,
-                             typename Real<S>::T* sm) {
+// Kinetic cell of a stage (or of the final combination), one warp.
+// Loads of one batch are issued together before any store of the batch:
+// the compiler cannot prove that the output arrays do not alias the inputs,
+// so without this every store would wait for the previous node's loads.
+#ifndef ESBGK_BATCH
+#define ESBGK_BATCH 2
+#endif
+constexpr int kBatch = ESBGK_BATCH;
+
+// The seven values of the transport stencil of node k (centre, then upwind,
+// downwind and far-upwind neighbours along x and along y for the sign of v).
+template <typename S, typename R>
+ESBGK_DEV void stencil_load(const S* __restrict__ f, unsigned o0, const unsigned (&o)[8], unsigned k, bool px,
+                            bool py, R (&q)[7]) {
+  q[0] = ld(f + o0 + k);
+  q[1] = ld(f + (px ? o[1] : o[2]) + k);
+  q[2] = ld(f + (px ? o[2] : o[1]) + k);
+  q[3] = ld(f + (px ? o[0] : o[3]) + k);
+  q[4] = ld(f + (py ? o[5] : o[6]) + k);
+  q[5] = ld(f + (py ? o[6] : o[5]) + k);
+  q[6] = ld(f + (py ? o[4] : o[7]) + k);
+}
+
+// L(f) at a node from its stencil values: upwind (Lax-Friedrichs with |v|)
+// flux of CWENO3 face values; L_x = |v_x| (F(face away from the upwind
+// neighbour) - F(face toward it)) / dx, the same along y.
+template <typename R>
+ESBGK_DEV R transport_of(const R (&q)[7], R vx, R vy, R idx, R idy, R epsw) {
+  const R Lx = rabs(vx) * (cweno_face(q[1], q[0], q[2], epsw) - cweno_face(q[3], q[1], q[0], epsw)) * idx;
+  const R Ly = rabs(vy) * (cweno_face(q[4], q[0], q[5], epsw) - cweno_face(q[6], q[4], q[0], epsw)) * idy;
+  return Lx + Ly;
+}
+
+// Compile-time shapes of a kinetic stage launch.  The inner loops test none
+// of these flags when they are fixed at compile time; kGeneric reads them all
+// at run time and serves any other tableau.
+enum StageMode : int {
+  kGeneric = 0,
+  kFirstRelax2 = 1,   // f* from f_src; relaxation; two accumulators started from f_src (ARS stage 2)
+  kLoadedRelax1 = 2,  // f* from a loaded accumulator; relaxation; one loaded accumulator (ARS stage 3)
+  kFinal = 3,         // no collision term; f* from a loaded accumulator; no accumulator (final combination)
+  kFirstRelax0 = 4,   // f* from f_src; relaxation; no accumulator (stiffly accurate last stage)
+  kNumModes = 5
+};
+template <int M>
+struct ModeT {  // kGeneric: unused values
+  static constexpr bool relax = false, base_src = false, acc_src = false;
+  static constexpr int nacc = 0;
+};
+template <>
+struct ModeT<kFirstRelax2> {
+  static constexpr bool relax = true, base_src = true, acc_src = true;
+  static constexpr int nacc = 2;
+};
+template <>
+struct ModeT<kLoadedRelax1> {
+  static constexpr bool relax = true, base_src = false, acc_src = false;
+  static constexpr int nacc = 1;
+};
+template <>
+struct ModeT<kFinal> {
+  static constexpr bool relax = false, base_src = false, acc_src = false;
+  static constexpr int nacc = 0;
+};
+template <>
+struct ModeT<kFirstRelax0> {
+  static constexpr bool relax = true, base_src = true, acc_src = false;
+  static constexpr int nacc = 0;
+};
+
+// Host-side choice of the specialisation for a launch.
+inline int stage_mode(const StageArgs& A) {
+  const bool relax = A.h_coef > 0.0;
+  if (!A.f_src) return kGeneric;
+  const bool bsrc = A.star_base == A.f_src;
+  if (bsrc && relax && A.nacc == 2 && A.acc_in[0] == A.f_src && A.acc_in[1] == A.f_src) return kFirstRelax2;
+  if (!bsrc && relax && A.nacc == 1 && A.acc_in[0] != A.f_src) return kLoadedRelax1;
+  if (!bsrc && !relax && !A.need_q && A.nacc == 0) return kFinal;
+  if (bsrc && relax && A.nacc == 0) return kFirstRelax0;
+  return kGeneric;
+}
+
+// Kinetic cell of a stage (or of the final combination), one warp.
+// Pass 1 forms f* = star_base + star_cL L(f_src) and its moments, keeps f* in
+// the warp's shared memory and writes the partial accumulators
+// acc_in + acc_cL L to the accumulator outputs; pass 3 adds acc_cQ Q to them
+// (a re-read that stays in L2) and writes f.  Without a collision term
+// (the final combination) everything is written in pass 1.
+template <typename S, int M>
+ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs) {
   using R = typename Real<S>::T;
+  constexpr bool GEN = M == kGeneric;
   const Geo& g = V.g;
-  R* sfs = sm;
-  R* sL = sm + g.nvv;
-  R* sG = sm + 2 * g.nvv;
-  R* sc0 = sm + 3 * g.nvv;
-  const size_t o0 = (size_t)c * g.nvv;
-  size_t o[8];
+  const unsigned o0 = (unsigned)c * (unsigned)g.nvv;
+  unsigned o[8];
   stencil_offsets(g, c, o);
   const S* fsrc = (const S*)A.f_src;
   const S* sbase = (const S*)A.star_base;
-  const bool base_is_src = A.star_base == A.f_src;
+  const bool has_src = GEN ? fsrc != nullptr : true;
+  const bool base_is_src = GEN ? A.star_base == A.f_src : ModeT<M>::base_src;
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
   const R idx = (R)(1.0 / g.dx), idy = (R)(1.0 / g.dy), epsw = (R)V.m.eps_w, cL = (R)A.star_cL;
+  const bool relax = GEN ? A.h_coef > 0.0 : ModeT<M>::relax;
+  const bool proj = GEN ? (relax || A.need_q) : ModeT<M>::relax;
+  S* fout = (S*)A.f_out;
+  const bool has_out = GEN ? fout != nullptr : true;
+  const int nacc = GEN ? A.nacc : ModeT<M>::nacc;
+  const S* ain[3];
+  S* aout[3];
+  bool asrc[3];
+  R aL[3], aQ[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    ain[t] = t < nacc ? (const S*)A.acc_in[t] : nullptr;
+    aout[t] = t < nacc ? (S*)A.acc_out[t] : nullptr;
+    asrc[t] = t < nacc && (GEN ? ain[t] == fsrc : ModeT<M>::acc_src);
+    aL[t] = t < nacc ? (R)A.acc_cL[t] : R(0);
+    aQ[t] = t < nacc ? (R)A.acc_cQ[t] : R(0);
+  }
+  R u0x, u0y;
+  ref_velocity(A.U_prev, g.nc, c, u0x, u0y);
 
   // pass 1: transport of the previous stage, f*, moments of f*
   R m[6];
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = R(0);
-  for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-    const int kx = k % g.nv, ky = k / g.nv;
-    const R vx = v0 + R(kx) * dv, vy = v0 + R(ky) * dv;
-    R L = R(0), q0 = R(0);
-    if (fsrc) L = transport_at<S, R>(fsrc, o0, o, k, vx, vy, idx, idy, epsw, q0);
-    const R base = base_is_src ? q0 : ld(sbase + o0 + k);
-    const R fs = base + cL * L;
-    sfs[k] = fs;
-    sL[k] = L;
-    sc0[k] = q0;
-    m[0] += fs;
-    m[1] += vx * fs;
-    m[2] += vy * fs;
-    m[3] += vx * vx * fs;
-    m[4] += vx * vy * fs;
-    m[5] += vy * vy * fs;
-  }
-  block_sum<6>(m, sh.red, sh.tot);
-
-  const bool relax = A.h_coef > 0.0;
-  const bool proj = relax || A.need_q;
-  if (threadIdx.x == 0) {
-    double mom[6];
+  NodeIter<R> it(lane, g.nv, v0, dv);
+  while (it.k < g.nvv) {
+    int kk[kBatch];
+    bool val[kBatch];
+    R vx[kBatch], vy[kBatch];
 #pragma unroll
-    for (int n = 0; n < 6; ++n) mom[n] = g.w * sh.tot[n];
-    const double nu = V.m.tau / V.eps[c];
-    sh.nu = nu;
-    sh.h = A.h_coef * nu;
-    int ok = 1;
-    if (proj) ok = cell_tensor(sh, mom, V.m.beta, sh.h, relax) ? 1 : 0;
-    sh.ok = ok;
-    // conserved variables of f* = those of f^(i) (the relaxation conserves them)
-    sh.U[0] = mom[0];
-    sh.U[1] = mom[1];
-    sh.U[2] = mom[2];
-    sh.U[3] = 0.5 * (mom[3] + mom[5]);
-  }
-  __syncthreads();
-  if (proj && sh.ok) gauss_project<R>(g, sh, sG);
-  if (proj && threadIdx.x == 0 && !sh.ok) report_error(V.err, kErrNonRealizable, c);
-
-  // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
-  const bool doproj = proj && sh.ok;
-  R a[6];
-#pragma unroll
-  for (int n = 0; n < 6; ++n) a[n] = (R)sh.a[n];
-  const R h = (R)sh.h, inv1h = R(1) / (R(1) + h), nu = (R)sh.nu;
-  S* fout = (S*)A.f_out;
-  for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-    const R fs = sfs[k], L = sL[k];
-    R fnew = fs, Q = R(0);
-    if (doproj) {
-      const R Gh = ghat_at<R>(g, sh, a, sG[k], k);
-      // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
-      if (relax) fnew = (fs + h * Gh) * inv1h;
-      Q = nu * (Gh - fs) * inv1h;
+    for (int u = 0; u < kBatch; ++u) {
+      kk[u] = it.k;
+      val[u] = it.k < g.nvv;
+      vx[u] = it.vx();
+      vy[u] = it.vy();
+      it.next();
     }
-    if (fout) st(fout + o0 + k, fnew);
-    for (int t = 0; t < A.nacc; ++t) {
-      const S* ai = (const S*)A.acc_in[t];
-      const R base = ai == fsrc ? sc0[k] : ldc(ai + o0 + k);
-      st((S*)A.acc_out[t] + o0 + k, base + (R)A.acc_cL[t] * L + (R)A.acc_cQ[t] * Q);
+    R q[kBatch][7], bs[kBatch], ai[kBatch][3];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (!val[u]) continue;
+      const int k = kk[u];
+      if (has_src) {
+        stencil_load<S, R>(fsrc, o0, o, k, vx[u] > R(0), vy[u] > R(0), q[u]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 7; ++e) q[u][e] = R(0);
+      }
+      bs[u] = base_is_src ? q[u][0] : ld(sbase + o0 + k);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t < nacc) ai[u][t] = asrc[t] ? q[u][0] : ld(ain[t] + o0 + k);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (!val[u]) continue;
+      const int k = kk[u];
+      const R L = has_src ? transport_of(q[u], vx[u], vy[u], idx, idy, epsw) : R(0);
+      const R fs = bs[u] + cL * L;
+      if (proj) {
+        sfs[k] = fs;
+      } else if (has_out) {
+        // no collision term: f = f*, Q = 0
+        st(fout + o0 + k, fs);
+      }
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t < nacc) st(aout[t] + o0 + k, ai[u][t] + aL[t] * L);
+      const R cx = vx[u] - u0x, cy = vy[u] - u0y;
+      m[0] += fs;
+      m[1] += cx * fs;
+      m[2] += cy * fs;
+      m[3] += cx * cx * fs;
+      m[4] += cx * cy * fs;
+      m[5] += cy * cy * fs;
     }
   }
-  if (threadIdx.x == 0) {
+#pragma unroll
+  for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
+  double Uc[4];
+  cons_from_sums(m, u0x, u0y, g.w, Uc);
+  if (lane == 0) {
     const size_t nc = g.nc;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? sh.U[q] : A.Un[q * nc + c];
+    for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
   }
-}
+  if (!proj) return;
 
-// Buffer cell of a stage: Euler update (thread 0), then f := M_hat[U]
-// (Eq. Coupling_FluKin) over the velocities when filling is on.
-template <typename S>
-__device__ void buffer_cell(const StageArgs& A, const View& V, int c, CellShared& sh,
-                            typename Real<S>::T* sm) {
-  using R = typename Real<S>::T;
-  const Geo& g = V.g;
-  if (threadIdx.x == 0) {
-    double Uc[4];
-    euler_cell<R>(A, V, c, Uc);
-    if (!A.hoc) {
+  const double nu_d = V.m.tau / V.eps[c];
+  const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
+  CellPar<R> P;
+  bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, relax, P);
+  if (ok) ok = project<R>(g, lane, P);
+  if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
+
+  // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
+  const R inv1h = R(1) / (R(1) + h);
+  NodeIter<R> jt(lane, g.nv, v0, dv);
+  while (jt.k < g.nvv) {
+    int kk[kBatch];
+    bool val[kBatch];
+    R vx[kBatch], vy[kBatch], pa[kBatch][3], fs[kBatch];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Uc[q] = A.Un[(size_t)q * g.nc + c];
+    for (int u = 0; u < kBatch; ++u) {
+      kk[u] = jt.k;
+      val[u] = jt.k < g.nvv;
+      vx[u] = jt.vx();
+      vy[u] = jt.vy();
+      jt.next();
     }
-    double rho, ux, uy, T;
-    prim_of(Uc, rho, ux, uy, T);
-    sh.ok = A.fill ? (cell_maxwell(sh, rho, ux, uy, T) ? 1 : 0) : 1;
-  }
-  __syncthreads();
-  if (!A.fill) return;
-  if (!sh.ok) {
-    if (threadIdx.x == 0) report_error(V.err, kErrNonRealizable, c);
-    return;
-  }
-  R* sG = sm;
-  gauss_project<R>(g, sh, sG);
-  R a[6];
 #pragma unroll
-  for (int n = 0; n < 6; ++n) a[n] = (R)sh.a[n];
-  S* fout = (S*)A.f_out;
-  const size_t o0 = (size_t)c * g.nvv;
-  for (int k = threadIdx.x; k < g.nvv; k += kThreads) st(fout + o0 + k, ghat_at<R>(g, sh, a, sG[k], k));
+    for (int u = 0; u < kBatch; ++u) {
+      if (!val[u]) continue;
+      fs[u] = sfs[kk[u]];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t < nacc) pa[u][t] = ldc(aout[t] + o0 + kk[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (!val[u]) continue;
+      const int k = kk[u];
+      R fnew = fs[u], Q = R(0);
+      if (ok) {
+        const R Gh = ghat(P, vx[u] - P.ux, vy[u] - P.uy);
+        // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
+        if (relax) fnew = (fs[u] + h * Gh) * inv1h;
+        Q = nu * (Gh - fs[u]) * inv1h;
+      }
+      if (has_out) st(fout + o0 + k, fnew);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t < nacc) st(aout[t] + o0 + k, pa[u][t] + aQ[t] * Q);
+    }
+  }
 }
 
+// Writes f := M_hat[U] (the discrete Maxwellian, Eq. Coupling_FluKin) into
+// cell c of f, one warp.  Returns false for a non-realizable U.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A, View V) {
+ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&U)[4]) {
+  using R = typename Real<S>::T;
+  double rho, ux, uy, T;
+  prim_of(U, rho, ux, uy, T);
+  CellPar<R> P;
+  if (!maxwell_params<R>(rho, ux, uy, T, P) || !project<R>(g, lane, P)) return false;
+  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const size_t o0 = (size_t)c * g.nvv;
+  NodeIter<R> it(lane, g.nv, v0, dv);
+#pragma unroll 2
+  for (; it.k < g.nvv; it.next()) st(f + o0 + it.k, ghat(P, it.vx() - P.ux, it.vy() - P.uy));
+  return true;
+}
+
+// Buffer cell of a stage: Euler update (lane 0), then f := M_hat[U] over the
+// velocities when filling is on.
+template <typename S>
+ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
+  using R = typename Real<S>::T;
+  double Uc[4] = {0, 0, 0, 0};
+  if (lane == 0) euler_cell<R>(A, V, c, Uc);
+  if (!A.fill) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Uc[q] = __shfl_sync(0xffffffffu, Uc[q], 0);
+  if (!A.hoc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Uc[q] = A.Un[(size_t)q * V.g.nc + c];
+  }
+  if (!fill_maxwell<S>((S*)A.f_out, V.g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
+}
+
+#ifndef ESBGK_STAGE_MIN_BLOCKS
+#define ESBGK_STAGE_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
+#endif
+template <typename S, int M>
+__global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ CellShared sh;
-  R* sm = reinterpret_cast<R*>(dsm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool proj = A.h_coef > 0.0 || A.need_q;
+  R* sfs = reinterpret_cast<R*>(dsm) + (proj ? (size_t)warp * V.g.nvv : 0);
   const int nK = V.counts[0], nB = V.counts[1], nF = V.counts[2];
-  const int nFc = (nF + kThreads - 1) / kThreads;
+  const int nFc = (nF + 31) / 32;
   const int total = nK + nB + nFc;
   long long mine = 0, fills = 0;
-  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
     if (u < nK) {
-      kinetic_cell<S>(A, V, V.klist[u], sh, sm);
+      kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
       ++mine;
     } else if (u < nK + nB) {
-      buffer_cell<S>(A, V, V.blist[u - nK], sh, sm);
+      buffer_cell<S>(A, V, V.blist[u - nK], lane);
       fills += A.fill ? 1 : 0;
     } else {
-      const int q = (u - nK - nB) * kThreads + threadIdx.x;
+      const int q = (u - nK - nB) * 32 + lane;
       if (q < nF) {
         double Uc[4];
         euler_cell<R>(A, V, V.flist[q], Uc);
       }
     }
-    __syncthreads();
   }
-  if (threadIdx.x == 0 && A.ctr) {
+  if (lane == 0 && A.ctr) {
     if (mine && A.f_src) atomicAdd((unsigned long long*)A.ctr, (unsigned long long)mine);
     if (fills) atomicAdd((unsigned long long*)A.ctr + 1, (unsigned long long)fills);
   }
@@ -485,192 +664,143 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A, View V) {
 // Fill f := M_hat[U] in the cells of two lists and copy U^n -> U^(1) in all
 // cells (start of a step), and remember the regime map.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) prep_kernel(PrepArgs P, View V) {
-  using R = typename Real<S>::T;
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ CellShared sh;
-  R* sG = reinterpret_cast<R*>(dsm);
+__global__ void __launch_bounds__(kCellThreads) prep_kernel(PrepArgs P, View V) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const Geo& g = V.g;
   const int n1 = P.count1 ? *P.count1 : 0, n2 = P.count2 ? *P.count2 : 0;
-  const int nCopy = P.copy_to ? (g.nc + kThreads - 1) / kThreads : 0;
+  const int nCopy = P.copy_to ? (g.nc + 31) / 32 : 0;
   const int total = n1 + n2 + nCopy;
   S* f = (S*)P.f;
-  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
     if (u < n1 + n2) {
       const int c = u < n1 ? P.list1[u] : P.list2[u - n1];
-      if (threadIdx.x == 0) {
-        double Uc[4];
+      double Uc[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + c];
-        double rho, ux, uy, T;
-        prim_of(Uc, rho, ux, uy, T);
-        sh.ok = cell_maxwell(sh, rho, ux, uy, T) ? 1 : 0;
-        if (!sh.ok) report_error(V.err, kErrNonRealizable, c);
-      }
-      __syncthreads();
-      if (sh.ok) {
-        gauss_project<R>(g, sh, sG);
-        R a[6];
-#pragma unroll
-        for (int n = 0; n < 6; ++n) a[n] = (R)sh.a[n];
-        const size_t o0 = (size_t)c * g.nvv;
-        for (int k = threadIdx.x; k < g.nvv; k += kThreads) st(f + o0 + k, ghat_at<R>(g, sh, a, sG[k], k));
-      }
+      for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + c];
+      if (!fill_maxwell<S>(f, g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
     } else {
-      const int c = (u - n1 - n2) * kThreads + threadIdx.x;
+      const int c = (u - n1 - n2) * 32 + lane;
       if (c < g.nc) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) P.copy_to[(size_t)q * g.nc + c] = P.U[(size_t)q * g.nc + c];
         if (P.flags_prev) P.flags_prev[c] = V.flags[c];
       }
     }
-    __syncthreads();
   }
+}
+
+// Moments of cell c of f into sf (when given) and m (raw sums about u0).
+template <typename S>
+ESBGK_DEV void load_moments(const S* f, const Geo& g, int c, int lane, typename Real<S>::T u0x,
+                            typename Real<S>::T u0y, typename Real<S>::T* sf, typename Real<S>::T (&m)[6]) {
+  using R = typename Real<S>::T;
+  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const size_t o0 = (size_t)c * g.nvv;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) m[n] = R(0);
+  NodeIter<R> it(lane, g.nv, v0, dv);
+#pragma unroll 2
+  for (; it.k < g.nvv; it.next()) {
+    const R x = ld(f + o0 + it.k);
+    if (sf) sf[it.k] = x;
+    const R cx = it.vx() - u0x, cy = it.vy() - u0y;
+    m[0] += x;
+    m[1] += cx * x;
+    m[2] += cy * x;
+    m[3] += cx * cx * x;
+    m[4] += cx * cy * x;
+    m[5] += cy * cy * x;
+  }
+#pragma unroll
+  for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
 }
 
 // ---------------------------------------------------------------------------
 // L1 deviation ||f - M_hat[f]||_{L1_v} of the kinetic cells (Eq. eqKintoFluid1).
 template <typename S>
-__global__ void __launch_bounds__(kThreads) l1_kernel(const void* fptr, double* L1, View V) {
+__global__ void __launch_bounds__(kCellThreads) l1_kernel(const void* fptr, const double* U, double* L1, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ CellShared sh;
-  R* sf = reinterpret_cast<R*>(dsm);
-  R* sG = sf + V.g.nvv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const Geo& g = V.g;
+  R* sf = reinterpret_cast<R*>(dsm) + (size_t)warp * g.nvv;
   const S* f = (const S*)fptr;
   const int nK = V.counts[0];
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
-  for (int u = blockIdx.x; u < nK; u += gridDim.x) {
+  for (int u = blockIdx.x * nwarps + warp; u < nK; u += gridDim.x * nwarps) {
     const int c = V.klist[u];
-    const size_t o0 = (size_t)c * g.nvv;
-    R m[6];
-#pragma unroll
-    for (int n = 0; n < 6; ++n) m[n] = R(0);
-    for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-      const R vx = v0 + R(k % g.nv) * dv, vy = v0 + R(k / g.nv) * dv;
-      const R x = ld(f + o0 + k);
-      sf[k] = x;
-      m[0] += x;
-      m[1] += vx * x;
-      m[2] += vy * x;
-      m[3] += vx * vx * x;
-      m[4] += vx * vy * x;
-      m[5] += vy * vy * x;
+    R u0x, u0y, m[6];
+    ref_velocity(U, g.nc, c, u0x, u0y);
+    load_moments<S>(f, g, c, lane, u0x, u0y, sf, m);
+    // Maxwellian of f's own moments: the ES tensor with beta = 0
+    CellPar<R> P;
+    bool ok = es_params<R>(m, u0x, u0y, (R)g.w, R(0), R(0), false, P);
+    if (ok) ok = project<R>(g, lane, P);
+    if (!ok) {
+      if (lane == 0) report_error(V.err, kErrNonRealizable, c);
+      continue;
     }
-    block_sum<6>(m, sh.red, sh.tot);
-    if (threadIdx.x == 0) {
-      double mom[6];
-#pragma unroll
-      for (int n = 0; n < 6; ++n) mom[n] = g.w * sh.tot[n];
-      // Maxwellian of f's own moments: the ES tensor with beta = 0
-      sh.ok = cell_tensor(sh, mom, 0.0, 0.0, false) ? 1 : 0;
-      if (!sh.ok) report_error(V.err, kErrNonRealizable, c);
-    }
-    __syncthreads();
-    if (sh.ok) {
-      gauss_project<R>(g, sh, sG);
-      R a[6];
-#pragma unroll
-      for (int n = 0; n < 6; ++n) a[n] = (R)sh.a[n];
-      R s[1] = {R(0)};
-      for (int k = threadIdx.x; k < g.nvv; k += kThreads) s[0] += fabs(sf[k] - ghat_at<R>(g, sh, a, sG[k], k));
-      block_sum<1>(s, sh.red, sh.tot);
-      if (threadIdx.x == 0) L1[c] = g.w * sh.tot[0];
-    }
-    __syncthreads();
+    R s = R(0);
+    NodeIter<R> it(lane, g.nv, v0, dv);
+#pragma unroll 2
+    for (; it.k < g.nvv; it.next()) s += rabs(sf[it.k] - ghat(P, it.vx() - P.ux, it.vy() - P.uy));
+    s = warp_sum(s);
+    if (lane == 0) L1[c] = g.w * (double)s;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Relaxation of independent cells (entry point esbgk_relax_cells).
 template <typename S>
-__global__ void __launch_bounds__(kThreads) relax_cells_kernel(const S* fstar, const double* h, int n, Geo g,
-                                                                double beta, S* fout, S* gout) {
+__global__ void __launch_bounds__(kCellThreads) relax_cells_kernel(const S* fstar, const double* h, int n, Geo g,
+                                                                    double beta, S* fout, S* gout) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ CellShared sh;
-  R* sf = reinterpret_cast<R*>(dsm);
-  R* sG = sf + g.nvv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  R* sf = reinterpret_cast<R*>(dsm) + (size_t)warp * g.nvv;
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
-  for (int c = blockIdx.x; c < n; c += gridDim.x) {
+  for (int c = blockIdx.x * nwarps + warp; c < n; c += gridDim.x * nwarps) {
     const size_t o0 = (size_t)c * g.nvv;
     R m[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) m[q] = R(0);
-    for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-      const R vx = v0 + R(k % g.nv) * dv, vy = v0 + R(k / g.nv) * dv;
-      const R x = ld(fstar + o0 + k);
-      sf[k] = x;
-      m[0] += x;
-      m[1] += vx * x;
-      m[2] += vy * x;
-      m[3] += vx * vx * x;
-      m[4] += vx * vy * x;
-      m[5] += vy * vy * x;
-    }
-    block_sum<6>(m, sh.red, sh.tot);
-    if (threadIdx.x == 0) {
-      double mom[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) mom[q] = g.w * sh.tot[q];
-      sh.h = h[c];
-      sh.ok = cell_tensor(sh, mom, beta, sh.h, true) ? 1 : 0;
-    }
-    __syncthreads();
-    if (sh.ok) gauss_project<R>(g, sh, sG);
+    load_moments<S>(fstar, g, c, lane, R(0), R(0), sf, m);
+    const R hh = (R)h[c];
+    CellPar<R> P;
+    bool ok = es_params<R>(m, R(0), R(0), (R)g.w, (R)beta, hh, true, P);
+    if (ok) ok = project<R>(g, lane, P);
     const R nan = R(__int_as_float(0x7fc00000));
-    R a[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) a[q] = (R)sh.a[q];
-    const R hh = (R)sh.h, inv1h = R(1) / (R(1) + hh);
-    for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-      if (sh.ok) {
-        const R Gh = ghat_at<R>(g, sh, a, sG[k], k);
-        st(fout + o0 + k, (sf[k] + hh * Gh) * inv1h);
-        st(gout + o0 + k, Gh);
+    const R inv1h = R(1) / (R(1) + hh);
+    NodeIter<R> it(lane, g.nv, v0, dv);
+    for (; it.k < g.nvv; it.next()) {
+      if (ok) {
+        const R Gh = ghat(P, it.vx() - P.ux, it.vy() - P.uy);
+        st(fout + o0 + it.k, (sf[it.k] + hh * Gh) * inv1h);
+        st(gout + o0 + it.k, Gh);
       } else {
-        st(fout + o0 + k, nan);
-        st(gout + o0 + k, nan);
+        st(fout + o0 + it.k, nan);
+        st(gout + o0 + it.k, nan);
       }
     }
-    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
 // U := moments(f) in the kinetic cells (Eq. Coupling_KinFlu).
 template <typename S>
-__global__ void __launch_bounds__(kThreads) moments_kernel(const void* fptr, double* U, View V) {
+__global__ void __launch_bounds__(kCellThreads) moments_kernel(const void* fptr, double* U, View V) {
   using R = typename Real<S>::T;
-  __shared__ CellShared sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const Geo& g = V.g;
   const S* f = (const S*)fptr;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
-  for (int u = blockIdx.x; u < V.counts[0]; u += gridDim.x) {
+  for (int u = blockIdx.x * nwarps + warp; u < V.counts[0]; u += gridDim.x * nwarps) {
     const int c = V.klist[u];
-    const size_t o0 = (size_t)c * g.nvv;
     R m[6];
+    load_moments<S>(f, g, c, lane, R(0), R(0), nullptr, m);
+    double Uc[4];
+    cons_from_sums(m, R(0), R(0), g.w, Uc);
+    if (lane == 0) {
 #pragma unroll
-    for (int n = 0; n < 6; ++n) m[n] = R(0);
-    for (int k = threadIdx.x; k < g.nvv; k += kThreads) {
-      const R vx = v0 + R(k % g.nv) * dv, vy = v0 + R(k / g.nv) * dv;
-      const R x = ld(f + o0 + k);
-      m[0] += x;
-      m[1] += vx * x;
-      m[2] += vy * x;
-      m[3] += vx * vx * x;
-      m[4] += vx * vy * x;
-      m[5] += vy * vy * x;
+      for (int q = 0; q < 4; ++q) U[(size_t)q * g.nc + c] = Uc[q];
     }
-    block_sum<6>(m, sh.red, sh.tot);
-    if (threadIdx.x == 0) {
-      U[c] = g.w * sh.tot[0];
-      U[g.nc + c] = g.w * sh.tot[1];
-      U[2 * (size_t)g.nc + c] = g.w * sh.tot[2];
-      U[3 * (size_t)g.nc + c] = 0.5 * g.w * (sh.tot[3] + sh.tot[5]);
-    }
-    __syncthreads();
   }
 }
 
@@ -679,49 +809,107 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(const void* fptr, dou
 template <typename S>
 struct Launch {
   using R = typename Real<S>::T;
-  static size_t smem_stage(const Geo& g) { return 4 * (size_t)g.nvv * sizeof(R); }
-  static size_t smem_two(const Geo& g) { return 2 * (size_t)g.nvv * sizeof(R); }
+  // Warps per CTA so that `arrays` shared arrays of N_v^2 values per warp fit
+  // the device's opt-in shared memory per block (fewer warps for large FP64
+  // velocity grids).
+  static int max_smem() {
+    static int v = 0;
+    if (!v) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (v <= 0) v = 48 * 1024;
+    }
+    return v;
+  }
+  static int warps_for(const Geo& g, int arrays) {
+    const size_t per = (size_t)arrays * g.nvv * sizeof(R);
+    int w = kCellWarps;
+    while (w > 1 && per * w > (size_t)max_smem()) --w;
+    return w;
+  }
+  static size_t smem_for(const Geo& g, int arrays) {
+    return (size_t)warps_for(g, arrays) * arrays * g.nvv * sizeof(R);
+  }
+  // Occupancy (blocks per SM), memoised: the launchers call it on every launch.
+  static int occ(const void* fn, int threads, size_t smem) {
+    struct Entry {
+      const void* fn;
+      int threads;
+      size_t smem;
+      int nb;
+    };
+    static Entry cache[32];
+    static int used = 0;
+    for (int q = 0; q < used; ++q)
+      if (cache[q].fn == fn && cache[q].threads == threads && cache[q].smem == smem) return cache[q].nb;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+    nb = nb < 1 ? 1 : nb;
+    if (used < 32) cache[used++] = {fn, threads, smem, nb};
+    return nb;
+  }
+
+  using StageFn = void (*)(StageArgs, View);
+  static StageFn stage_fn(int m) {
+    switch (m) {
+      case kFirstRelax2: return stage_kernel<S, kFirstRelax2>;
+      case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1>;
+      case kFinal: return stage_kernel<S, kFinal>;
+      case kFirstRelax0: return stage_kernel<S, kFirstRelax0>;
+      default: return stage_kernel<S, kGeneric>;
+    }
+  }
 
   static cudaError_t setup(const Geo& g) {
+    if ((size_t)g.nvv * sizeof(R) > (size_t)max_smem()) return cudaErrorInvalidValue;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(stage_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_stage(g))) != cudaSuccess)
+    const int mx = max_smem();
+    for (int m = 0; m < kNumModes; ++m)
+      if ((e = cudaFuncSetAttribute(stage_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(prep_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_two(g))) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_two(g))) != cudaSuccess)
-      return e;
-    return cudaFuncSetAttribute(relax_cells_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_two(g));
+    return cudaFuncSetAttribute(relax_cells_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   }
   static int blocks_per_sm(const Geo& g) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<S>, kThreads, smem_stage(g));
-    return nb < 1 ? 1 : nb;
+    return occ((const void*)stage_fn(kGeneric), kCellThreads, smem_for(g, 1));
+  }
+  // `grid` is the SM count times blocks_per_sm(); each launch rescales it to
+  // its own footprint.
+  static int rescale(const Geo& g, int grid, const void* fn, int threads, size_t smem) {
+    const int nsm = grid / blocks_per_sm(g);
+    const int g2 = (nsm > 0 ? nsm : 1) * occ(fn, threads, smem);
+    return g2 > 0 ? g2 : grid;
   }
   static void stage(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
-    stage_kernel<S><<<grid, kThreads, smem_stage(V.g), s>>>(A, V);
+    const bool proj = A.h_coef > 0.0 || A.need_q;
+    const int threads = 32 * warps_for(V.g, 1);
+    const size_t smem = proj ? smem_for(V.g, 1) : 0;
+    const StageFn fn = stage_fn(stage_mode(A));
+    fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {
-    prep_kernel<S><<<grid, kThreads, smem_two(V.g), s>>>(P, V);
+    prep_kernel<S><<<rescale(V.g, grid, (const void*)prep_kernel<S>, kCellThreads, 0), kCellThreads, 0, s>>>(P, V);
   }
-  static void l1(const void* f, double* L1, const View& V, int grid, cudaStream_t s) {
-    l1_kernel<S><<<grid, kThreads, smem_two(V.g), s>>>(f, L1, V);
+  static void l1(const void* f, const double* U, double* L1, const View& V, int grid, cudaStream_t s) {
+    const int threads = 32 * warps_for(V.g, 1);
+    const size_t smem = smem_for(V.g, 1);
+    l1_kernel<S><<<rescale(V.g, grid, (const void*)l1_kernel<S>, threads, smem), threads, smem, s>>>(f, U, L1, V);
   }
   static void relax_cells(const void* fs, const double* h, int n, const Geo& g, double beta, void* fo, void* go,
                           int grid, cudaStream_t s) {
-    relax_cells_kernel<S><<<grid, kThreads, smem_two(g), s>>>((const S*)fs, h, n, g, beta, (S*)fo, (S*)go);
+    const int threads = 32 * warps_for(g, 1);
+    relax_cells_kernel<S><<<grid, threads, smem_for(g, 1), s>>>((const S*)fs, h, n, g, beta, (S*)fo, (S*)go);
   }
   static void moments(const void* f, double* U, const View& V, int grid, cudaStream_t s) {
-    moments_kernel<S><<<grid, kThreads, 0, s>>>(f, U, V);
+    moments_kernel<S><<<rescale(V.g, grid, (const void*)moments_kernel<S>, kCellThreads, 0), kCellThreads, 0, s>>>(
+        f, U, V);
   }
 };
 
-#define ESBGK_INSTANTIATE(S, NAME)                                                  \
-  const Launchers NAME = {sizeof(S),          &Launch<S>::setup,  &Launch<S>::blocks_per_sm, \
-                          &Launch<S>::stage,  &Launch<S>::prep,   &Launch<S>::l1,            \
-                          &Launch<S>::relax_cells, &Launch<S>::moments};
+#define ESBGK_INSTANTIATE(S, NAME)                                                                          \
+  const Launchers NAME = {sizeof(S),        &Launch<S>::setup, &Launch<S>::blocks_per_sm, &Launch<S>::stage, \
+                          &Launch<S>::prep, &Launch<S>::l1,    &Launch<S>::relax_cells,   &Launch<S>::moments};
 
 }  // namespace esbgk

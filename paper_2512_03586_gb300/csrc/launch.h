@@ -78,7 +78,7 @@ struct Launchers {
   int (*blocks_per_sm)(const Geo&);
   void (*stage)(const StageArgs&, const View&, int grid, cudaStream_t);
   void (*prep)(const PrepArgs&, const View&, int grid, cudaStream_t);
-  void (*l1)(const void* f, double* L1, const View&, int grid, cudaStream_t);
+  void (*l1)(const void* f, const double* U, double* L1, const View&, int grid, cudaStream_t);
   void (*relax_cells)(const void* fs, const double* h, int n, const Geo&, double beta, void* fo, void* go,
                       int grid, cudaStream_t);
   void (*moments)(const void* f, double* U, const View&, int grid, cudaStream_t);
