@@ -45,15 +45,16 @@ struct CellPar {
 // v0 + R(kx) dv.
 template <typename R>
 struct NodeIter {
-  int k, kx, dkx, nv;
+  int k, kx, dkx, nv, step;
   R fx, fy, fdkx, fdky, fnv, v0, dv;
-  ESBGK_DEV NodeIter(int lane, int nv_, R v0_, R dv_)
-      : k(lane), kx(lane % nv_), dkx(32 % nv_), nv(nv_), fx(R(lane % nv_)), fy(R(lane / nv_)),
-        fdkx(R(32 % nv_)), fdky(R(32 / nv_)), fnv(R(nv_)), v0(v0_), dv(dv_) {}
+  // Nodes start, start + step, ... (step = 32 lanes x nodes per lane).
+  ESBGK_DEV NodeIter(int start, int nv_, R v0_, R dv_, int step_ = 32)
+      : k(start), kx(start % nv_), dkx(step_ % nv_), nv(nv_), step(step_), fx(R(start % nv_)), fy(R(start / nv_)),
+        fdkx(R(step_ % nv_)), fdky(R(step_ / nv_)), fnv(R(nv_)), v0(v0_), dv(dv_) {}
   ESBGK_DEV R vx() const { return v0 + fx * dv; }
   ESBGK_DEV R vy() const { return v0 + fy * dv; }
   ESBGK_DEV void next() {
-    k += 32;
+    k += step;
     kx += dkx;
     fx += fdkx;
     fy += fdky;
@@ -63,6 +64,87 @@ struct NodeIter {
       fy += R(1);
     }
   }
+};
+
+// Vector loads and stores of W consecutive nodes (16 bytes at most).
+template <typename S, int W>
+struct VecIO;
+template <>
+struct VecIO<float, 4> {
+  static ESBGK_DEV void ld(const float* p, float (&v)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  }
+  static ESBGK_DEV void ldc(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  }
+  static ESBGK_DEV void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct VecIO<double, 2> {
+  static ESBGK_DEV void ld(const double* p, double (&v)[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x, v[1] = t.y;
+  }
+  static ESBGK_DEV void ldc(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  }
+  static ESBGK_DEV void st(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <>
+struct VecIO<__nv_bfloat16, 4> {
+  static ESBGK_DEV void unpack(uint2 t, float (&v)[4]) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.y));
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+  static ESBGK_DEV void ld(const __nv_bfloat16* p, float (&v)[4]) {
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), v);
+  }
+  static ESBGK_DEV void ldc(const __nv_bfloat16* p, float (&v)[4]) {
+    unpack(*reinterpret_cast<const uint2*>(p), v);
+  }
+  static ESBGK_DEV void st(__nv_bfloat16* p, const float (&v)[4]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 t;
+    t.x = *reinterpret_cast<const unsigned*>(&a);
+    t.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = t;
+  }
+};
+// shared-memory copies of f* in the arithmetic type
+template <typename R, int W>
+struct SmemVec;
+template <>
+struct SmemVec<float, 4> {
+  static ESBGK_DEV void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static ESBGK_DEV void ld(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  }
+};
+template <>
+struct SmemVec<double, 2> {
+  static ESBGK_DEV void st(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+  static ESBGK_DEV void ld(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  }
+};
+// nodes per vector group for storage type S
+template <typename S>
+struct VecW {
+  static constexpr int value = 16 / sizeof(typename Real<S>::T) < 4 ? 16 / sizeof(typename Real<S>::T) : 4;
 };
 
 // Temperature tensor from the moments of a cell (hypothesis H3 and Sec. 2).
@@ -141,16 +223,18 @@ ESBGK_DEV R gauss_at(const CellPar<R>& P, R cx, R cy) {
 // sums w sum G xi^p eta^q over the nodes, then H a = t - r with
 // H_mn = w sum G psi_m psi_n, r_m = w sum G psi_m, psi = (1, x, y, x^2, xy, y^2).
 // After this G_hat = G (1 + a . psi) has w sum psi G_hat = t.
-template <typename R>
+template <typename R, int W = 1>
 ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
   R s[15];
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
-  NodeIter<R> it(lane, g.nv, v0, dv);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
 #pragma unroll 2
-  for (; it.k < g.nvv; it.next()) {
-    const R cx = it.vx() - P.ux, cy = it.vy() - P.uy;
+  for (; it.k < g.nvv; it.next())
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+    const R cx = it.vx() + R(j) * dv - P.ux, cy = it.vy() - P.uy;
     const R G = gauss_at(P, cx, cy);
     const R x = cx * P.isT, y = cy * P.isT;
     const R Gx = G * x, Gy = G * y;
@@ -591,6 +675,148 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
   }
 }
 
+// Vector form of kinetic_cell for a specialised launch mode: each lane takes W
+// consecutive nodes of one velocity row per iteration (one 16-byte load per
+// stencil array instead of W), which needs N_v divisible by 2W (a group never
+// straddles v_x = 0 or a row end) and 16-byte aligned arrays.
+template <typename S, int M, int W>
+ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs) {
+  using R = typename Real<S>::T;
+  using IO = VecIO<S, W>;
+  using SM = SmemVec<R, W>;
+  using MT = ModeT<M>;
+  const Geo& g = V.g;
+  const unsigned o0 = (unsigned)c * (unsigned)g.nvv;
+  unsigned o[8];
+  stencil_offsets(g, c, o);
+  const S* fsrc = (const S*)A.f_src;
+  const S* sbase = (const S*)A.star_base;
+  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R idx = (R)(1.0 / g.dx), idy = (R)(1.0 / g.dy), epsw = (R)V.m.eps_w, cL = (R)A.star_cL;
+  constexpr bool relax = MT::relax;
+  constexpr int nacc = MT::nacc;
+  S* fout = (S*)A.f_out;
+  const S* ain[nacc > 0 ? nacc : 1];
+  S* aout[nacc > 0 ? nacc : 1];
+  R aL[nacc > 0 ? nacc : 1], aQ[nacc > 0 ? nacc : 1];
+#pragma unroll
+  for (int t = 0; t < nacc; ++t) {
+    ain[t] = (const S*)A.acc_in[t];
+    aout[t] = (S*)A.acc_out[t];
+    aL[t] = (R)A.acc_cL[t];
+    aQ[t] = (R)A.acc_cQ[t];
+  }
+  R u0x, u0y;
+  ref_velocity(A.U_prev, g.nc, c, u0x, u0y);
+
+  // pass 1: transport of the previous stage, f*, moments of f*
+  R m[6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) m[n] = R(0);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+#pragma unroll 2
+  for (; it.k < g.nvv; it.next()) {
+    const unsigned k = it.k;
+    const R vx0 = it.vx(), vy = it.vy();
+    const bool px = vx0 > R(0), py = vy > R(0);
+    R q0[W], ux[W], dx[W], fx[W], uy[W], dy[W], fy[W], bs[W], ai[nacc > 0 ? nacc : 1][W];
+    IO::ld(fsrc + o0 + k, q0);
+    IO::ld(fsrc + (px ? o[1] : o[2]) + k, ux);
+    IO::ld(fsrc + (px ? o[2] : o[1]) + k, dx);
+    IO::ld(fsrc + (px ? o[0] : o[3]) + k, fx);
+    IO::ld(fsrc + (py ? o[5] : o[6]) + k, uy);
+    IO::ld(fsrc + (py ? o[6] : o[5]) + k, dy);
+    IO::ld(fsrc + (py ? o[4] : o[7]) + k, fy);
+    if (MT::base_src) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) bs[j] = q0[j];
+    } else {
+      IO::ld(sbase + o0 + k, bs);
+    }
+#pragma unroll
+    for (int t = 0; t < nacc; ++t) {
+      if (MT::acc_src) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) ai[t][j] = q0[j];
+      } else {
+        IO::ld(ain[t] + o0 + k, ai[t]);
+      }
+    }
+    R fs[W], pa[nacc > 0 ? nacc : 1][W];
+    const R ay = rabs(vy) * idy;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const R vx = vx0 + R(j) * dv;
+      const R Lx = rabs(vx) * idx * (cweno_face(ux[j], q0[j], dx[j], epsw) - cweno_face(fx[j], ux[j], q0[j], epsw));
+      const R Ly = ay * (cweno_face(uy[j], q0[j], dy[j], epsw) - cweno_face(fy[j], uy[j], q0[j], epsw));
+      const R L = Lx + Ly;
+      fs[j] = bs[j] + cL * L;
+#pragma unroll
+      for (int t = 0; t < nacc; ++t) pa[t][j] = ai[t][j] + aL[t] * L;
+      const R cx = vx - u0x, cy = vy - u0y;
+      m[0] += fs[j];
+      m[1] += cx * fs[j];
+      m[2] += cy * fs[j];
+      m[3] += cx * cx * fs[j];
+      m[4] += cx * cy * fs[j];
+      m[5] += cy * cy * fs[j];
+    }
+    if (relax) {
+      SM::st(sfs + k, fs);
+    } else {
+      IO::st(fout + o0 + k, fs);
+    }
+#pragma unroll
+    for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pa[t]);
+  }
+#pragma unroll
+  for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
+  double Uc[4];
+  cons_from_sums(m, u0x, u0y, g.w, Uc);
+  if (lane == 0) {
+    const size_t nc = g.nc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
+  }
+  if (!relax) return;
+
+  const double nu_d = V.m.tau / V.eps[c];
+  const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
+  CellPar<R> P;
+  bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, true, P);
+  if (ok) ok = project<R, W>(g, lane, P);
+  if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
+
+  // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
+  const R inv1h = R(1) / (R(1) + h);
+  NodeIter<R> jt(lane * W, g.nv, v0, dv, 32 * W);
+#pragma unroll 2
+  for (; jt.k < g.nvv; jt.next()) {
+    const unsigned k = jt.k;
+    R fs[W], pa[nacc > 0 ? nacc : 1][W], fn[W];
+    SM::ld(sfs + k, fs);
+#pragma unroll
+    for (int t = 0; t < nacc; ++t) IO::ldc(aout[t] + o0 + k, pa[t]);
+    const R cy = jt.vy() - P.uy, cx0 = jt.vx() - P.ux;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      R Q = R(0);
+      fn[j] = fs[j];
+      if (ok) {
+        const R Gh = ghat(P, cx0 + R(j) * dv, cy);
+        // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
+        fn[j] = (fs[j] + h * Gh) * inv1h;
+        Q = nu * (Gh - fs[j]) * inv1h;
+      }
+#pragma unroll
+      for (int t = 0; t < nacc; ++t) pa[t][j] += aQ[t] * Q;
+    }
+    IO::st(fout + o0 + k, fn);
+#pragma unroll
+    for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pa[t]);
+  }
+}
+
 // Writes f := M_hat[U] (the discrete Maxwellian, Eq. Coupling_FluKin) into
 // cell c of f, one warp.  Returns false for a non-realizable U.
 template <typename S>
@@ -628,7 +854,7 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 #ifndef ESBGK_STAGE_MIN_BLOCKS
 #define ESBGK_STAGE_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
 #endif
-template <typename S, int M>
+template <typename S, int M, int W>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -641,7 +867,10 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
   long long mine = 0, fills = 0;
   for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
     if (u < nK) {
-      kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
+      if constexpr (W > 1)
+        kinetic_cell_vec<S, M, W>(A, V, V.klist[u], lane, sfs);
+      else
+        kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
       ++mine;
     } else if (u < nK + nB) {
       buffer_cell<S>(A, V, V.blist[u - nK], lane);
@@ -851,14 +1080,26 @@ struct Launch {
   }
 
   using StageFn = void (*)(StageArgs, View);
-  static StageFn stage_fn(int m) {
+  static constexpr int kW = VecW<S>::value;
+  // vec: the vector form (specialised modes only)
+  static StageFn stage_fn(int m, bool vec = false) {
     switch (m) {
-      case kFirstRelax2: return stage_kernel<S, kFirstRelax2>;
-      case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1>;
-      case kFinal: return stage_kernel<S, kFinal>;
-      case kFirstRelax0: return stage_kernel<S, kFirstRelax0>;
-      default: return stage_kernel<S, kGeneric>;
+      case kFirstRelax2: return vec ? stage_kernel<S, kFirstRelax2, kW> : stage_kernel<S, kFirstRelax2, 1>;
+      case kLoadedRelax1: return vec ? stage_kernel<S, kLoadedRelax1, kW> : stage_kernel<S, kLoadedRelax1, 1>;
+      case kFinal: return vec ? stage_kernel<S, kFinal, kW> : stage_kernel<S, kFinal, 1>;
+      case kFirstRelax0: return vec ? stage_kernel<S, kFirstRelax0, kW> : stage_kernel<S, kFirstRelax0, 1>;
+      default: return stage_kernel<S, kGeneric, 1>;
     }
+  }
+  static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+  // The vector form applies when groups of kW nodes stay on one side of
+  // v_x = 0 and inside a row, and every f-sized array is 16-byte aligned.
+  static bool vector_ok(const StageArgs& A, const Geo& g, int mode) {
+    if (mode == kGeneric || g.nv % (2 * kW) != 0) return false;
+    if (!aligned16(A.f_src) || !aligned16(A.star_base) || !aligned16(A.f_out)) return false;
+    for (int t = 0; t < A.nacc; ++t)
+      if (!aligned16(A.acc_in[t]) || !aligned16(A.acc_out[t])) return false;
+    return true;
   }
 
   static cudaError_t setup(const Geo& g) {
@@ -866,8 +1107,10 @@ struct Launch {
     cudaError_t e;
     const int mx = max_smem();
     for (int m = 0; m < kNumModes; ++m)
-      if ((e = cudaFuncSetAttribute(stage_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
-        return e;
+      for (int v = 0; v < 2; ++v)
+        if ((e = cudaFuncSetAttribute(stage_fn(m, v != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+            cudaSuccess)
+          return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
     return cudaFuncSetAttribute(relax_cells_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -886,7 +1129,8 @@ struct Launch {
     const bool proj = A.h_coef > 0.0 || A.need_q;
     const int threads = 32 * warps_for(V.g, 1);
     const size_t smem = proj ? smem_for(V.g, 1) : 0;
-    const StageFn fn = stage_fn(stage_mode(A));
+    const int mode = stage_mode(A);
+    const StageFn fn = stage_fn(mode, vector_ok(A, V.g, mode));
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {

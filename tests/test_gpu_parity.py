@@ -2,9 +2,10 @@
 
 Tolerances: FP64 storage -- relative L1 <= 1e-10 on the macroscopic fields
 (rho, E; momentum relative to rho) and on f; FP32 storage -- <= 1e-5.  Flags
-must be identical except in cells within 1e-6 relative of a threshold
-(lambda_A vs eta, or the L1 deviation vs delta), where the oracle's flag is
-imposed on the library so that the fields stay comparable.
+must be identical except in cells within 1e-6 (FP64) or 1e-3 (FP32 storage)
+relative of a threshold (lambda_A vs eta, or the L1 deviation vs delta),
+where the oracle's flag is imposed on the library so that the fields stay
+comparable.
 """
 
 import numpy as np
@@ -68,7 +69,8 @@ def run_parity(wl, steps, prec="fp64", check_f=True, **over):
             lam_g, l1_g = g.indicators()
             # indicators agree to round-off on the scale of the threshold they
             # are compared with (values far below eta or delta only need to stay below)
-            tol_ind = 1e-9 if prec == "fp64" else 1e-4
+            # FP32 storage: the L1 sum of |f - M| carries ~1e-7 absolute rounding
+            tol_ind = 1e-9 if prec == "fp64" else 1e-3
             eta = P.eta_factor * st.eps
             assert np.all(np.abs(lam_g - lam_o) <= tol_ind * np.maximum(np.abs(lam_o), eta)), "lambda_A"
             dl1 = np.abs(l1_g - l1_o)[st.kin]
@@ -77,7 +79,7 @@ def run_parity(wl, steps, prec="fp64", check_f=True, **over):
             near = (np.abs(lam_o - eta) <= 1e-6 * np.maximum(eta, 1e-300)) | \
                    (st.kin & (np.abs(l1_o - P.delta) <= 1e-6 * P.delta))
             if prec != "fp64":
-                near |= (np.abs(lam_o - eta) <= 1e-4 * eta) | (st.kin & (np.abs(l1_o - P.delta) <= 1e-4 * P.delta))
+                near |= (np.abs(lam_o - eta) <= 1e-3 * eta) | (st.kin & (np.abs(l1_o - P.delta) <= 1e-3 * P.delta))
             assert not (bad & ~near).any(), "flag mismatch away from thresholds at %s" % np.argwhere(bad & ~near)[:5]
             if bad.any():
                 exempt_total += int(bad.sum())
