@@ -125,6 +125,7 @@ struct esbgk_ctx {
   long long* ctr;
   int cur;
   bool have_state, conv_pending;
+  bool l1_fresh;  // L1 holds ||f^n - M_hat||_1 of the kinetic cells (from the last final combination)
   long long steps;
   int status;
   long long bad_cell;
@@ -241,10 +242,11 @@ int compact(esbgk_ctx* X) {
 
 int regime_update(esbgk_ctx* X) {
   const View V = X->view();
-  {
+  if (!X->l1_fresh) {
     Timed t(X, ESBGK_K_L1);
     X->L->l1(X->F[X->cur], X->Un, X->L1, V, X->grid_stage, X->stream);
   }
+  X->l1_fresh = false;
   int r = after_launch(X, "l1 kernel");
   if (r) return r;
   {
@@ -387,13 +389,17 @@ int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
     A.fill = 0;
     A.kin_u_moments = 1;
     A.ctr = X->ctr;
+    // the deviation ||f^{n+1} - M_hat||_1 the next regime update needs
+    A.l1_out = X->sw == ESBGK_SWITCH_PLAIN ? X->L1 : nullptr;
     {
       Timed t(X, ESBGK_K_FINAL);
       X->L->stage(A, V, X->grid_stage, X->stream);
     }
     if ((r = after_launch(X, "final kernel"))) return r;
+    X->l1_fresh = A.l1_out != nullptr;
   } else {
     X->cur = prev_buf;
+    X->l1_fresh = false;
   }
   X->steps += 1;
   return ESBGK_OK;
@@ -559,6 +565,7 @@ int esbgk_set_state(esbgk_ctx* X, const double* rho, const double* ux, const dou
   if ((r = after_launch(X, "initial Maxwellian"))) return r;
   X->have_state = true;
   X->conv_pending = false;
+  X->l1_fresh = false;
   return ESBGK_OK;
 }
 
@@ -578,6 +585,7 @@ int esbgk_set_f(esbgk_ctx* X, const double* f) {
   if (r) return r;
   X->L->moments(X->F[X->cur], X->Un, X->view(), X->grid_stage, X->stream);
   if ((r = after_launch(X, "moments kernel"))) return r;
+  X->l1_fresh = false;
   return cuda_check(X, cudaStreamSynchronize(X->stream), "set_f sync");
 }
 
@@ -616,6 +624,7 @@ int esbgk_set_flags(esbgk_ctx* X, const uint8_t* kinetic) {
   if (!r) r = compact(X);
   if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_flags sync");
   if (!r) X->conv_pending = true;
+  X->l1_fresh = false;
   return r;
 }
 
@@ -890,6 +899,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.cur = 0;
   X.have_state = true;
   X.conv_pending = false;
+  X.l1_fresh = false;
   X.steps = 0;
   X.status = ESBGK_OK;
   X.bad_cell = -1;

@@ -25,6 +25,23 @@ void launch_init_state(const double* prim, const uint8_t* kin_in, double* Un, do
   init_state_kernel<<<(nc + 255) / 256, 256, 0, s>>>(prim, kin_in, Un, eps, flags, flags_prev, nc);
 }
 
+// 1/x and sqrt(x) in float64 for positive normal x: a float estimate refined
+// by two Newton-Raphson steps (the error squares at each step, so 2^-24
+// becomes far below float64 rounding); cheaper than the float64 divide and
+// square-root sequences on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = r * fma(-x, r, 2.0);
+  return r * fma(-x, r, 2.0);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!(x > 0.0)) return 0.0;
+  double y = (double)rsqrtf((float)x);  // y ~ 1/sqrt(x)
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return x * y;
+}
+
 // Regime criteria of Sec. 3.1.2 for one cell.  X = I - S_1 with
 //   S_1 = I - eps D(u) mu/(rho T) - 2/3 (eps kappa/(rho T^{3/2}))^2 grad T grad T^T,
 //   mu/(rho T) = 1/(tau (1-beta)),  kappa/(rho T^{3/2}) = 5/2 /(tau sqrt T),
@@ -42,9 +59,10 @@ __global__ void flags_kernel(View V, const double* __restrict__ Un, const double
   const size_t nc = g.nc;
   auto prim = [&](int cc, double& ux, double& uy, double& T) {
     const double rho = Un[cc], mx = Un[nc + cc], my = Un[2 * nc + cc], E = Un[3 * nc + cc];
-    ux = mx / rho;
-    uy = my / rho;
-    T = (E - 0.5 * rho * (ux * ux + uy * uy)) / rho;
+    const double ir = rcp_nr(rho);
+    ux = mx * ir;
+    uy = my * ir;
+    T = (E - 0.5 * rho * (ux * ux + uy * uy)) * ir;
   };
   double uxE, uyE, TE, uxW, uyW, TW, uxN, uyN, TN, uxS, uyS, TS, ux0, uy0, T0;
   prim(j * g.nx + nb(i + 1, g.nx, g.bcx), uxE, uyE, TE);
@@ -62,13 +80,13 @@ __global__ void flags_kernel(View V, const double* __restrict__ Un, const double
   const double Dxy = dudy + dvdx;
   const double eps = V.eps[c];
   const double c1 = eps / (V.m.tau * (1.0 - V.m.beta));
-  const double kk = 2.5 * eps / (V.m.tau * sqrt(T0));
+  const double kk = 2.5 * eps * rcp_nr(V.m.tau * sqrt_nr(T0));
   const double c2 = (2.0 / 3.0) * kk * kk;
   const double Xxx = c1 * Dxx + c2 * dTdx * dTdx;
   const double Xxy = c1 * Dxy + c2 * dTdx * dTdy;
   const double Xyy = c1 * Dyy + c2 * dTdy * dTdy;
   const double mean = 0.5 * (Xxx + Xyy), half = 0.5 * (Xxx - Xyy);
-  const double lam = fabs(mean) + sqrt(half * half + Xxy * Xxy);
+  const double lam = fabs(mean) + sqrt_nr(half * half + Xxy * Xxy);
   const uint8_t kin = V.flags[c];
   const double l1 = kin ? L1in[c] : 0.0;
   lamA[c] = lam;
@@ -78,7 +96,7 @@ __global__ void flags_kernel(View V, const double* __restrict__ Un, const double
 
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
                   uint8_t* flags_out, cudaStream_t s) {
-  flags_kernel<<<(V.g.nc + 255) / 256, 256, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+  flags_kernel<<<(V.g.nc + 127) / 128, 128, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
 }
 
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
@@ -138,29 +156,52 @@ __device__ int block_exclusive_scan(int v, int* sm, int& total) {
   return before + x - v;
 }
 
+// Each thread owns a run of `chunk` categories (a multiple of 16, so the run
+// is read with 16-byte loads); two passes: count, scan, emit.
+__device__ __forceinline__ void count_cats(uint32_t w, int base, int nc, int (&n)[4]) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int t = (w >> (8 * b)) & 0xff;
+    const bool in = base + b < nc;
+    n[0] += in && (t & 3) == 0;
+    n[1] += in && t == 1;
+    n[2] += in && t == 2;
+    n[3] += in && t == 4;
+  }
+}
+
 __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint8_t* __restrict__ cat, int nc, int* klist,
                                                                int* blist, int* flist, int* clist, int* counts) {
   __shared__ int sm[64];
-  const int chunk = (nc + kScanThreads - 1) / kScanThreads;
+  const int chunk = ((nc + kScanThreads - 1) / kScanThreads + 15) / 16 * 16;
   const int lo = threadIdx.x * chunk;
   const int hi = min(nc, lo + chunk);
+  const uint4* v = reinterpret_cast<const uint4*>(cat);
   int n[4] = {0, 0, 0, 0};
-  for (int c = lo; c < hi; ++c) {
-    const int t = cat[c];
-    n[0] += (t & 3) == 0;
-    n[1] += t == 1;
-    n[2] += t == 2;
-    n[3] += t == 4;
+#pragma unroll 4
+  for (int c = lo; c < hi; c += 16) {
+    const uint4 x = v[c / 16];
+    count_cats(x.x, c, nc, n);
+    count_cats(x.y, c + 4, nc, n);
+    count_cats(x.z, c + 8, nc, n);
+    count_cats(x.w, c + 12, nc, n);
   }
   int off[4], tot[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) off[q] = block_exclusive_scan(n[q], sm, tot[q]);
-  for (int c = lo; c < hi; ++c) {
-    const int t = cat[c];
-    if ((t & 3) == 0) klist[off[0]++] = c;
-    if (t == 1) blist[off[1]++] = c;
-    if (t == 2) flist[off[2]++] = c;
-    if (t == 4) clist[off[3]++] = c;
+  for (int c = lo; c < hi; c += 16) {
+    const uint4 x = v[c / 16];
+    const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const int cc = c + b;
+      if (cc >= nc) break;
+      const int t = (w4[b / 4] >> (8 * (b % 4))) & 0xff;
+      if ((t & 3) == 0) klist[off[0]++] = cc;
+      if (t == 1) blist[off[1]++] = cc;
+      if (t == 2) flist[off[2]++] = cc;
+      if (t == 4) clist[off[3]++] = cc;
+    }
   }
   if (threadIdx.x == 0) {
 #pragma unroll

@@ -469,6 +469,22 @@ ESBGK_DEV R transport_of(const R (&q)[7], R vx, R vy, R idx, R idy, R epsw) {
   return Lx + Ly;
 }
 
+// ||f - M_hat[f]||_{L1_v} of the cell whose node values are in sf and whose raw
+// moment sums about u0 are m (Eq. eqKintoFluid1), one warp; -1 if the
+// moments are not realizable.
+template <typename R, int W>
+ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, const R* sf) {
+  CellPar<R> P;
+  if (!es_params<R>(m, u0x, u0y, (R)g.w, R(0), R(0), false, P) || !project<R, W>(g, lane, P)) return R(-1);
+  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  R s = R(0);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+  for (; it.k < g.nvv; it.next())
+#pragma unroll
+    for (int j = 0; j < W; ++j) s += rabs(sf[it.k + j] - ghat(P, it.vx() + R(j) * dv - P.ux, it.vy() - P.uy));
+  return warp_sum(s) * (R)g.w;
+}
+
 // Compile-time shapes of a kinetic stage launch.  The inner loops test none
 // of these flags when they are fixed at compile time; kGeneric reads them all
 // at run time and serves any other tableau.
@@ -599,9 +615,10 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
       const R fs = bs[u] + cL * L;
       if (proj) {
         sfs[k] = fs;
-      } else if (has_out) {
+      } else {
         // no collision term: f = f*, Q = 0
-        st(fout + o0 + k, fs);
+        if (has_out) st(fout + o0 + k, fs);
+        if (A.l1_out) sfs[k] = fs;
       }
 #pragma unroll
       for (int t = 0; t < 3; ++t)
@@ -624,7 +641,17 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
   }
-  if (!proj) return;
+  if (!proj) {
+    if (A.l1_out) {
+      __syncwarp();
+      const R l1 = l1_deviation<R, 1>(g, lane, m, u0x, u0y, sfs);
+      if (lane == 0) {
+        if (l1 < R(0)) report_error(V.err, kErrNonRealizable, c);
+        A.l1_out[c] = (double)l1;
+      }
+    }
+    return;
+  }
 
   const double nu_d = V.m.tau / V.eps[c];
   const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
@@ -765,6 +792,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
       SM::st(sfs + k, fs);
     } else {
       IO::st(fout + o0 + k, fs);
+      if (A.l1_out) SM::st(sfs + k, fs);
     }
 #pragma unroll
     for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pa[t]);
@@ -778,7 +806,17 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
   }
-  if (!relax) return;
+  if (!relax) {
+    if (A.l1_out) {
+      __syncwarp();
+      const R l1 = l1_deviation<R, W>(g, lane, m, u0x, u0y, sfs);
+      if (lane == 0) {
+        if (l1 < R(0)) report_error(V.err, kErrNonRealizable, c);
+        A.l1_out[c] = (double)l1;
+      }
+    }
+    return;
+  }
 
   const double nu_d = V.m.tau / V.eps[c];
   const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
@@ -859,7 +897,7 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const bool proj = A.h_coef > 0.0 || A.need_q;
+  const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
   R* sfs = reinterpret_cast<R*>(dsm) + (proj ? (size_t)warp * V.g.nvv : 0);
   const int nK = V.counts[0], nB = V.counts[1], nF = V.counts[2];
   const int nFc = (nF + 31) / 32;
@@ -1126,7 +1164,7 @@ struct Launch {
     return g2 > 0 ? g2 : grid;
   }
   static void stage(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
-    const bool proj = A.h_coef > 0.0 || A.need_q;
+    const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
     const int threads = 32 * warps_for(V.g, 1);
     const size_t smem = proj ? smem_for(V.g, 1) : 0;
     const int mode = stage_mode(A);

@@ -30,7 +30,8 @@ struct View {
 //   f     = relax(f*, h = h_coef * nu)            (h_coef > 0), else f*
 //   Q     = nu (G_hat - f)                        (h_coef > 0 or need_q)
 //   acc_out[t] = acc_in[t] + acc_cL[t] L + acc_cQ[t] Q
-//   f_out = f;  U_out = moments(f*) if kin_u_moments else U^n
+//   f_out = f;  U_out = moments(f*) if kin_u_moments else U^n;
+//   l1_out = ||f - M_hat[f]||_{L1_v} when set and there is no collision term
 // For fluid cells: Phi[phi_store] = Phi(U_prev) (phi_store >= 0), then
 //   U_out = U^n - sum_{j < nphi} phi_coef[j] Phi[j]; buffer cells also get
 //   f_out = M_hat[U_out] (hoc) or M_hat[U^n] when `fill`.
@@ -56,6 +57,7 @@ struct StageArgs {
   int fill;
   int kin_u_moments;
   long long* ctr;
+  double* l1_out;  // when set (final combination only): ||f - M_hat[f]||_L1 of the result per kinetic cell
 };
 
 // Start-of-step preparation: f := M_hat[U] in the cells of list1 and list2;
