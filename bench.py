@@ -9,7 +9,7 @@ coupling, final combination).  Metric: kinetic (cell x velocity) stage updates
 per second = sum over steps of K_kinetic * N_v^2 * (transport evaluations).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload riemann|blob|sine] [--prec fp32|fp64|bf16]
+                [--workload riemann|blob|sine|batch] [--prec fp32|fp64|bf16]
 Under torchrun every rank runs an independent replica (seed = rank): weak
 scaling, no collective on the data path.  Prints one JSON line on rank 0.
 """
@@ -100,12 +100,17 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    val, desc, per = oracle_sample(args.workload, args.steps, warmup=args.warmup)
-    wl = make_workload(args.workload, 0)
+    if args.workload == "batch":
+        val, desc, per = batch_oracle_sample(args.steps)
+        cfg = {"workload": "batched form: one case of the 64-case recipe (32x32 cells, 28x28 velocities), "
+                           "FP64 oracle", "prec": "fp64"}
+    else:
+        val, desc, per = oracle_sample(args.workload, args.steps, warmup=args.warmup)
+        cfg = describe(make_workload(args.workload, 0), args.workload, "fp64")
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": describe(wl, args.workload, "fp64"), "impl": "reference",
+           "config": cfg, "impl": "reference",
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -339,13 +344,179 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
+def batch_oracle_sample(steps):
+    """FP64 oracle on a bounded sample of the batched workload: one case of
+    the same recipe on 32 x 32 cells with N_v = 28 (the mean of 16..40)."""
+    import oracle as O
+    wl = W.batched_cases(n_cases=1, seed0=0, sizes=[32], nvs=[28])[0]
+    P = O.Problem(**wl["grid"], **wl["vmesh"], **wl["params"])
+    st = O.init_state(P, **wl["fields"])
+    upd, per = 0, []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st = O.step(P, st, wl["dt"], O.ARS233)
+        per.append(time.perf_counter() - t0)
+        upd += int(st.kin.sum()) * P.nv * P.nv * 3
+    desc = "FP64 numpy oracle, %d ARS(2,3,3) steps of one batched-recipe case on 32x32 cells, 28x28 " \
+           "velocities, plain switch, single-threaded" % steps
+    return upd / sum(per), desc, per
+
+
+def batch_arm(args):
+    """Batched form: 64 independent cases (uneven grids and velocity meshes)
+    advanced by one launch per kernel, replayed as a CUDA graph."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2512_03586_gb300 as G
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cases = W.batched_cases(n_cases=args.cases, seed0=rank * args.cases)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    b = G.BatchSolver([(c["grid"], c["vmesh"], c["params"]) for c in cases], prec=args.prec, device=dev,
+                      stream=stream)
+    for i, c in enumerate(cases):
+        f = c["fields"]
+        b.set_state(i, f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    dts = np.array([c["dt"] for c in cases])
+    tab = G.make_tableau("ars233")
+    threads, ctas = b.autotune(dts, tab)
+    for _ in range(args.warmup):
+        b.step(dts, tab)
+    b.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    c0 = b.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            b.step(dts, tab)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = sum(a.elapsed_time(e) for a, e in ev)
+    b.sync()
+    c1 = b.counters()
+    updates = (c1["element_updates"] - c0["element_updates"]) * 1.0
+    if world > 1:
+        t = torch.tensor([ms, updates], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_max, updates_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, updates_all = ms, updates
+    value = updates_all / (ms_max * 1e-3)
+
+    # per-kernel device times (plain launches with events)
+    k2 = max(3, min(args.steps, 10))
+    b.timing(True)
+    b.timing_read()
+    cb = b.counters()
+    for k in range(k2):
+        flush.fill_(float(k))
+        b.step(dts, tab)
+    tk = b.timing_read()
+    b.timing(False)
+    ca = b.counters()
+    el = ca["element_updates"] - cb["element_updates"]
+    ebytes = ELEM[args.prec]
+    st_ms = tk["stage"][0] + tk["final"][0]
+    st_n = tk["stage"][1] + tk["final"][1]
+    algo_bytes = el * (12 / 3) * ebytes
+    achieved = algo_bytes / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
+    peak, peak_src = measured_peak()
+    # launches per step: l1 offsets + l1 + flags, categorize + compact + offsets, prep, stages
+    launches_per_step = 3 + 3 + 1 + (tk["stage"][1] + tk["final"][1]) / k2
+
+    # end to end: every case's state from pinned host memory, one step, every case's moments back
+    pins = []
+    for i, c in enumerate(cases):
+        nx, ny = c["grid"]["nx"], c["grid"]["ny"]
+        m = b.moments(i)
+        arr = torch.empty((5, nx * ny), dtype=torch.float64).pin_memory().numpy()
+        arr[:4] = m.reshape(4, -1)
+        arr[4] = c["fields"]["eps"].reshape(-1)
+        kin = torch.empty(nx * ny, dtype=torch.uint8).pin_memory().numpy()
+        kin[:] = b.flags(i).reshape(-1)
+        outp = torch.empty((4, ny, nx), dtype=torch.float64).pin_memory().numpy()
+        pins.append((arr, kin, outp))
+    k3 = 3
+    e0 = b.counters()["element_updates"]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k3):
+        for i, (arr, kin, _o) in enumerate(pins):
+            b.set_state(i, arr[0], arr[1], arr[2], arr[3], arr[4], kin)
+        b.step(dts, tab)
+        for i, (_a, _k, outp) in enumerate(pins):
+            b.moments(i, out=outp)
+    t_e2e = time.perf_counter() - t0
+    e_upd = b.counters()["element_updates"] - e0
+    ncells = sum(c["grid"]["nx"] * c["grid"]["ny"] for c in cases)
+    elems = sum(c["grid"]["nx"] * c["grid"]["ny"] * c["vmesh"]["nv"] ** 2 for c in cases)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cv, cdesc, _ = batch_oracle_sample(max(2, args.cpu_steps // 4))
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
+    cfg = {"workload": "batched form: %d independent periodic cases, N_x = N_y in 64..256, N_v in 16..40 on "
+                       "[-8,8]^2, eps log-uniform [1e-4,1e-1], plain switch, ARS(2,3,3), %s storage" % (
+                           len(cases), args.prec),
+           "cases": len(cases), "cells": ncells, "elements": elems, "prec": args.prec,
+           "l2": "flushed (256 MB write) before every timed step; f arrays far exceed L2",
+           "parallelism": "replicas" if world > 1 else "single GPU",
+           "autotuned": {"threads": threads, "ctas_per_sm": ctas}, "cuda_graph": True,
+           "kinetic_fraction_end": c1["kinetic_cells"] / ncells}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic", "config": cfg,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": (achieved / peak) if achieved else None, "traffic": None,
+                        "kernel": "batch_stage_kernel (all cases, fused IMEX stage + final combination)",
+                        "algorithmic_bytes_per_launch": algo_bytes / st_n if st_n else None,
+                        "avg_launch_ms": st_ms / st_n if st_n else None, "peak_source": peak_src,
+                        "bytes_model": "12 f-array accesses per element per step / 3 transport evaluations x %d B"
+                                       % ebytes},
+           "kernel_ms_per_step": {k: v[0] / k2 for k, v in tk.items()},
+           "e2e": {"value": e_upd / t_e2e, "unit": UNIT,
+                   "h2d_bytes_per_step": sum(5 * 8 * c["grid"]["nx"] * c["grid"]["ny"] + c["grid"]["nx"] * c["grid"]["ny"]
+                                             for c in cases),
+                   "d2h_bytes_per_step": 4 * 8 * ncells,
+                   "note": "each step: esbgk_batch_set_state of every case from pinned host arrays, "
+                           "esbgk_batch_step, esbgk_batch_get_moments of every case to pinned host arrays"},
+           "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch"])
+    ap.add_argument("--cases", type=int, default=64, help="cases of the batched workload")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -354,6 +525,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch":
+        batch_arm(args)
     else:
         ours_arm(args)
 

@@ -217,6 +217,90 @@ int esbgk_last_error(esbgk_ctx* ctx, char* buf, size_t n, long long* bad_cell);
 int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax,
                       double beta, int32_t prec, void* f_out, void* g_out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: n independent problems (cases) of uneven sizes advanced
+ * together.  (The paper advances one problem at a time; the batch is a
+ * throughput service.  Each case follows Algorithm 1 and the regime update of
+ * Sec. 3.1.2 as a single context would, through the same per-cell device
+ * code compiled into separate kernels: results agree with a single context
+ * to rounding -- a few units in the last place, which an under-resolved
+ * velocity grid can amplify through the moment system -- not bit for bit.)
+ * Each case is a full problem as above (its own grid, velocity mesh,
+ * parameters, state and regime map); every step runs as one launch per kernel
+ * over all cases -- one persistent stage launch walks the concatenated
+ * compacted work lists (kinetic cells, buffer cells, chunks of 32 fluid cells)
+ * of every case -- and, on a stream other than the legacy default stream, the
+ * launches of a step are captured once into a CUDA graph and replayed.
+ * All cases share the storage precision.  Cases are addressed by index
+ * 0..n-1; per-case host arrays follow the single-problem conventions.
+ * Errors: ESBGK_E_ARG (bad argument, mixed precisions, case index out of
+ * range), ESBGK_E_WORKSPACE (workspace too small or not 256-byte aligned),
+ * ESBGK_E_CUDA, ESBGK_E_NONREALIZABLE (reported by esbgk_batch_sync for the
+ * first case with a device error), ESBGK_E_STATE (a case has no state).
+ * A failed step leaves the batch in the failed state until a set_state. */
+typedef struct esbgk_batch esbgk_batch;
+
+/* Bytes of device workspace for the batch: the sum of the cases' workspaces
+ * plus a few KB of per-case descriptor tables.  0 on invalid input. */
+size_t esbgk_batch_workspace_bytes(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes,
+                                   const esbgk_params* params);
+
+/* Create a batch of n >= 1 cases (arrays grids[n], vmeshes[n], params[n]) on
+ * one caller-owned device workspace (256-byte aligned, owned by the caller
+ * and kept alive until esbgk_batch_destroy) and one stream (NULL = legacy
+ * default stream).  *out receives the handle. */
+int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes,
+                       const esbgk_params* params, void* workspace, size_t workspace_bytes,
+                       void* stream, esbgk_batch** out);
+void esbgk_batch_destroy(esbgk_batch* b);
+
+/* esbgk_set_state for case i. */
+int esbgk_batch_set_state(esbgk_batch* b, int32_t i, const double* rho, const double* ux,
+                          const double* uy, const double* T, const double* eps, const uint8_t* kinetic);
+
+/* One step of every case (esbgk_step semantics: the regime update of
+ * plain-switch cases, then Algorithm 1): dt[n] host array of case time steps,
+ * one tableau for all.  use_graph != 0 replays a captured CUDA graph of the
+ * step when the stream allows capture (not the legacy default stream).
+ * Asynchronous: errors of the kernels surface at esbgk_batch_sync or at a
+ * read-back. */
+int esbgk_batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, int32_t use_graph);
+
+/* Per-case read-back (as esbgk_get_moments, esbgk_get_cons, esbgk_get_flags). */
+int esbgk_batch_get_moments(esbgk_batch* b, int32_t i, double* rho, double* ux, double* uy, double* T);
+int esbgk_batch_get_cons(esbgk_batch* b, int32_t i, double* U);
+int esbgk_batch_get_flags(esbgk_batch* b, int32_t i, uint8_t* kinetic);
+
+/* Work counters summed over cases (see esbgk_counters): kinetic cell
+ * updates (transport evaluations of kinetic cells), the same weighted by each
+ * case's N_v^2 (kinetic (cell x velocity) element updates), batched steps,
+ * and the current number of kinetic cells.  Any pointer may be NULL. */
+int esbgk_batch_counters(esbgk_batch* b, long long* kinetic_cell_updates, long long* element_updates,
+                         long long* steps, long long* kinetic_cells);
+
+/* Autotuner of the batched stage launch.  For each candidate launch shape
+ * (32, 64 or 128 threads per CTA, within the shared-memory limit, x 0, 2, 4
+ * or 8 CTAs per SM, 0 meaning as many as fit) it runs one untimed and two
+ * timed steps (dt, tab) on the current state -- so it advances the batch by
+ * three steps per candidate -- and keeps the fastest shape for later steps.
+ * Reports the choice (either pointer may be NULL). */
+int esbgk_batch_autotune(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, int32_t* threads,
+                         int32_t* ctas_per_sm);
+
+/* Wait for the stream; report a pending device error of any case. */
+int esbgk_batch_sync(esbgk_batch* b);
+
+/* Per-launch timing of the batched step, as esbgk_timing / esbgk_timing_read
+ * (the same kernel classes; a class sums the launches of all cases).  While
+ * enabled, steps run as plain launches (no graph replay). */
+int esbgk_batch_timing(esbgk_batch* b, int32_t enable);
+int esbgk_batch_timing_read(esbgk_batch* b, double* ms, long long* launches, int32_t n);
+
+/* Message of the last failure of the batch or of one of its cases into
+ * buf[n] (NUL-terminated); *case_index (may be NULL) receives the failing
+ * case or -1. */
+int esbgk_batch_last_error(esbgk_batch* b, char* buf, size_t n, int32_t* case_index);
+
 /* Allocation-free stepping of an all-kinetic problem.  (The paper has no
  * counterpart: this is a service for callers.)
  *

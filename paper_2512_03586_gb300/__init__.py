@@ -37,7 +37,7 @@ SWITCH = {"frozen": 0, "plain": 1}
 COUPLING = {"stage": 0, "step": 1}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 
-__all__ = ["Solver", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
+__all__ = ["Solver", "BatchSolver", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
 
 _ALPHA = (3.0 + 3.0 ** 0.5) / 6.0
 #: ARS(2,3,3) (Sec. 3.4): explicit (At, bt), implicit (A, b), alpha = (3+sqrt 3)/6.
@@ -84,6 +84,18 @@ def _f64(a, n):
     return a
 
 
+def _structs(_abi, grid, vmesh, params, prec):
+    g = _abi.Grid(int(grid["nx"]), int(grid["ny"]), float(grid.get("x0", 0.0)), float(grid.get("x1", 1.0)),
+                  float(grid.get("y0", 0.0)), float(grid.get("y1", 1.0)), BC[grid.get("bc_x", "periodic")],
+                  BC[grid.get("bc_y", "periodic")])
+    v = _abi.VMesh(int(vmesh["nv"]), float(vmesh["vmax"]))
+    p = params
+    q = _abi.Params(float(p.get("beta", -0.5)), float(p.get("tau", 1.0)), float(p.get("eta_factor", 1.0)),
+                    float(p.get("delta", 1e-3)), float(p.get("cweno_eps", 1e-6)),
+                    SWITCH[p.get("switch", "frozen")], COUPLING[p.get("coupling", "stage")], PREC[prec])
+    return g, v, q
+
+
 class Solver:
     """One problem on one GPU: wraps esbgk_create / esbgk_* on a torch workspace.
 
@@ -98,14 +110,7 @@ class Solver:
         _abi = _lib()
         self._abi = _abi
         self.torch = torch
-        self.grid = _abi.Grid(int(grid["nx"]), int(grid["ny"]), float(grid.get("x0", 0.0)), float(grid.get("x1", 1.0)),
-                         float(grid.get("y0", 0.0)), float(grid.get("y1", 1.0)), BC[grid.get("bc_x", "periodic")],
-                         BC[grid.get("bc_y", "periodic")])
-        self.vmesh = _abi.VMesh(int(vmesh["nv"]), float(vmesh["vmax"]))
-        p = params
-        self.params = _abi.Params(float(p.get("beta", -0.5)), float(p.get("tau", 1.0)), float(p.get("eta_factor", 1.0)),
-                             float(p.get("delta", 1e-3)), float(p.get("cweno_eps", 1e-6)),
-                             SWITCH[p.get("switch", "frozen")], COUPLING[p.get("coupling", "stage")], PREC[prec])
+        self.grid, self.vmesh, self.params = _structs(_abi, grid, vmesh, params, prec)
         self.nx, self.ny, self.nv = self.grid.nx, self.grid.ny, self.vmesh.nv
         self.nc = self.nx * self.ny
         nbytes = _abi.esbgk_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.vmesh), ctypes.byref(self.params))
@@ -225,6 +230,130 @@ class Solver:
 
     def sync(self):
         self._check(self._abi.esbgk_sync(self._ctx), "sync")
+
+
+class BatchSolver:
+    """n independent problems advanced together (esbgk_batch_*): one launch per
+    kernel per step over all cases, replayed as a CUDA graph on a non-default
+    stream.  cases: list of (grid, vmesh, params) dicts as for Solver; all
+    share `prec`."""
+
+    def __init__(self, cases, prec="fp64", device=None, stream=None):
+        import torch
+        _abi = _lib()
+        self._abi = _abi
+        n = len(cases)
+        if n < 1:
+            raise ValueError("need at least one case")
+        self.n = n
+        G = (_abi.Grid * n)()
+        V = (_abi.VMesh * n)()
+        Pp = (_abi.Params * n)()
+        self.shapes = []
+        for i, (grid, vmesh, params) in enumerate(cases):
+            G[i], V[i], Pp[i] = _structs(_abi, grid, vmesh, params, prec)
+            self.shapes.append((G[i].nx, G[i].ny, V[i].nv))
+        self._G, self._V, self._P = G, V, Pp
+        nbytes = _abi.esbgk_batch_workspace_bytes(n, G, V, Pp)
+        if nbytes == 0:
+            raise Error(-1, "invalid batch description")
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._b = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            r = _abi.esbgk_batch_create(n, G, V, Pp, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._b))
+        if r != 0:
+            raise Error(r, "esbgk_batch_create")
+        self.workspace_bytes = nbytes
+
+    def _check(self, r, what):
+        if r != 0:
+            buf = ctypes.create_string_buffer(512)
+            at = ctypes.c_int32(-1)
+            self._abi.esbgk_batch_last_error(self._b, buf, 512, ctypes.byref(at))
+            raise Error(r, "%s (case %d): %s" % (what, at.value, buf.value.decode(errors="replace")))
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._abi.esbgk_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dt(self, dt):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (self.n,)))
+        return d
+
+    def set_state(self, i, rho, ux, uy, T, eps, kin=None):
+        nx, ny, _ = self.shapes[i]
+        arrs = [_f64(a, nx * ny) for a in (rho, ux, uy, T, eps)]
+        k = None if kin is None else np.ascontiguousarray(np.asarray(kin).reshape(-1), dtype=np.uint8)
+        self._check(self._abi.esbgk_batch_set_state(self._b, i, *[_dptr(a) for a in arrs],
+                                                    None if k is None else _u8ptr(k)), "set_state")
+
+    def step(self, dt, tableau="ars233", graph=True):
+        """One step of every case; dt is a scalar or one value per case."""
+        t = tableau if isinstance(tableau, self._abi.Tableau) else make_tableau(tableau)
+        d = self._dt(dt)
+        self._check(self._abi.esbgk_batch_step(self._b, _dptr(d), ctypes.byref(t), int(bool(graph))), "step")
+
+    def autotune(self, dt, tableau="ars233"):
+        """Pick the stage launch shape (advances the batch); returns (threads, ctas_per_sm)."""
+        t = tableau if isinstance(tableau, self._abi.Tableau) else make_tableau(tableau)
+        d = self._dt(dt)
+        th, ct = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._abi.esbgk_batch_autotune(self._b, _dptr(d), ctypes.byref(t), ctypes.byref(th),
+                                                   ctypes.byref(ct)), "autotune")
+        return th.value, ct.value
+
+    def moments(self, i, out=None):
+        nx, ny, _ = self.shapes[i]
+        if out is None:
+            out = np.empty((4, ny, nx))
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 4 * nx * ny
+        o = out.reshape(4, -1)
+        self._check(self._abi.esbgk_batch_get_moments(self._b, i, *[_dptr(o[q]) for q in range(4)]), "get_moments")
+        return out
+
+    def cons(self, i):
+        nx, ny, _ = self.shapes[i]
+        out = np.empty((4, ny, nx))
+        self._check(self._abi.esbgk_batch_get_cons(self._b, i, _dptr(out)), "get_cons")
+        return out
+
+    def flags(self, i):
+        nx, ny, _ = self.shapes[i]
+        out = np.empty((ny, nx), np.uint8)
+        self._check(self._abi.esbgk_batch_get_flags(self._b, i, _u8ptr(out)), "get_flags")
+        return out.astype(bool)
+
+    def counters(self):
+        u, e, s, k = (ctypes.c_longlong() for _ in range(4))
+        self._check(self._abi.esbgk_batch_counters(self._b, ctypes.byref(u), ctypes.byref(e), ctypes.byref(s),
+                                                   ctypes.byref(k)), "counters")
+        return dict(kinetic_cell_updates=u.value, element_updates=e.value, steps=s.value, kinetic_cells=k.value)
+
+    def timing(self, enable=True):
+        """Bracket every batched launch with CUDA events (steps then run
+        without graph replay)."""
+        self._check(self._abi.esbgk_batch_timing(self._b, int(bool(enable))), "timing")
+
+    def timing_read(self):
+        """{kernel class: (milliseconds, launches)} since the last read."""
+        n = len(self._abi.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(self._abi.esbgk_batch_timing_read(self._b, ms, cnt, n), "timing_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self._abi.KERNEL_CLASSES)}
+
+    def sync(self):
+        self._check(self._abi.esbgk_batch_sync(self._b), "sync")
 
 
 def relax_cells(fstar, h, vmax, beta=-0.5, prec="fp64", stream=None):

@@ -92,6 +92,23 @@ _SIGS = {
     "esbgk_last_error": (I, [P, ctypes.c_char_p, ctypes.c_size_t, LL]),
     "esbgk_relax_cells": (I, [P, D, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                               ctypes.c_int32, P, P, P]),
+    "esbgk_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Grid), ctypes.POINTER(VMesh),
+                                                      ctypes.POINTER(Params)]),
+    "esbgk_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(Grid), ctypes.POINTER(VMesh), ctypes.POINTER(Params),
+                               P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+    "esbgk_batch_destroy": (None, [P]),
+    "esbgk_batch_set_state": (I, [P, ctypes.c_int32, D, D, D, D, D, U8]),
+    "esbgk_batch_step": (I, [P, D, ctypes.POINTER(Tableau), ctypes.c_int32]),
+    "esbgk_batch_get_moments": (I, [P, ctypes.c_int32, D, D, D, D]),
+    "esbgk_batch_get_cons": (I, [P, ctypes.c_int32, D]),
+    "esbgk_batch_get_flags": (I, [P, ctypes.c_int32, U8]),
+    "esbgk_batch_counters": (I, [P, LL, LL, LL, LL]),
+    "esbgk_batch_autotune": (I, [P, D, ctypes.POINTER(Tableau), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_batch_sync": (I, [P]),
+    "esbgk_batch_timing": (I, [P, ctypes.c_int32]),
+    "esbgk_batch_timing_read": (I, [P, D, LL, ctypes.c_int32]),
+    "esbgk_batch_last_error": (I, [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32)]),
     "esbgk_kinetic_steps_noalloc": (I, [ctypes.POINTER(Grid), ctypes.POINTER(VMesh), ctypes.POINTER(Params),
                                         ctypes.c_double, ctypes.POINTER(Tableau), ctypes.c_int32, D, P, D, P]),
 }

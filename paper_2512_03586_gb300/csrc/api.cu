@@ -277,13 +277,23 @@ bool valid_tableau(const esbgk_tableau* t) {
   return true;
 }
 
-// One step of Algorithm 1 with the current regime map.  Stage i (0-based)
-// kernels consume L(f^(i-1)) and fold every explicit and implicit term into
-// running accumulators of the later stages and of the final combination, so
-// that no L_j or Q_j is ever stored: per element and ARS(2,3,3) step this
-// reads f^n, f^(2), D_3, D_fin, f^(3), D_fin' and writes f^(2), D_3, D_fin,
-// f^(3), D_fin', f^{n+1} (12 accesses for 3 transport evaluations).
-int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
+// The launches of one step of Algorithm 1 with the current regime map.
+// Stage i (0-based) kernels consume L(f^(i-1)) and fold every explicit and
+// implicit term into running accumulators of the later stages and of the
+// final combination, so that no L_j or Q_j is ever stored: per element and
+// ARS(2,3,3) step this reads f^n, f^(2), D_3, D_fin, f^(3), D_fin' and writes
+// f^(2), D_3, D_fin, f^(3), D_fin', f^{n+1} (12 accesses for 3 transport
+// evaluations).
+struct StepPlan {
+  PrepArgs prep;
+  int n;                              // launches after prep
+  StageArgs st[kMaxStages + 1];
+  bool fin[kMaxStages + 1];           // final combination (vs a stage)
+  bool shortcut;                      // the last stage is the result
+  int new_cur;
+};
+
+int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
   const int s = T->s;
   bool shortcut = T->bt[s - 1] == 0.0;
   for (int j = 0; j < s && shortcut; ++j)
@@ -300,38 +310,33 @@ int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
   auto slot = [&](int k) { return k - (i0 + 1); };  // k == s means the final combination
   const int slot_fin = s - 1 - i0;
 
-  const View V = X->view();
   int other[2], n = 0;
   for (int q = 0; q < 3; ++q)
     if (q != X->cur) other[n++] = q;
   void* Fc = X->F[X->cur];
 
   // start of step: coupling into f^n (buffer cells, converted cells), U^(0)
-  PrepArgs P{};
+  PrepArgs& P = PL.prep;
+  P = PrepArgs{};
   P.f = Fc;
   P.U = X->Un;
   P.list1 = X->blist;
   P.count1 = X->counts + 1;
   P.list2 = X->conv_pending ? X->clist : nullptr;
   P.count2 = X->conv_pending ? X->counts + 3 : nullptr;
-  P.copy_to = trivial0 ? X->Us[0] : nullptr;
+  // U^(0) = U^n; without a trivial first stage the copy still refreshes flags_prev
+  P.copy_to = trivial0 ? X->Us[0] : X->Us[1];
   P.flags_prev = X->flags_prev;
-  if (!trivial0) {
-    // flags_prev still has to be refreshed: reuse the copy path into Us[1]
-    P.copy_to = X->Us[1];
-  }
-  {
-    Timed t(X, ESBGK_K_PREP);
-    X->L->prep(P, V, X->grid_stage, X->stream);
-  }
-  int r = after_launch(X, "prep kernel");
-  if (r) return r;
-  X->conv_pending = false;
 
+  PL.n = 0;
+  PL.shortcut = shortcut;
   int prev_buf = X->cur;
   for (int i = i0; i < s; ++i) {
     const bool first = i == i0, last = i == s - 1;
-    StageArgs A{};
+    StageArgs& A = PL.st[PL.n];
+    PL.fin[PL.n] = false;
+    ++PL.n;
+    A = StageArgs{};
     A.f_src = i == 0 ? nullptr : X->F[prev_buf];
     A.star_base = first ? Fc : X->ACC[slot(i)];
     A.star_cL = i == 0 ? 0.0 : -dt * T_(T, i, i - 1);
@@ -362,15 +367,13 @@ int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
     A.fill = (last && shortcut) ? 0 : 1;
     A.kin_u_moments = (A.hoc || (last && shortcut)) ? 1 : 0;
     A.ctr = X->ctr;
-    {
-      Timed t(X, ESBGK_K_STAGE);
-      X->L->stage(A, V, X->grid_stage, X->stream);
-    }
-    if ((r = after_launch(X, "stage kernel"))) return r;
     prev_buf = outbuf;
   }
   if (!shortcut) {
-    StageArgs A{};
+    StageArgs& A = PL.st[PL.n];
+    PL.fin[PL.n] = true;
+    ++PL.n;
+    A = StageArgs{};
     A.f_src = X->F[prev_buf];
     A.star_base = X->ACC[slot_fin];
     A.star_cL = -dt * T->bt[s - 1];
@@ -391,17 +394,39 @@ int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
     A.ctr = X->ctr;
     // the deviation ||f^{n+1} - M_hat||_1 the next regime update needs
     A.l1_out = X->sw == ESBGK_SWITCH_PLAIN ? X->L1 : nullptr;
-    {
-      Timed t(X, ESBGK_K_FINAL);
-      X->L->stage(A, V, X->grid_stage, X->stream);
-    }
-    if ((r = after_launch(X, "final kernel"))) return r;
-    X->l1_fresh = A.l1_out != nullptr;
+    PL.new_cur = X->cur;
   } else {
-    X->cur = prev_buf;
-    X->l1_fresh = false;
+    PL.new_cur = prev_buf;
   }
+  return ESBGK_OK;
+}
+
+// Host state after the launches of a planned step.
+void finish_step(esbgk_ctx* X, const StepPlan& PL) {
+  X->conv_pending = false;
+  X->cur = PL.new_cur;
+  X->l1_fresh = !PL.shortcut && PL.st[PL.n - 1].l1_out != nullptr;
   X->steps += 1;
+}
+
+int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
+  StepPlan PL;
+  int r = plan_step(X, dt, T, PL);
+  if (r) return r;
+  const View V = X->view();
+  {
+    Timed t(X, ESBGK_K_PREP);
+    X->L->prep(PL.prep, V, X->grid_stage, X->stream);
+  }
+  if ((r = after_launch(X, "prep kernel"))) return r;
+  for (int q = 0; q < PL.n; ++q) {
+    {
+      Timed t(X, PL.fin[q] ? ESBGK_K_FINAL : ESBGK_K_STAGE);
+      X->L->stage(PL.st[q], V, X->grid_stage, X->stream);
+    }
+    if ((r = after_launch(X, PL.fin[q] ? "final kernel" : "stage kernel"))) return r;
+  }
+  finish_step(X, PL);
   return ESBGK_OK;
 }
 
@@ -787,6 +812,505 @@ int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv,
   const int grid = n < nsm * 8 ? n : nsm * 8;
   L->relax_cells(fstar, h, n, g, beta, f_out, g_out, grid, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? ESBGK_OK : ESBGK_E_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form.
+
+// A batch keeps a few versions of its device tables, each with its own
+// CUDA graph: a tableau whose last stage is the result swaps f buffers every
+// step, so consecutive steps alternate between two sets of descriptors.
+constexpr int kTabSets = 3;
+
+struct BatchTabSet {
+  CaseRegime* reg = nullptr;
+  CaseStage* stage = nullptr;  // [kMaxStages + 1][n]
+  CasePrep* prep = nullptr;
+  std::vector<CaseRegime> h_reg;
+  std::vector<CaseStage> h_stage;
+  std::vector<CasePrep> h_prep;
+  bool valid = false, any_plain = false;
+  int nlaunch = 0;
+  int modes[kMaxStages + 1] = {0};
+  bool fin[kMaxStages + 1] = {false};
+  cudaGraphExec_t gexec = nullptr;
+  long long used = 0;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+};
+
+struct esbgk_batch {
+  int n = 0, prec = 0;
+  const Launchers* L = nullptr;
+  cudaStream_t stream = nullptr;
+  int nsm = 0, total_cells = 0, max_nvv = 0, max_threads = 128;
+  std::vector<esbgk_ctx*> cs;
+  BatchTabSet sets[kTabSets];
+  int* d_cell_off = nullptr;
+  int *d_off_stage = nullptr, *d_off_prep = nullptr, *d_off_l1 = nullptr;
+  int* d_l1_fresh = nullptr;
+  // launch shape of the batched stage kernel (autotuned): threads per CTA and
+  // CTAs per SM (0 = as many as fit)
+  int threads = 128, ctas = 0;
+  long long steps = 0;
+  bool timing = false;  // per-launch events (recorded through case 0's context); disables graphs
+  int status = ESBGK_OK;
+  std::string msg;
+
+  ~esbgk_batch() {
+    for (auto& t : sets) t.drop_graph();
+    for (auto* c : cs) delete c;
+  }
+  void drop_graphs() {
+    for (auto& t : sets) t.drop_graph();
+  }
+  BatchTabs tabs(const BatchTabSet& t) const {
+    BatchTabs T{};
+    T.reg = t.reg;
+    T.cell_off = d_cell_off;
+    T.off_stage = d_off_stage;
+    T.off_prep = d_off_prep;
+    T.off_l1 = d_off_l1;
+    T.n = n;
+    T.total_cells = total_cells;
+    return T;
+  }
+};
+
+namespace {
+
+struct BatchLayout {
+  std::vector<size_t> case_off;
+  size_t reg[kTabSets], stage[kTabSets], prep[kTabSets];
+  size_t cell_off, off_stage, off_prep, off_l1, l1_fresh, total;
+};
+
+bool batch_layout(int n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes, const esbgk_params* params,
+                  BatchLayout& B) {
+  if (n < 1 || !grids || !vmeshes || !params) return false;
+  size_t p = 0;
+  long long cells = 0;
+  B.case_off.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (!valid_inputs(&grids[i], &vmeshes[i], &params[i]) || params[i].prec != params[0].prec) return false;
+    B.case_off[i] = p;
+    p += up(esbgk_workspace_bytes(&grids[i], &vmeshes[i], &params[i]));
+    cells += (long long)grids[i].nx * grids[i].ny;
+  }
+  if (cells >= (1LL << 31)) return false;
+  auto take = [&](size_t bytes) {
+    const size_t at = p;
+    p += up(bytes);
+    return at;
+  };
+  for (int t = 0; t < kTabSets; ++t) {
+    B.reg[t] = take(n * sizeof(CaseRegime));
+    B.stage[t] = take((size_t)(kMaxStages + 1) * n * sizeof(CaseStage));
+    B.prep[t] = take(n * sizeof(CasePrep));
+  }
+  B.cell_off = take((n + 1) * sizeof(int));
+  B.off_stage = take((n + 1) * sizeof(int));
+  B.off_prep = take((n + 1) * sizeof(int));
+  B.off_l1 = take((n + 1) * sizeof(int));
+  B.l1_fresh = take(n * sizeof(int));
+  B.total = p;
+  return true;
+}
+
+int bfail(esbgk_batch* b, int code, const std::string& why) {
+  b->status = code;
+  b->msg = why;
+  return code;
+}
+
+int bcheck(esbgk_batch* b, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return ESBGK_OK;
+  return bfail(b, ESBGK_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+CaseRegime regime_of(esbgk_batch* b, int i) {
+  esbgk_ctx* X = b->cs[i];
+  CaseRegime R;
+  memset(&R, 0, sizeof R);
+  R.V = X->view();
+  R.f = X->F[X->cur];
+  R.Un = X->Un;
+  R.L1 = X->L1;
+  R.lamA = X->lamA;
+  R.flags = X->flags;
+  R.flags_prev = X->flags_prev;
+  R.cat = X->cat;
+  R.klist = X->klist;
+  R.blist = X->blist;
+  R.flist = X->flist;
+  R.clist = X->clist;
+  R.counts = X->counts;
+  R.l1_fresh = b->d_l1_fresh + i;
+  R.plain = X->sw == ESBGK_SWITCH_PLAIN;
+  return R;
+}
+
+// CTAs of a batched stage launch.
+int batch_stage_grid(esbgk_batch* b, int mode) {
+  const int occ = b->L->batch_stage_occupancy(mode, b->max_nvv, b->threads);
+  const int per_sm = b->ctas > 0 && b->ctas < occ ? b->ctas : occ;
+  return b->nsm * per_sm;
+}
+
+// The launches of one batched step: plain kernel launches only (no host
+// synchronisation, no attribute or occupancy queries), so that the sequence
+// can be captured into a CUDA graph.
+void batch_launches(esbgk_batch* b, const BatchTabSet& t, const int* grids) {
+  const BatchTabs T = b->tabs(t);
+  const int grid_small = b->nsm * 4;
+  esbgk_ctx* X0 = b->cs[0];  // holds the timing events (same stream)
+  if (t.any_plain) {
+    {
+      Timed tm(X0, ESBGK_K_L1);
+      launch_batch_l1_offsets(T, b->stream);
+      b->L->batch_l1(t.reg, b->d_off_l1, b->n, b->max_nvv, grid_small, b->stream);
+    }
+    Timed tm(X0, ESBGK_K_FLAGS);
+    launch_batch_flags(T, b->stream);
+  }
+  {
+    Timed tm(X0, ESBGK_K_COMPACT);
+    launch_batch_categorize(T, b->stream);
+    launch_batch_compact(T, b->stream);
+    launch_batch_offsets(T, b->stream);
+  }
+  {
+    Timed tm(X0, ESBGK_K_PREP);
+    b->L->batch_prep(t.prep, b->d_off_prep, b->n, grid_small, b->stream);
+  }
+  for (int j = 0; j < t.nlaunch; ++j) {
+    Timed tm(X0, t.fin[j] ? ESBGK_K_FINAL : ESBGK_K_STAGE);
+    b->L->batch_stage(t.stage + (size_t)j * b->n, b->d_off_stage, b->n, t.modes[j], b->max_nvv, b->threads, grids[j],
+                      b->stream);
+  }
+}
+
+// Plan every case's step, pick (or upload) the matching table set, run the
+// launches (replaying the set's graph when allowed), update the host state.
+int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool use_graph) {
+  const int n = b->n;
+  std::vector<StepPlan> plans(n);
+  bool any_plain = false;
+  for (int i = 0; i < n; ++i) {
+    esbgk_ctx* X = b->cs[i];
+    // the batched regime update runs before the stages of every plain case
+    if (X->sw == ESBGK_SWITCH_PLAIN) X->conv_pending = true;
+    any_plain = any_plain || X->sw == ESBGK_SWITCH_PLAIN;
+    const int r = plan_step(X, dt[i], tab, plans[i]);
+    if (r) return bfail(b, r, X->msg);
+  }
+  const int nl = plans[0].n;
+  std::vector<CaseStage> st((size_t)nl * n);
+  std::vector<CasePrep> pr(n);
+  std::vector<CaseRegime> rg(n);
+  int modes[kMaxStages + 1];
+  for (int j = 0; j < nl; ++j) modes[j] = stage_mode(plans[0].st[j]);
+  for (int i = 0; i < n; ++i) {
+    esbgk_ctx* X = b->cs[i];
+    const View V = X->view();
+    for (int j = 0; j < nl; ++j) {
+      CaseStage& c = st[(size_t)j * n + i];
+      memset(&c, 0, sizeof c);
+      c.V = V;
+      c.A = plans[i].st[j];
+      c.vec = b->L->vector_ok(c.A, X->g) ? 1 : 0;
+      if (stage_mode(c.A) != modes[j]) return bfail(b, ESBGK_E_STATE, "batched cases disagree on a launch shape");
+    }
+    memset(&pr[i], 0, sizeof(CasePrep));
+    pr[i].V = V;
+    pr[i].P = plans[i].prep;
+    rg[i] = regime_of(b, i);
+    rg[i].l1_next = (!plans[i].shortcut && rg[i].plain) ? 1 : 0;
+    rg[i].prep_copy = plans[i].prep.copy_to != nullptr;
+    rg[i].conv = plans[i].prep.list2 != nullptr;
+  }
+  // find the table set with these descriptors, else overwrite the least recently used
+  BatchTabSet* t = nullptr;
+  for (auto& q : b->sets)
+    if (q.valid && q.nlaunch == nl && q.h_stage.size() == st.size() &&
+        !memcmp(q.h_stage.data(), st.data(), st.size() * sizeof(CaseStage)) &&
+        !memcmp(q.h_prep.data(), pr.data(), pr.size() * sizeof(CasePrep)) &&
+        !memcmp(q.h_reg.data(), rg.data(), rg.size() * sizeof(CaseRegime)))
+      t = &q;
+  int r;
+  if (!t) {
+    t = &b->sets[0];
+    for (auto& q : b->sets)
+      if (!q.valid || q.used < t->used) t = &q;
+    // the set may be in use by queued launches: wait, then copy in stream order
+    // and wait again (the host vectors are reused)
+    if ((r = bcheck(b, cudaStreamSynchronize(b->stream), "batch sync"))) return r;
+    t->valid = false;
+    t->drop_graph();
+    const cudaError_t e1 = cudaMemcpyAsync(t->stage, st.data(), st.size() * sizeof(CaseStage), cudaMemcpyHostToDevice,
+                                           b->stream);
+    const cudaError_t e2 = cudaMemcpyAsync(t->prep, pr.data(), pr.size() * sizeof(CasePrep), cudaMemcpyHostToDevice,
+                                           b->stream);
+    const cudaError_t e3 = cudaMemcpyAsync(t->reg, rg.data(), rg.size() * sizeof(CaseRegime), cudaMemcpyHostToDevice,
+                                           b->stream);
+    if ((r = bcheck(b, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "upload tables"))) return r;
+    if ((r = bcheck(b, cudaStreamSynchronize(b->stream), "upload sync"))) return r;
+    t->h_stage = st;
+    t->h_prep = pr;
+    t->h_reg = rg;
+    t->nlaunch = nl;
+    t->any_plain = any_plain;
+    for (int j = 0; j < nl; ++j) {
+      t->modes[j] = modes[j];
+      t->fin[j] = plans[0].fin[j];
+    }
+    t->valid = true;
+  }
+  t->used = b->steps + 1;
+  int grids[kMaxStages + 1];
+  for (int j = 0; j < nl; ++j) grids[j] = batch_stage_grid(b, t->modes[j]);
+  if (use_graph && b->stream && !b->timing) {
+    if (!t->gexec) {
+      cudaGraph_t g = nullptr;
+      if ((r = bcheck(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+        return r;
+      batch_launches(b, *t, grids);
+      const cudaError_t el = cudaGetLastError();
+      const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      if ((r = bcheck(b, el, "batched step launch")) || (r = bcheck(b, e, "end capture"))) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      r = bcheck(b, cudaGraphInstantiate(&t->gexec, g, 0), "graph instantiate");
+      cudaGraphDestroy(g);
+      if (r) return r;
+    }
+    if ((r = bcheck(b, cudaGraphLaunch(t->gexec, b->stream), "graph launch"))) return r;
+  } else {
+    batch_launches(b, *t, grids);
+    if ((r = bcheck(b, cudaGetLastError(), "batched step launch"))) return r;
+  }
+  for (int i = 0; i < n; ++i) finish_step(b->cs[i], plans[i]);
+  b->steps += 1;
+  return ESBGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t esbgk_batch_workspace_bytes(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes,
+                                   const esbgk_params* params) {
+  BatchLayout B;
+  return batch_layout(n, grids, vmeshes, params, B) ? B.total : 0;
+}
+
+int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes, const esbgk_params* params,
+                       void* workspace, size_t workspace_bytes, void* stream, esbgk_batch** out) {
+  if (!out) return ESBGK_E_ARG;
+  *out = nullptr;
+  BatchLayout B;
+  if (!batch_layout(n, grids, vmeshes, params, B) || !workspace) return ESBGK_E_ARG;
+  if (workspace_bytes < B.total || ((uintptr_t)workspace % kAlign) != 0) return ESBGK_E_WORKSPACE;
+  esbgk_batch* b = new (std::nothrow) esbgk_batch();
+  if (!b) return ESBGK_E_ARG;
+  b->n = n;
+  b->prec = params[0].prec;
+  b->L = launchers_for(b->prec);
+  b->stream = (cudaStream_t)stream;
+  unsigned char* w = (unsigned char*)workspace;
+  std::vector<int> cell_off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    esbgk_ctx* X = nullptr;
+    const size_t bytes = esbgk_workspace_bytes(&grids[i], &vmeshes[i], &params[i]);
+    const int r = esbgk_create(&grids[i], &vmeshes[i], &params[i], w + B.case_off[i], bytes, stream, &X);
+    if (r) {
+      delete b;
+      return r;
+    }
+    b->cs.push_back(X);
+    cell_off[i + 1] = cell_off[i] + X->g.nc;
+    if (X->g.nvv > b->max_nvv) b->max_nvv = X->g.nvv;
+  }
+  b->total_cells = cell_off[n];
+  for (int t = 0; t < kTabSets; ++t) {
+    b->sets[t].reg = (CaseRegime*)(w + B.reg[t]);
+    b->sets[t].stage = (CaseStage*)(w + B.stage[t]);
+    b->sets[t].prep = (CasePrep*)(w + B.prep[t]);
+  }
+  b->d_cell_off = (int*)(w + B.cell_off);
+  b->d_off_stage = (int*)(w + B.off_stage);
+  b->d_off_prep = (int*)(w + B.off_prep);
+  b->d_off_l1 = (int*)(w + B.off_l1);
+  b->d_l1_fresh = (int*)(w + B.l1_fresh);
+  int dev = 0;
+  int r = bcheck(b, cudaGetDevice(&dev), "cudaGetDevice");
+  if (!r) r = bcheck(b, cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  int optin = 0;
+  if (!r) r = bcheck(b, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+  if (!r) {
+    // one f-sized shared array per warp of the batched stage kernel
+    const size_t per_warp = (size_t)b->max_nvv * (b->prec == ESBGK_FP64 ? 8 : 4);
+    int w = 4;
+    while (w > 1 && per_warp * w + kBatchStaticSmem > (size_t)optin) w >>= 1;
+    b->max_threads = b->threads = 32 * w;
+  }
+  if (!r)
+    r = bcheck(b, cudaMemcpyAsync(b->d_cell_off, cell_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                                  b->stream),
+               "upload cell offsets");
+  if (!r) r = bcheck(b, cudaMemsetAsync(b->d_l1_fresh, 0, n * sizeof(int), b->stream), "clear L1 flags");
+  if (!r) r = bcheck(b, cudaStreamSynchronize(b->stream), "batch create sync");
+  if (r) {
+    delete b;
+    return r;
+  }
+  *out = b;
+  return ESBGK_OK;
+}
+
+void esbgk_batch_destroy(esbgk_batch* b) { delete b; }
+
+int esbgk_batch_set_state(esbgk_batch* b, int32_t i, const double* rho, const double* ux, const double* uy,
+                          const double* T, const double* eps, const uint8_t* kinetic) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  const int r = esbgk_set_state(b->cs[i], rho, ux, uy, T, eps, kinetic);
+  if (r) return r;
+  b->status = ESBGK_OK;
+  return bcheck(b, cudaMemsetAsync(b->d_l1_fresh + i, 0, sizeof(int), b->stream), "clear L1 flag");
+}
+
+int esbgk_batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, int32_t use_graph) {
+  if (!b || !dt) return ESBGK_E_ARG;
+  if (b->status) return b->status;
+  if (!valid_tableau(tab)) return bfail(b, ESBGK_E_ARG, "batch step: bad tableau");
+  for (int i = 0; i < b->n; ++i) {
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return bfail(b, ESBGK_E_ARG, "batch step: bad dt");
+    if (!b->cs[i]->have_state) return bfail(b, ESBGK_E_STATE, "batch step: a case has no state");
+    if (b->cs[i]->status) return b->cs[i]->status;
+  }
+  return batch_step(b, dt, tab, use_graph != 0);
+}
+
+int esbgk_batch_get_moments(esbgk_batch* b, int32_t i, double* rho, double* ux, double* uy, double* T) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  return esbgk_get_moments(b->cs[i], rho, ux, uy, T);
+}
+
+int esbgk_batch_get_cons(esbgk_batch* b, int32_t i, double* U) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  return esbgk_get_cons(b->cs[i], U);
+}
+
+int esbgk_batch_get_flags(esbgk_batch* b, int32_t i, uint8_t* kinetic) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  return esbgk_get_flags(b->cs[i], kinetic);
+}
+
+int esbgk_batch_counters(esbgk_batch* b, long long* updates, long long* element_updates, long long* steps,
+                         long long* kinetic_cells) {
+  if (!b) return ESBGK_E_ARG;
+  long long u = 0, e = 0, k = 0;
+  for (auto* X : b->cs) {
+    long long ui = 0, ki = 0;
+    const int r = esbgk_counters(X, &ui, nullptr, &ki, nullptr);
+    if (r) return r;
+    u += ui;
+    e += ui * X->g.nvv;
+    k += ki;
+  }
+  if (updates) *updates = u;
+  if (element_updates) *element_updates = e;
+  if (steps) *steps = b->steps;
+  if (kinetic_cells) *kinetic_cells = k;
+  return ESBGK_OK;
+}
+
+int esbgk_batch_autotune(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, int32_t* threads,
+                         int32_t* ctas_per_sm) {
+  if (!b || !dt) return ESBGK_E_ARG;
+  if (b->status) return b->status;
+  // candidates: warps per CTA x CTAs per SM (0 = as many as fit); each is
+  // timed over two steps after one untimed step
+  const int cand_threads[3] = {32, 64, 128};
+  const int cand_ctas[4] = {0, 2, 4, 8};
+  float best = 1e30f;
+  int bt = b->threads, bc = b->ctas;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int r = bcheck(b, cudaEventCreate(&e0), "autotune event");
+  if (!r) r = bcheck(b, cudaEventCreate(&e1), "autotune event");
+  for (int t : cand_threads) {
+    for (int c : cand_ctas) {
+      if (r || t > b->max_threads) break;
+      b->threads = t;
+      b->ctas = c;
+      if ((r = esbgk_batch_step(b, dt, tab, 0))) break;
+      if ((r = bcheck(b, cudaEventRecord(e0, b->stream), "autotune record"))) break;
+      for (int k = 0; k < 2 && !r; ++k) r = esbgk_batch_step(b, dt, tab, 0);
+      if (r || (r = bcheck(b, cudaEventRecord(e1, b->stream), "autotune record"))) break;
+      if ((r = bcheck(b, cudaEventSynchronize(e1), "autotune sync"))) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bt = t;
+        bc = c;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->threads = bt;
+  b->ctas = bc;
+  b->drop_graphs();
+  if (threads) *threads = bt;
+  if (ctas_per_sm) *ctas_per_sm = bc;
+  return r;
+}
+
+int esbgk_batch_sync(esbgk_batch* b) {
+  if (!b) return ESBGK_E_ARG;
+  if (b->status) return b->status;
+  for (auto* X : b->cs) {
+    const int r = esbgk_sync(X);
+    if (r) return r;
+  }
+  return ESBGK_OK;
+}
+
+int esbgk_batch_timing(esbgk_batch* b, int32_t enable) {
+  if (!b) return ESBGK_E_ARG;
+  b->timing = enable != 0;
+  return esbgk_timing(b->cs[0], enable);
+}
+
+int esbgk_batch_timing_read(esbgk_batch* b, double* ms, long long* launches, int32_t n) {
+  if (!b) return ESBGK_E_ARG;
+  return esbgk_timing_read(b->cs[0], ms, launches, n);
+}
+
+int esbgk_batch_last_error(esbgk_batch* b, char* buf, size_t n, int32_t* case_index) {
+  if (!b) return ESBGK_E_ARG;
+  std::string m = b->msg;
+  int at = -1;
+  if (!b->status) {
+    for (int i = 0; i < b->n && at < 0; ++i)
+      if (b->cs[i]->status) {
+        at = i;
+        m = b->cs[i]->msg;
+      }
+  }
+  if (case_index) *case_index = at;
+  if (buf && n > 0) {
+    const size_t k = m.size() < n - 1 ? m.size() : n - 1;
+    memcpy(buf, m.data(), k);
+    buf[k] = 0;
+  }
+  return ESBGK_OK;
 }
 
 }  // extern "C"

@@ -122,6 +122,20 @@ ESBGK_DEV R cweno_face(R a, R b, R c, R epsw) {
   return fdiv(a0 * P0 + aL * PL + aR * PR, a0 + aL + aR);
 }
 
+// Case of global work unit u: the largest c with off[c] <= u (off ascending,
+// off[0] = 0, n >= 1).
+ESBGK_DEV int find_case(const int* off, int n, int u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 template <typename R>
 ESBGK_DEV R warp_sum(R v) {
 #pragma unroll

@@ -50,11 +50,9 @@ __device__ __forceinline__ double sqrt_nr(double x) {
 // Gradients: central differences of cell-centre u and T, ghost cells by BC.
 // New flag (Eqs. crit:CompEuler, eqKintoFluid1):
 //   lambda_A > eta   or   (kinetic and ||f - M||_1 > delta).
-__global__ void flags_kernel(View V, const double* __restrict__ Un, const double* __restrict__ L1in,
-                             double* L1out, double* lamA, uint8_t* flags_out) {
+__device__ void flags_cell(const View& V, const double* __restrict__ Un, const double* __restrict__ L1in,
+                           double* L1out, double* lamA, uint8_t* flags_out, int c, bool plain) {
   const Geo& g = V.g;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.nc) return;
   const int i = c % g.nx, j = c / g.nx;
   const size_t nc = g.nc;
   auto prim = [&](int cc, double& ux, double& uy, double& T) {
@@ -91,7 +89,13 @@ __global__ void flags_kernel(View V, const double* __restrict__ Un, const double
   const double l1 = kin ? L1in[c] : 0.0;
   lamA[c] = lam;
   L1out[c] = l1;
-  flags_out[c] = (lam > V.m.eta_factor * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
+  if (plain) flags_out[c] = (lam > V.m.eta_factor * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
+}
+
+__global__ void flags_kernel(View V, const double* __restrict__ Un, const double* __restrict__ L1in,
+                             double* L1out, double* lamA, uint8_t* flags_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < V.g.nc) flags_cell(V, Un, L1in, L1out, lamA, flags_out, c, true);
 }
 
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
@@ -102,10 +106,8 @@ void launch_flags(const View& V, const double* Un, const double* L1in, double* L
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
 // cross stencil of a kinetic cell, Remark rem_coupling), 2 other fluid; bit 2
 // (value 4) marks a kinetic cell that was fluid in the previous step.
-__global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
-                                  uint8_t* cat) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.nc) return;
+__device__ void categorize_cell(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
+                                uint8_t* cat, int c) {
   if (flags[c]) {
     cat[c] = prev[c] ? 0 : 4;
     return;
@@ -119,6 +121,12 @@ __global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, cons
     hit |= flags[nb(j + d[q], g.ny, g.bcy) * g.nx + i] != 0;
   }
   cat[c] = hit ? 1 : 2;
+}
+
+__global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
+                                  uint8_t* cat) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nc) categorize_cell(g, flags, prev, cat, c);
 }
 
 void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
@@ -170,8 +178,8 @@ __device__ __forceinline__ void count_cats(uint32_t w, int base, int nc, int (&n
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint8_t* __restrict__ cat, int nc, int* klist,
-                                                               int* blist, int* flist, int* clist, int* counts) {
+__device__ void compact_block(const uint8_t* __restrict__ cat, int nc, int* klist, int* blist, int* flist,
+                              int* clist, int* counts) {
   __shared__ int sm[64];
   const int chunk = ((nc + kScanThreads - 1) / kScanThreads + 15) / 16 * 16;
   const int lo = threadIdx.x * chunk;
@@ -207,6 +215,11 @@ __global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint8_t* __
 #pragma unroll
     for (int q = 0; q < 4; ++q) counts[q] = tot[q];
   }
+}
+
+__global__ void __launch_bounds__(kScanThreads) compact_kernel(const uint8_t* __restrict__ cat, int nc, int* klist,
+                                                               int* blist, int* flist, int* clist, int* counts) {
+  compact_block(cat, nc, klist, blist, flist, clist, counts);
 }
 
 void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* flist, int* clist, int* counts,
@@ -260,5 +273,74 @@ void launch_totals(const double* Un, int nc, double* partial, double* out, doubl
   totals_partial_kernel<<<grid, 256, 0, s>>>(Un, nc, partial);
   totals_final_kernel<<<1, 32, 0, s>>>(partial, grid, out, dxdy);
 }
+
+// ---------------------------------------------------------------------------
+// Batched regime update.
+
+// L1 units: the kinetic cells of plain-switch cases whose L1 is not fresh.
+__global__ void batch_l1_offsets_kernel(BatchTabs T) {
+  if (threadIdx.x != 0) return;
+  int acc = 0;
+  for (int c = 0; c < T.n; ++c) {
+    T.off_l1[c] = acc;
+    const CaseRegime& R = T.reg[c];
+    acc += (R.plain && !*R.l1_fresh) ? R.counts[0] : 0;
+  }
+  T.off_l1[T.n] = acc;
+}
+
+void launch_batch_l1_offsets(const BatchTabs& T, cudaStream_t s) { batch_l1_offsets_kernel<<<1, 32, 0, s>>>(T); }
+
+__global__ void batch_flags_kernel(BatchTabs T) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= T.total_cells) return;
+  const int c = find_case(T.cell_off, T.n, u);
+  const CaseRegime& R = T.reg[c];
+  flags_cell(R.V, R.Un, R.L1, R.L1, R.lamA, R.flags, u - T.cell_off[c], R.plain != 0);
+}
+
+void launch_batch_flags(const BatchTabs& T, cudaStream_t s) {
+  batch_flags_kernel<<<(T.total_cells + 127) / 128, 128, 0, s>>>(T);
+}
+
+__global__ void batch_categorize_kernel(BatchTabs T) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= T.total_cells) return;
+  const int c = find_case(T.cell_off, T.n, u);
+  const CaseRegime& R = T.reg[c];
+  categorize_cell(R.V.g, R.flags, R.flags_prev, R.cat, u - T.cell_off[c]);
+}
+
+void launch_batch_categorize(const BatchTabs& T, cudaStream_t s) {
+  batch_categorize_kernel<<<(T.total_cells + 255) / 256, 256, 0, s>>>(T);
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_compact_kernel(BatchTabs T) {
+  const CaseRegime& R = T.reg[blockIdx.x];
+  compact_block(R.cat, R.V.g.nc, R.klist, R.blist, R.flist, R.clist, R.counts);
+}
+
+void launch_batch_compact(const BatchTabs& T, cudaStream_t s) { batch_compact_kernel<<<T.n, kScanThreads, 0, s>>>(T); }
+
+// Stage units (kinetic cells, buffer cells, chunks of 32 fluid cells) and
+// start-of-step units per case; marks L1 fresh where this step's final
+// combination computes it.
+__global__ void batch_offsets_kernel(BatchTabs T) {
+  if (threadIdx.x != 0) return;
+  int as = 0, ap = 0;
+  for (int c = 0; c < T.n; ++c) {
+    const CaseRegime& R = T.reg[c];
+    const int* k = R.counts;
+    T.off_stage[c] = as;
+    T.off_prep[c] = ap;
+    as += k[0] + k[1] + (k[2] + 31) / 32;
+    ap += k[1] + (R.conv ? k[3] : 0) + (R.prep_copy ? (R.V.g.nc + 31) / 32 : 0);
+    *R.l1_fresh = R.l1_next;
+  }
+  T.off_stage[T.n] = as;
+  T.off_prep[T.n] = ap;
+}
+
+void launch_batch_offsets(const BatchTabs& T, cudaStream_t s) { batch_offsets_kernel<<<1, 32, 0, s>>>(T); }
 
 }  // namespace esbgk

@@ -485,17 +485,7 @@ ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, 
   return warp_sum(s) * (R)g.w;
 }
 
-// Compile-time shapes of a kinetic stage launch.  The inner loops test none
-// of these flags when they are fixed at compile time; kGeneric reads them all
-// at run time and serves any other tableau.
-enum StageMode : int {
-  kGeneric = 0,
-  kFirstRelax2 = 1,   // f* from f_src; relaxation; two accumulators started from f_src (ARS stage 2)
-  kLoadedRelax1 = 2,  // f* from a loaded accumulator; relaxation; one loaded accumulator (ARS stage 3)
-  kFinal = 3,         // no collision term; f* from a loaded accumulator; no accumulator (final combination)
-  kFirstRelax0 = 4,   // f* from f_src; relaxation; no accumulator (stiffly accurate last stage)
-  kNumModes = 5
-};
+// Flag values of each compile-time stage shape (StageMode).
 template <int M>
 struct ModeT {  // kGeneric: unused values
   static constexpr bool relax = false, base_src = false, acc_src = false;
@@ -522,17 +512,6 @@ struct ModeT<kFirstRelax0> {
   static constexpr int nacc = 0;
 };
 
-// Host-side choice of the specialisation for a launch.
-inline int stage_mode(const StageArgs& A) {
-  const bool relax = A.h_coef > 0.0;
-  if (!A.f_src) return kGeneric;
-  const bool bsrc = A.star_base == A.f_src;
-  if (bsrc && relax && A.nacc == 2 && A.acc_in[0] == A.f_src && A.acc_in[1] == A.f_src) return kFirstRelax2;
-  if (!bsrc && relax && A.nacc == 1 && A.acc_in[0] != A.f_src) return kLoadedRelax1;
-  if (!bsrc && !relax && !A.need_q && A.nacc == 0) return kFinal;
-  if (bsrc && relax && A.nacc == 0) return kFirstRelax0;
-  return kGeneric;
-}
 
 // Kinetic cell of a stage (or of the final combination), one warp.
 // Pass 1 forms f* = star_base + star_cL L(f_src) and its moments, keeps f* in
@@ -1072,6 +1051,120 @@ __global__ void __launch_bounds__(kCellThreads) moments_kernel(const void* fptr,
 }
 
 // ---------------------------------------------------------------------------
+// Batched form.  A warp copies the descriptor of its unit's case into shared
+// memory and runs the same per-cell code as the single-case kernels.
+
+// Copy a descriptor of `bytes` (multiple of 4) with the 32 lanes of a warp.
+ESBGK_DEV void warp_copy(void* dst, const void* src, int bytes, int lane) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int w = lane; w < bytes / 4; w += 32) d[w] = s[w];
+  __syncwarp();
+}
+
+static_assert(kCellWarps * sizeof(CaseStage) <= kBatchStaticSmem && sizeof(CaseStage) % 4 == 0, "descriptor copies");
+static_assert(kCellWarps * sizeof(CaseRegime) <= kBatchStaticSmem && sizeof(CaseRegime) % 4 == 0, "descriptor copies");
+static_assert(kCellWarps * sizeof(CasePrep) <= kBatchStaticSmem && sizeof(CasePrep) % 4 == 0, "descriptor copies");
+
+template <typename S, int M>
+__global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
+    batch_stage_kernel(const CaseStage* __restrict__ cases, const int* __restrict__ off, int n, int max_nvv) {
+  using R = typename Real<S>::T;
+  constexpr int kW = VecW<S>::value;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(16) CaseStage cs[kCellWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  R* sfs = reinterpret_cast<R*>(dsm) + (size_t)warp * max_nvv;
+  const int total = off[n];
+  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
+    const int c = find_case(off, n, u);
+    __syncwarp();
+    warp_copy(&cs[warp], &cases[c], sizeof(CaseStage), lane);
+    const View& V = cs[warp].V;
+    const StageArgs& A = cs[warp].A;
+    const int local = u - off[c];
+    const int nK = V.counts[0], nB = V.counts[1], nF = V.counts[2];
+    if (local < nK) {
+      if (M != kGeneric && cs[warp].vec) {
+        if constexpr (M != kGeneric) kinetic_cell_vec<S, M, kW>(A, V, V.klist[local], lane, sfs);
+      } else {
+        kinetic_cell<S, M>(A, V, V.klist[local], lane, sfs);
+      }
+      if (lane == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
+    } else if (local < nK + nB) {
+      buffer_cell<S>(A, V, V.blist[local - nK], lane);
+      if (lane == 0 && A.ctr && A.fill) atomicAdd((unsigned long long*)A.ctr + 1, 1ull);
+    } else {
+      const int q = (local - nK - nB) * 32 + lane;
+      if (q < nF) {
+        double Uc[4];
+        euler_cell<R>(A, V, V.flist[q], Uc);
+      }
+    }
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kCellThreads) batch_prep_kernel(const CasePrep* __restrict__ cases,
+                                                                   const int* __restrict__ off, int n) {
+  __shared__ __align__(16) CasePrep cp[kCellWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int total = off[n];
+  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
+    const int c = find_case(off, n, u);
+    __syncwarp();
+    warp_copy(&cp[warp], &cases[c], sizeof(CasePrep), lane);
+    const View& V = cp[warp].V;
+    const PrepArgs& P = cp[warp].P;
+    const Geo& g = V.g;
+    const int local = u - off[c];
+    const int n1 = P.count1 ? *P.count1 : 0, n2 = P.count2 ? *P.count2 : 0;
+    if (local < n1 + n2) {
+      const int cell = local < n1 ? P.list1[local] : P.list2[local - n1];
+      double Uc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + cell];
+      if (!fill_maxwell<S>((S*)P.f, g, cell, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, cell);
+    } else {
+      const int cell = (local - n1 - n2) * 32 + lane;
+      if (cell < g.nc && P.copy_to) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.copy_to[(size_t)q * g.nc + cell] = P.U[(size_t)q * g.nc + cell];
+        if (P.flags_prev) P.flags_prev[cell] = V.flags[cell];
+      }
+    }
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kCellThreads) batch_l1_kernel(const CaseRegime* __restrict__ cases,
+                                                                 const int* __restrict__ off, int n, int max_nvv) {
+  using R = typename Real<S>::T;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(16) CaseRegime cr[kCellWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  R* sf = reinterpret_cast<R*>(dsm) + (size_t)warp * max_nvv;
+  const int total = off[n];
+  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
+    const int c = find_case(off, n, u);
+    __syncwarp();
+    warp_copy(&cr[warp], &cases[c], sizeof(CaseRegime), lane);
+    const CaseRegime& Rg = cr[warp];
+    const Geo& g = Rg.V.g;
+    const int cell = Rg.klist[u - off[c]];
+    R u0x, u0y, m[6];
+    ref_velocity(Rg.Un, g.nc, cell, u0x, u0y);
+    load_moments<S>((const S*)Rg.f, g, cell, lane, u0x, u0y, sf, m);
+    __syncwarp();
+    const R l1 = l1_deviation<R, 1>(g, lane, m, u0x, u0y, sf);
+    if (lane == 0) {
+      if (l1 < R(0)) report_error(Rg.V.err, kErrNonRealizable, cell);
+      Rg.L1[cell] = (double)l1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers for storage type S.
 template <typename S>
 struct Launch {
@@ -1140,6 +1233,16 @@ struct Launch {
     return true;
   }
 
+  using BatchFn = void (*)(const CaseStage*, const int*, int, int);
+  static BatchFn batch_fn(int m) {
+    switch (m) {
+      case kFirstRelax2: return batch_stage_kernel<S, kFirstRelax2>;
+      case kLoadedRelax1: return batch_stage_kernel<S, kLoadedRelax1>;
+      case kFinal: return batch_stage_kernel<S, kFinal>;
+      case kFirstRelax0: return batch_stage_kernel<S, kFirstRelax0>;
+      default: return batch_stage_kernel<S, kGeneric>;
+    }
+  }
   static cudaError_t setup(const Geo& g) {
     if ((size_t)g.nvv * sizeof(R) > (size_t)max_smem()) return cudaErrorInvalidValue;
     cudaError_t e;
@@ -1150,6 +1253,13 @@ struct Launch {
             cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+      return e;
+    // batched kernels: set here so that their launches can be graph-captured
+    const int mb = mx - kBatchStaticSmem;
+    for (int m = 0; m < kNumModes; ++m)
+      if ((e = cudaFuncSetAttribute(batch_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(batch_l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
       return e;
     return cudaFuncSetAttribute(relax_cells_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   }
@@ -1184,14 +1294,33 @@ struct Launch {
     const int threads = 32 * warps_for(g, 1);
     relax_cells_kernel<S><<<grid, threads, smem_for(g, 1), s>>>((const S*)fs, h, n, g, beta, (S*)fo, (S*)go);
   }
+  static size_t batch_smem(int max_nvv, int threads) { return (size_t)(threads / 32) * max_nvv * sizeof(R); }
+  static int batch_stage_occupancy(int mode, int max_nvv, int threads) {
+    return occ((const void*)batch_fn(mode), threads, batch_smem(max_nvv, threads));
+  }
+  static void batch_stage(const CaseStage* cases, const int* off, int n, int mode, int max_nvv, int threads, int grid,
+                          cudaStream_t s) {
+    const BatchFn fn = batch_fn(mode);
+    fn<<<grid, threads, batch_smem(max_nvv, threads), s>>>(cases, off, n, max_nvv);
+  }
+  static void batch_prep(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t s) {
+    batch_prep_kernel<S><<<grid, kCellThreads, 0, s>>>(cases, off, n);
+  }
+  static void batch_l1(const CaseRegime* cases, const int* off, int n, int max_nvv, int grid, cudaStream_t s) {
+    batch_l1_kernel<S><<<grid, kCellThreads, kCellWarps * (size_t)max_nvv * sizeof(R), s>>>(cases, off, n, max_nvv);
+  }
+  static bool vector_ok_public(const StageArgs& A, const Geo& g) { return vector_ok(A, g, stage_mode(A)); }
   static void moments(const void* f, double* U, const View& V, int grid, cudaStream_t s) {
     moments_kernel<S><<<rescale(V.g, grid, (const void*)moments_kernel<S>, kCellThreads, 0), kCellThreads, 0, s>>>(
         f, U, V);
   }
 };
 
-#define ESBGK_INSTANTIATE(S, NAME)                                                                          \
-  const Launchers NAME = {sizeof(S),        &Launch<S>::setup, &Launch<S>::blocks_per_sm, &Launch<S>::stage, \
-                          &Launch<S>::prep, &Launch<S>::l1,    &Launch<S>::relax_cells,   &Launch<S>::moments};
+#define ESBGK_INSTANTIATE(S, NAME)                                                                            \
+  const Launchers NAME = {sizeof(S),                          &Launch<S>::setup,        &Launch<S>::blocks_per_sm, \
+                          &Launch<S>::stage,                  &Launch<S>::prep,         &Launch<S>::l1,            \
+                          &Launch<S>::relax_cells,            &Launch<S>::moments,      &Launch<S>::batch_stage,   \
+                          &Launch<S>::batch_prep,             &Launch<S>::batch_l1,                               \
+                          &Launch<S>::batch_stage_occupancy, &Launch<S>::vector_ok_public};
 
 }  // namespace esbgk

@@ -73,6 +73,86 @@ struct PrepArgs {
   uint8_t* flags_prev;
 };
 
+// Compile-time shapes of a kinetic stage launch.  The inner loops test none
+// of these flags when they are fixed at compile time; kGeneric reads them all
+// at run time and serves any other tableau.
+enum StageMode : int {
+  kGeneric = 0,
+  kFirstRelax2 = 1,   // f* from f_src; relaxation; two accumulators started from f_src (ARS stage 2)
+  kLoadedRelax1 = 2,  // f* from a loaded accumulator; relaxation; one loaded accumulator (ARS stage 3)
+  kFinal = 3,         // no collision term; f* from a loaded accumulator; no accumulator (final combination)
+  kFirstRelax0 = 4,   // f* from f_src; relaxation; no accumulator (stiffly accurate last stage)
+  kNumModes = 5
+};
+
+// Host-side choice of the specialisation for a launch.
+inline int stage_mode(const StageArgs& A) {
+  const bool relax = A.h_coef > 0.0;
+  if (!A.f_src) return kGeneric;
+  const bool bsrc = A.star_base == A.f_src;
+  if (bsrc && relax && A.nacc == 2 && A.acc_in[0] == A.f_src && A.acc_in[1] == A.f_src) return kFirstRelax2;
+  if (!bsrc && relax && A.nacc == 1 && A.acc_in[0] != A.f_src) return kLoadedRelax1;
+  if (!bsrc && !relax && !A.need_q && A.nacc == 0) return kFinal;
+  if (bsrc && relax && A.nacc == 0) return kFirstRelax0;
+  return kGeneric;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent cases advanced by one launch per kernel.
+// Every per-case descriptor lives in device memory; a global work unit u
+// belongs to the case c with off[c] <= u < off[c+1].
+
+// Shared memory the batched kernels reserve for their per-warp descriptor
+// copies; the dynamic f-sized arrays get the rest of the opt-in limit.
+constexpr int kBatchStaticSmem = 8 * 1024;
+
+// One case of a batched stage launch (vec: the vector node-group form applies).
+struct CaseStage {
+  View V;
+  StageArgs A;
+  int vec;
+  int pad;
+};
+
+// One case of a batched start-of-step launch.
+struct CasePrep {
+  View V;
+  PrepArgs P;
+};
+
+// One case of the batched regime update.
+struct CaseRegime {
+  View V;
+  const void* f;          // f^n
+  double* Un;
+  double* L1;
+  double* lamA;
+  uint8_t* flags;
+  uint8_t* flags_prev;
+  uint8_t* cat;
+  int* klist;
+  int* blist;
+  int* flist;
+  int* clist;
+  int* counts;
+  int* l1_fresh;          // device flag: L1 already holds the deviation of f^n
+  int plain;              // plain switch (else the regime map is kept)
+  int l1_next;            // the final combination of this step computes L1
+  int prep_copy;          // the start-of-step launch copies U^n and flags (units of 32 cells)
+  int conv;               // the start-of-step launch fills converted cells
+};
+
+// Device tables of a batch.
+struct BatchTabs {
+  const CaseRegime* reg;  // [n]
+  const int* cell_off;    // [n+1] prefix of cells
+  int* off_stage;         // [n+1] prefix of stage units
+  int* off_prep;          // [n+1] prefix of start-of-step units
+  int* off_l1;            // [n+1] prefix of L1 units
+  int n;
+  int total_cells;
+};
+
 // Per-storage-type launchers (one table per precision).
 struct Launchers {
   size_t elem;
@@ -84,6 +164,13 @@ struct Launchers {
   void (*relax_cells)(const void* fs, const double* h, int n, const Geo&, double beta, void* fo, void* go,
                       int grid, cudaStream_t);
   void (*moments)(const void* f, double* U, const View&, int grid, cudaStream_t);
+  // batched form; threads per CTA (multiple of 32, <= 128) and grid chosen by the caller
+  void (*batch_stage)(const CaseStage* cases, const int* off, int n, int mode, int max_nvv, int threads, int grid,
+                      cudaStream_t);
+  void (*batch_prep)(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t);
+  void (*batch_l1)(const CaseRegime* cases, const int* off, int n, int max_nvv, int grid, cudaStream_t);
+  int (*batch_stage_occupancy)(int mode, int max_nvv, int threads);
+  bool (*vector_ok)(const StageArgs& A, const Geo& g);
 };
 
 extern const Launchers kLaunchF64;
@@ -102,5 +189,12 @@ void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* fli
 void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
 void launch_totals(const double* Un, int nc, double* partial /*[grid][4]*/, double* out, double dxdy, int grid,
                    cudaStream_t s);
+// batched regime update: offsets of the L1 units, flags, categories,
+// compaction (one CTA per case), offsets of the stage and start-of-step units
+void launch_batch_l1_offsets(const BatchTabs& T, cudaStream_t s);
+void launch_batch_flags(const BatchTabs& T, cudaStream_t s);
+void launch_batch_categorize(const BatchTabs& T, cudaStream_t s);
+void launch_batch_compact(const BatchTabs& T, cudaStream_t s);
+void launch_batch_offsets(const BatchTabs& T, cudaStream_t s);
 
 }  // namespace esbgk

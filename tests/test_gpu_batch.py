@@ -1,0 +1,164 @@
+"""Batched form: many independent problems advanced by one launch per kernel.
+
+Every case of a batch must reproduce the same problem advanced alone: the
+batched kernels run the single-problem per-cell code, but they are separate
+kernels, so the compiler may contract a few products into FMAs differently
+and the results agree to rounding, not bit for bit.  Per field, the relative
+L1 difference must stay within TOL_BATCH and the regime maps must be
+identical, for mixed grid sizes, velocity grids (vector and scalar node
+groups), switches and tableaux, with and without CUDA-graph replay.  One small
+batch is also checked directly against the FP64 oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# batch vs single problem: rounding differences only (FP64: a few ulp,
+# FP32 / BF16 storage: the storage rounding of f can flip)
+TOL_BATCH = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 1e-3}
+
+
+def _mixed_cases():
+    """Uneven sizes, N_v even/odd (vector form on/off), plain and frozen
+    switches, all-kinetic, hybrid and initially all-fluid maps.  Every
+    velocity grid resolves the thermal speed of its data (dv <= sqrt(T)
+    in most cells), so that rounding differences are not amplified by an
+    ill-conditioned moment system."""
+    out = []
+    out.append(W.riemann_quadrants(nx=24, ny=20, nv=16, seed=3))               # plain, starts fluid
+    out += W.batched_cases(n_cases=2, seed0=11, sizes=[16, 24], nvs=[12, 16])  # plain, all kinetic
+    out.append(W.sine_periodic(nx=10, ny=14, nv=15, scheme="ars233"))        # frozen, odd N_v
+    hyb = W.gaussian_blob(nx=18, ny=12, nv=8, vmax=4.0)
+    rng = np.random.default_rng(5)
+    hyb["fields"]["kin"] = rng.random((12, 18)) < 0.4                          # frozen hybrid map
+    out.append(hyb)
+    return out
+
+
+def _single(wl, prec):
+    import paper_2512_03586_gb300 as G
+    s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=prec)
+    f = wl["fields"]
+    s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    return s
+
+
+def _batch(cases, prec, stream=None):
+    import paper_2512_03586_gb300 as G
+    b = G.BatchSolver([(c["grid"], c["vmesh"], c["params"]) for c in cases], prec=prec, stream=stream)
+    for i, c in enumerate(cases):
+        f = c["fields"]
+        b.set_state(i, f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    return b
+
+
+def _compare(b, singles, prec):
+    for i, s in enumerate(singles):
+        Ub, Us = b.cons(i), s.cons()
+        r = np.abs(Us[0]).sum()
+        for q in range(4):
+            scale = np.abs(Us[3]).sum() if q == 3 else r
+            err = np.abs(Ub[q] - Us[q]).sum() / scale
+            assert err <= TOL_BATCH[prec], "case %d field %d: %.3e" % (i, q, err)
+        np.testing.assert_array_equal(b.flags(i), s.flags(), err_msg="case %d flags" % i)
+
+
+@pytest.mark.parametrize("prec,tableau,graph", [("fp64", "ars233", True), ("fp32", "ars233", True),
+                                                ("fp32", "imex_euler", True), ("fp64", "ars233", False),
+                                                ("bf16", "ars233", True)])
+def test_batch_equals_single_cases(prec, tableau, graph):
+    import torch
+    cases = _mixed_cases()
+    for c in cases:
+        c["scheme"] = tableau
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, prec, stream=stream)
+        singles = [_single(c, prec) for c in cases]
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(5):
+            for s, c in zip(singles, cases):
+                s.step(c["dt"], tableau)
+            b.step(dts, tableau, graph=graph)
+        b.sync()
+        _compare(b, singles, prec)
+        cb = b.counters()
+        cs = [s.counters() for s in singles]
+        assert cb["kinetic_cell_updates"] == sum(c["kinetic_cell_updates"] for c in cs)
+        assert cb["kinetic_cells"] == sum(c["kinetic_cells"] for c in cs)
+        assert cb["steps"] == 5
+
+
+def test_batch_on_default_stream_runs_without_graph():
+    cases = _mixed_cases()[:3]
+    b = _batch(cases, "fp64")
+    singles = [_single(c, "fp64") for c in cases]
+    dts = np.array([c["dt"] for c in cases])
+    for _ in range(3):
+        b.step(dts, "ars233", graph=True)  # legacy stream: plain launches
+        for s, c in zip(singles, cases):
+            s.step(c["dt"], "ars233")
+    _compare(b, singles, "fp64")
+
+
+def test_batch_autotune_keeps_results():
+    import torch
+    cases = W.batched_cases(n_cases=6, seed0=20, sizes=[16, 32, 48], nvs=[16, 20, 24])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, "fp32", stream=stream)
+        dts = np.array([c["dt"] for c in cases])
+        threads, ctas = b.autotune(dts)
+        assert threads in (32, 64, 128) and ctas in (0, 2, 4, 8)
+        n_tuned = b.counters()["steps"]
+        assert n_tuned > 0
+        b.step(dts)
+        singles = [_single(c, "fp32") for c in cases]
+        for s, c in zip(singles, cases):
+            for _ in range(n_tuned + 1):
+                s.step(c["dt"], "ars233")
+        _compare(b, singles, "fp32")
+
+
+def test_batch_matches_oracle_small():
+    import torch
+    w1 = W.riemann_quadrants(nx=16, ny=12, nv=12, seed=1)
+    w1["params"] = dict(w1["params"], switch="frozen")
+    w1["fields"]["kin"] = np.random.default_rng(2).random((12, 16)) < 0.5
+    w2 = W.gaussian_blob(nx=10, ny=8, nv=16, steps=2)
+    cases = [w1, w2]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, "fp64", stream=stream)
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(2):
+            b.step(dts)
+        b.sync()
+    for i, wl in enumerate(cases):
+        P = O.Problem(**wl["grid"], **wl["vmesh"], **wl["params"])
+        st = O.init_state(P, **wl["fields"])
+        for _ in range(2):
+            st = O.step(P, st, wl["dt"], O.ARS233)
+        U = b.cons(i)
+        r = np.abs(st.U[0]).sum()
+        for q in range(4):
+            scale = np.abs(st.U[3]).sum() if q == 3 else r
+            assert np.abs(U[q] - st.U[q]).sum() / scale <= 1e-10, (i, q)
+
+
+def test_batch_rejects_bad_input():
+    import paper_2512_03586_gb300 as G
+    w = W.sine_periodic(nx=4, ny=4, nv=8)
+    with pytest.raises(ValueError):
+        G.BatchSolver([])
+    b = G.BatchSolver([(w["grid"], w["vmesh"], w["params"])], prec="fp64")
+    with pytest.raises(G.Error):  # no state yet
+        b.step(w["dt"])
+    out = np.empty(4 * 16)
+    assert b._abi.esbgk_batch_get_cons(b._b, 5, out.ctypes.data_as(b._abi.D)) == b._abi.E_ARG
+    assert b._abi.esbgk_batch_get_cons(b._b, -1, out.ctypes.data_as(b._abi.D)) == b._abi.E_ARG
