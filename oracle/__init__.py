@@ -20,7 +20,9 @@ Arithmetic is numpy float64.  Library primitives used as steps: ``np.sum``,
 
 Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 pinned -- moments, Gaussian, projected Gaussian, relaxation, CWENO3, transport,
-Euler flux, regime criterion, tableaux, stepper (order, conservation, limits).
+Euler flux, regime criterion, tableaux, stepper (order, conservation, limits),
+and the learned switch in ``oracle.cnn`` (network forward and gradients,
+features, Adam, the learned map rule).
 Parity unpinned beyond invariants: the CWENO epsilon value, the choice of the
 quadratic moment projection, and the criterion constants (paper's printed
 d_v = 3 values), which are readings, not results the paper fixes.
@@ -33,5 +35,6 @@ from .transport import pad_cells, cweno3_faces, cweno3_indicators, kinetic_trans
 from .scheme import (Problem, State, ARS233, IMEX_EULER, Tableau, init_state,
                      regime_indicators, regime_update, convert, buffer_mask,
                      advance, step, totals, macro)
+from . import cnn
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -1,0 +1,126 @@
+"""Pins of the learned-switch oracle (oracle/cnn.py) against things other
+than itself: torch's float64 conv2d and autograd (an independent library),
+central finite differences of the loss, the closed form of the features and
+the Adam update's first step."""
+
+import numpy as np
+import pytest
+
+from oracle import cnn as C
+
+torch = pytest.importorskip("torch")
+
+
+def _case(seed=0, N=2, H=6, W=7):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(N, H, W, C.C_IN))
+    y = (rng.random((N, H, W)) < 0.3).astype(np.float64)
+    theta = C.init_params(seed)
+    # non-zero biases so that every term of the chain rule is exercised
+    p = C.unpack(theta.copy())
+    p["b1"][:] = rng.normal(0, 0.1, C.C_HID)
+    p["b2"][:] = rng.normal(0, 0.1, C.C_HID)
+    p["b3"][:] = 0.2
+    return C.pack(p), x, y
+
+
+def _torch_forward(theta, x):
+    p = {k: torch.tensor(v) for k, v in C.unpack(theta).items()}
+    xt = torch.tensor(x).permute(0, 3, 1, 2)                        # N C H W
+    w1 = p["W1"].permute(0, 3, 1, 2)                                # O I kh kw
+    w2 = p["W2"].permute(0, 3, 1, 2)
+    a1 = torch.relu(torch.nn.functional.conv2d(xt, w1, p["b1"], padding=1))
+    a2 = torch.relu(torch.nn.functional.conv2d(a1, w2, p["b2"], padding=1))
+    z3 = torch.einsum("nchw,c->nhw", a2, p["w3"]) + p["b3"][0]
+    return z3
+
+
+def test_forward_matches_torch_conv2d():
+    theta, x, _ = _case(1)
+    z_or = C.forward(theta, x)["z3"]
+    z_t = _torch_forward(theta, x).numpy()
+    np.testing.assert_allclose(z_or, z_t, rtol=1e-12, atol=1e-12)
+
+
+def test_gradient_matches_torch_autograd():
+    theta, x, y = _case(2)
+    pw = 2.5
+    L, g = C.grad(theta, x, y, pw)
+    th = torch.tensor(theta, requires_grad=True)
+    # rebuild the network from the flat vector so autograd sees the packing
+    parts, o = {}, 0
+    for name, shp in C.SHAPES:
+        n = int(np.prod(shp))
+        parts[name] = th[o:o + n].reshape(shp)
+        o += n
+    xt = torch.tensor(x).permute(0, 3, 1, 2)
+    a1 = torch.relu(torch.nn.functional.conv2d(xt, parts["W1"].permute(0, 3, 1, 2), parts["b1"], padding=1))
+    a2 = torch.relu(torch.nn.functional.conv2d(a1, parts["W2"].permute(0, 3, 1, 2), parts["b2"], padding=1))
+    z = torch.einsum("nchw,c->nhw", a2, parts["w3"]) + parts["b3"][0]
+    yt = torch.tensor(y)
+    w = torch.where(yt > 0.5, torch.tensor(pw, dtype=torch.float64), torch.tensor(1.0, dtype=torch.float64))
+    Lt = torch.mean(w * torch.nn.functional.binary_cross_entropy_with_logits(z, yt, reduction="none"))
+    Lt.backward()
+    assert abs(L - Lt.item()) <= 1e-12 * abs(L)
+    np.testing.assert_allclose(g, th.grad.numpy(), rtol=1e-9, atol=1e-13)
+
+
+def test_gradient_matches_finite_differences():
+    theta, x, y = _case(3, N=1, H=5, W=5)
+    pw = 3.0
+    _, g = C.grad(theta, x, y, pw)
+    rng = np.random.default_rng(0)
+    # a sample of every parameter block
+    offs, o = [], 0
+    for _, shp in C.SHAPES:
+        n = int(np.prod(shp))
+        offs += list(o + rng.choice(n, size=min(n, 6), replace=False))
+        o += n
+    h = 1e-6
+    for k in offs:
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (C.loss(tp, x, y, pw) - C.loss(tm, x, y, pw)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1e-3, abs(g[k])), (k, fd, g[k])
+
+
+def test_conv_of_centre_tap_is_a_matmul():
+    """A kernel with only the centre tap is a per-cell linear map."""
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(1, 4, 5, 3))
+    Wt = np.zeros((2, 3, 3, 3))
+    Wt[:, 1, 1, :] = rng.normal(size=(2, 3))
+    b = rng.normal(size=2)
+    np.testing.assert_allclose(C.conv3x3(x, Wt, b), x @ Wt[:, 1, 1, :].T + b, rtol=1e-14)
+
+
+def test_features_closed_form():
+    rho = np.array([[1.0, 0.5]])
+    ux = np.array([[0.3, -0.2]])
+    uy = np.array([[0.0, 0.1]])
+    T = np.array([[2.0, 0.25]])
+    U = np.stack([rho, rho * ux, rho * uy, 0.5 * rho * (ux ** 2 + uy ** 2) + rho * T])
+    eps = np.array([[1e-2, 1e-4]])
+    F = C.features(U, eps, 1.0 / 128)
+    np.testing.assert_allclose(F[..., 0], np.log(rho))
+    np.testing.assert_allclose(F[..., 1], ux, atol=1e-15)
+    np.testing.assert_allclose(F[..., 2], uy, atol=1e-15)
+    np.testing.assert_allclose(F[..., 3], np.log(T), atol=1e-14)
+    np.testing.assert_allclose(F[..., 4], [[np.log10(1.28), np.log10(0.0128)]], atol=1e-14)
+
+
+def test_adam_first_step_is_signed_lr():
+    """With m = v = 0, the first Adam step moves each weight by lr sign(g)
+    (up to eps)."""
+    g = np.array([0.5, -2.0, 1e-3])
+    th, m, v = C.adam(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
+    np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_learned_map_keeps_every_plain_kinetic_cell():
+    rng = np.random.default_rng(5)
+    plain = rng.random((8, 8)) < 0.3
+    pred = rng.random((8, 8)) < 0.3
+    m = C.learned_map(plain, pred)
+    assert np.all(m[plain]) and np.all(m[pred]) and not np.any(m[~plain & ~pred])
