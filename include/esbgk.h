@@ -53,7 +53,7 @@ typedef enum {
 
 typedef enum { ESBGK_FP64 = 0, ESBGK_FP32 = 1, ESBGK_BF16 = 2 } esbgk_prec;
 typedef enum { ESBGK_BC_PERIODIC = 0, ESBGK_BC_OUTFLOW = 1 } esbgk_bc;
-typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1 } esbgk_switch;
+typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1, ESBGK_SWITCH_LEARNED = 2 } esbgk_switch;
 typedef enum { ESBGK_COUPLE_STAGE = 0, ESBGK_COUPLE_STEP = 1 } esbgk_coupling;
 
 /* Cartesian grid of Sec. 3.2: N_x x N_y cells on [x0,x1] x [y0,y1]; two ghost
@@ -77,7 +77,9 @@ typedef struct {
  *  delta      threshold of Eq. eqKintoFluid1 (absolute L1 deviation).
  *  cweno_eps  epsilon of the CWENO3 nonlinear weights (Sec. 3.2).
  *  sw         esbgk_switch: FROZEN keeps the regime map, PLAIN applies
- *             Sec. 3.1.2 before every step.
+ *             Sec. 3.1.2 before every step, LEARNED applies Sec. 3.1.2 and
+ *             adds the cells a trained network predicts kinetic for the
+ *             next step (see "Learned regime switch" below).
  *  coupling   esbgk_coupling: STAGE couples at every stage (Algorithm 1),
  *             STEP only at step end (the LOC-hybrid of Sec. 3.5).
  *  prec       esbgk_prec of f storage and per-element arithmetic: FP64; FP32;
@@ -185,7 +187,7 @@ enum {
   ESBGK_K_PREP = 3,    /* start-of-step coupling (buffer and converted cells)  */
   ESBGK_K_STAGE = 4,   /* fused IMEX stage kernels                             */
   ESBGK_K_FINAL = 5,   /* final combination (same kernel as the stages)        */
-  ESBGK_K_OTHER = 6,
+  ESBGK_K_OTHER = 6,    /* learned-switch inference (features, network, judge)  */
   ESBGK_K_COUNT = 7
 };
 
@@ -300,6 +302,72 @@ int esbgk_batch_timing_read(esbgk_batch* b, double* ms, long long* launches, int
  * buf[n] (NUL-terminated); *case_index (may be NULL) receives the failing
  * case or -1. */
 int esbgk_batch_last_error(esbgk_batch* b, char* buf, size_t n, int32_t* case_index);
+
+/* ------------------------------------------------------------------------
+ * Learned regime switch.  (An addition to the paper, whose regime decision is
+ * the criterion of Sec. 3.1.2 alone.)  A 3-layer convolutional network reads
+ * five features of every cell of a 5 x 5 neighbourhood at step n --
+ * (log rho, s u_x, s u_y, log T, log10(eps s^2)), s = (1/128) / min(dx, dy),
+ * scaled so that the criterion's velocity-gradient and temperature-gradient
+ * terms are the same function of the features on every grid -- and
+ * predicts the flag the criterion gives the cell at step n + 1:
+ *   a1 = relu(b1 + conv3x3(x, W1)), a2 = relu(b2 + conv3x3(a1, W2)),
+ *   z = b3 + a2 . w3, predicted kinetic iff z > 0,
+ * with 'same' zero padding, 32 hidden channels, bf16 operands and float32
+ * accumulation on the tensor cores.  Parameters (ESBGK_CNN_PARAMS float32,
+ * this order): W1 [32][3][3][5], b1[32], W2 [32][3][3][32], b2[32], w3[32],
+ * b3[1].
+ * With sw = ESBGK_SWITCH_LEARNED the regime update applies the criterion
+ * (it is the judge and the fallback: every cell it marks kinetic is
+ * kinetic) and adds the cells predicted kinetic for the next step.  It
+ * counts, per update after the first, the cells predicted kinetic at the
+ * previous update, those the criterion now marks kinetic that were not
+ * predicted (missed) and those predicted but not marked (extra).
+ * Features on the device: [cell][ESBGK_CNN_CHANNELS] bf16, channels 5..15
+ * zero, cell = j * N_x + i. */
+#define ESBGK_CNN_PARAMS 10753
+#define ESBGK_CNN_CHANNELS 16
+
+/* Load the network of a LEARNED context (host float32 theta[ESBGK_CNN_PARAMS]);
+ * required before the first step.  ESBGK_E_STATE for another switch. */
+int esbgk_set_switch_params(esbgk_ctx* ctx, const float* theta);
+
+/* Judge statistics accumulated since create (any pointer may be NULL):
+ * judged cells, cells predicted kinetic, missed, extra. */
+int esbgk_switch_stats(esbgk_ctx* ctx, long long* judged_cells, long long* predicted, long long* missed,
+                       long long* extra);
+
+/* Features of the current state into device memory x (16-byte aligned,
+ * N_c * ESBGK_CNN_CHANNELS bf16); asynchronous on the context's stream.
+ * Any switch mode. */
+int esbgk_features(esbgk_ctx* ctx, void* x);
+
+/* Training and evaluation of the network on batches of n images of H x W
+ * cells (features as above, [img][H][W][16] bf16 in device memory; labels
+ * y [img][H][W] uint8 in device memory).  Loss: class-weighted binary
+ * cross-entropy averaged over cells, weight pos_weight on kinetic labels.
+ * Optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the float32
+ * parameters.  The workspace (256-byte aligned, caller-owned) holds the
+ * parameters, optimiser state, activations and gradients. */
+typedef struct esbgk_cnn esbgk_cnn;
+size_t esbgk_cnn_workspace_bytes(int32_t max_images, int32_t H, int32_t W);
+int esbgk_cnn_create(int32_t max_images, int32_t H, int32_t W, void* workspace, size_t workspace_bytes,
+                     void* stream, esbgk_cnn** out);
+void esbgk_cnn_destroy(esbgk_cnn* c);
+/* Set (and reset the optimiser) / read the float32 parameters (host). */
+int esbgk_cnn_set_params(esbgk_cnn* c, const float* theta);
+int esbgk_cnn_get_params(esbgk_cnn* c, float* theta);
+/* Logits of n <= max_images images into device memory logits[n][H][W]. */
+int esbgk_cnn_forward(esbgk_cnn* c, const void* x, int32_t n, float* logits);
+/* Loss and gradient (host float *loss, float grad[ESBGK_CNN_PARAMS]; either
+ * may be NULL) without an update; synchronises. */
+int esbgk_cnn_gradient(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n, float pos_weight, float* loss,
+                       float* grad);
+/* One Adam step at learning rate lr; the loss of the batch before the step
+ * into *loss when non-NULL (then it synchronises). */
+int esbgk_cnn_train_step(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n, float pos_weight, float lr,
+                         float* loss);
+int esbgk_cnn_sync(esbgk_cnn* c);
 
 /* Allocation-free stepping of an all-kinetic problem.  (The paper has no
  * counterpart: this is a service for callers.)

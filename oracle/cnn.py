@@ -68,17 +68,28 @@ def init_params(seed=0):
     return pack(p)
 
 
-def features(U, eps, dx):
+DX_REF = 1.0 / 128.0
+
+
+def features(U, eps, dx, dx_ref=DX_REF):
     """Input channels of a cell from the conserved variables U (4, H, W)
     (rho, rho u_x, rho u_y, E with E = rho |u|^2 / 2 + rho T, Sec. 2 with
     d_v = 2), the Knudsen number eps (H, W) and the cell size dx:
-    (log rho, u_x, u_y, log T, log10(eps / dx)).  The last channel is the
-    cell Knudsen number: the criterion of Sec. 3.1.2 multiplies eps by
-    central differences over one cell, so eps / dx is what it sees."""
+      (log rho, s u_x, s u_y, log T, log10(eps s^2)),  s = dx_ref / dx.
+    Reading: the criterion of Sec. 3.1.2 divided by eps depends on the
+    velocity jumps between neighbours through D ~ (jump of u) / (2 dx) and on
+    the temperature jumps through eps (jump of T / (2 dx))^2 / T.  With
+    velocities scaled by s, neighbour differences of s u are 2 dx_ref D; with
+    eps scaled by s^2, the temperature term is the same function of the
+    channels at every grid spacing.  So a network trained on one grid sees
+    the same inputs for the same physical state on a finer one.  At
+    dx = dx_ref (the 128 x 128 grid of the unit square) the channels are
+    (log rho, u_x, u_y, log T, log10 eps)."""
+    s = dx_ref / dx
     rho = U[0]
     ux, uy = U[1] / rho, U[2] / rho
     T = (U[3] - 0.5 * rho * (ux * ux + uy * uy)) / rho
-    return np.stack([np.log(rho), ux, uy, np.log(T), np.log10(eps / dx)], axis=-1)
+    return np.stack([np.log(rho), s * ux, s * uy, np.log(T), np.log10(eps * s * s)], axis=-1)
 
 
 def _shift(x, dy, dx):
@@ -100,14 +111,23 @@ def conv3x3(x, Wt, b):
     return out + b
 
 
-def forward(theta, x):
-    """All activations of the network for inputs x (N, H, W, 5)."""
+def _keep(a):
+    return a
+
+
+def forward(theta, x, rnd=None):
+    """All activations of the network for inputs x (N, H, W, 5).
+
+    rnd: optional rounding applied to the stored activations a1, a2, for
+    comparison with an implementation that stores them in a narrower type
+    (bf16); None keeps float64 throughout."""
+    rnd = rnd or _keep
     p = unpack(theta)
     x = np.asarray(x, np.float64)
     z1 = conv3x3(x, p["W1"], p["b1"])
-    a1 = np.maximum(z1, 0.0)
+    a1 = rnd(np.maximum(z1, 0.0))
     z2 = conv3x3(a1, p["W2"], p["b2"])
-    a2 = np.maximum(z2, 0.0)
+    a2 = rnd(np.maximum(z2, 0.0))
     z3 = a2 @ p["w3"] + p["b3"][0]
     return dict(x=x, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3)
 
@@ -124,7 +144,7 @@ def loss(theta, x, y, pos_weight):
     return float(np.mean(w * (np.logaddexp(0.0, z) - y * z)))
 
 
-def grad(theta, x, y, pos_weight):
+def grad(theta, x, y, pos_weight, rnd=None):
     """(loss, gradient vector) by the chain rule through the layers above.
 
     dL/dz3 = w (sigmoid(z3) - y) / M; the 1 x 1 head gives dL/dw3 = sum a2 dz3
@@ -132,9 +152,11 @@ def grad(theta, x, y, pos_weight):
     zero-padded convolution z = conv3x3(a, W) gives
       dL/dW[o, ky, kx, c] = sum_{n,y,x} dz[n,y,x,o] a[n, y+ky-1, x+kx-1, c],
       dL/da[n,y,x,c]      = sum_{ky,kx,o} dz[n, y-ky+1, x-kx+1, o] W[o,ky,kx,c],
-      dL/db[o]            = sum dz[..., o]."""
+      dL/db[o]            = sum dz[..., o].
+    rnd: as in ``forward``, applied also to the stored gradients dz2, dz1."""
+    rnd = rnd or _keep
     p = unpack(theta)
-    f = forward(theta, x)
+    f = forward(theta, x, rnd)
     y = np.asarray(y, np.float64)
     M = y.size
     w = np.where(y > 0.5, pos_weight, 1.0)
@@ -144,7 +166,7 @@ def grad(theta, x, y, pos_weight):
     dz3 = w * (sig - y) / M
     g = {"b3": np.array([dz3.sum()]), "w3": np.einsum("nyx,nyxc->c", dz3, f["a2"])}
     da2 = dz3[..., None] * p["w3"]
-    dz2 = da2 * (f["z2"] > 0)
+    dz2 = rnd(da2 * (f["z2"] > 0))
     g["b2"] = dz2.sum(axis=(0, 1, 2))
     g["W2"] = np.zeros_like(p["W2"])
     da1 = np.zeros_like(f["a1"])
@@ -152,7 +174,7 @@ def grad(theta, x, y, pos_weight):
         for kx in range(3):
             g["W2"][:, ky, kx, :] = np.einsum("nyxo,nyxc->oc", dz2, _shift(f["a1"], ky - 1, kx - 1))
             da1 += np.einsum("nyxo,oc->nyxc", _shift(dz2, 1 - ky, 1 - kx), p["W2"][:, ky, kx, :])
-    dz1 = da1 * (f["z1"] > 0)
+    dz1 = rnd(da1 * (f["z1"] > 0))
     g["b1"] = dz1.sum(axis=(0, 1, 2))
     g["W1"] = np.zeros_like(p["W1"])
     for ky in range(3):

@@ -33,11 +33,12 @@ class Error(RuntimeError):
 
 
 BC = {"periodic": 0, "outflow": 1}
-SWITCH = {"frozen": 0, "plain": 1}
+SWITCH = {"frozen": 0, "plain": 1, "learned": 2}
+CNN_PARAMS, CNN_CHANNELS = 10753, 16
 COUPLING = {"stage": 0, "step": 1}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 
-__all__ = ["Solver", "BatchSolver", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
+__all__ = ["Solver", "BatchSolver", "SwitchNet", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
 
 _ALPHA = (3.0 + 3.0 ** 0.5) / 6.0
 #: ARS(2,3,3) (Sec. 3.4): explicit (At, bt), implicit (A, b), alpha = (3+sqrt 3)/6.
@@ -230,6 +231,120 @@ class Solver:
 
     def sync(self):
         self._check(self._abi.esbgk_sync(self._ctx), "sync")
+
+    # -- learned switch --------------------------------------------------------
+    def set_switch_params(self, theta):
+        """Network parameters (CNN_PARAMS float32) of a 'learned' switch."""
+        th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(-1))
+        assert th.size == CNN_PARAMS
+        self._check(self._abi.esbgk_set_switch_params(self._ctx, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                    "set_switch_params")
+
+    def switch_stats(self):
+        j, p, m, e = (ctypes.c_longlong() for _ in range(4))
+        self._check(self._abi.esbgk_switch_stats(self._ctx, ctypes.byref(j), ctypes.byref(p), ctypes.byref(m),
+                                                 ctypes.byref(e)), "switch_stats")
+        return dict(judged=j.value, predicted=p.value, missed=m.value, extra=e.value)
+
+    def features(self, out=None):
+        """Network features of the current state as a (ny, nx, 16) bf16
+        device tensor (written into `out` when given)."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty((self.ny, self.nx, CNN_CHANNELS), dtype=torch.bfloat16, device=self.device)
+        assert out.dtype == torch.bfloat16 and out.is_contiguous() and out.numel() == self.nc * CNN_CHANNELS
+        self._check(self._abi.esbgk_features(self._ctx, ctypes.c_void_p(out.data_ptr())), "features")
+        return out
+
+
+class SwitchNet:
+    """Training and evaluation of the learned-switch network (esbgk_cnn_*) on
+    batches of up to max_images images of H x W cells: features (n, H, W, 16)
+    bf16 and labels (n, H, W) uint8, torch device tensors."""
+
+    def __init__(self, max_images, H, W, device=None, stream=None):
+        import torch
+        _abi = _lib()
+        self._abi = _abi
+        self.torch = torch
+        self.max_images, self.H, self.W = int(max_images), int(H), int(W)
+        nbytes = _abi.esbgk_cnn_workspace_bytes(self.max_images, self.H, self.W)
+        if nbytes == 0:
+            raise Error(-1, "invalid network batch shape")
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._c = ctypes.c_void_p()
+        r = _abi.esbgk_cnn_create(self.max_images, self.H, self.W, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._c))
+        if r != 0:
+            raise Error(r, "esbgk_cnn_create")
+
+    def close(self):
+        if getattr(self, "_c", None) and self._c.value:
+            self._abi.esbgk_cnn_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _fptr(a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+    def _chk(self, r, what):
+        if r != 0:
+            raise Error(r, what)
+
+    def _xy(self, x, y=None):
+        torch = self.torch
+        assert x.dtype == torch.bfloat16 and x.is_contiguous() and x.shape[1:] == (self.H, self.W, CNN_CHANNELS)
+        n = x.shape[0]
+        assert 1 <= n <= self.max_images
+        if y is not None:
+            assert y.dtype == torch.uint8 and y.is_contiguous() and tuple(y.shape) == (n, self.H, self.W)
+        return n
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(-1))
+        assert th.size == CNN_PARAMS
+        self._chk(self._abi.esbgk_cnn_set_params(self._c, self._fptr(th)), "set_params")
+
+    def params(self):
+        out = np.empty(CNN_PARAMS, np.float32)
+        self._chk(self._abi.esbgk_cnn_get_params(self._c, self._fptr(out)), "get_params")
+        return out
+
+    def forward(self, x):
+        """Logits (n, H, W) float32 device tensor."""
+        n = self._xy(x)
+        out = self.torch.empty((n, self.H, self.W), dtype=self.torch.float32, device=self.device)
+        self._chk(self._abi.esbgk_cnn_forward(self._c, ctypes.c_void_p(x.data_ptr()), n,
+                                              ctypes.c_void_p(out.data_ptr())), "forward")
+        return out
+
+    def gradient(self, x, y, pos_weight):
+        """(loss, gradient (CNN_PARAMS,) float32) without an update."""
+        n = self._xy(x, y)
+        g = np.empty(CNN_PARAMS, np.float32)
+        L = ctypes.c_float()
+        self._chk(self._abi.esbgk_cnn_gradient(self._c, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                               n, float(pos_weight), ctypes.byref(L), self._fptr(g)), "gradient")
+        return L.value, g
+
+    def train_step(self, x, y, pos_weight, lr, want_loss=False):
+        n = self._xy(x, y)
+        L = ctypes.c_float()
+        self._chk(self._abi.esbgk_cnn_train_step(self._c, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                                 n, float(pos_weight), float(lr),
+                                                 ctypes.byref(L) if want_loss else None), "train_step")
+        return L.value if want_loss else None
+
+    def sync(self):
+        self._chk(self._abi.esbgk_cnn_sync(self._c), "sync")
 
 
 class BatchSolver:

@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_WORKSPACE", -3: "E_CUDA", -4: "E_NO
                 -5: "E_TIMEOUT", -6: "E_STATE", -7: "E_TOO_LARGE"}
 FP64, FP32, BF16 = 0, 1, 2
 BC = {"periodic": 0, "outflow": 1}
-SWITCH = {"frozen": 0, "plain": 1}
+SWITCH = {"frozen": 0, "plain": 1, "learned": 2}
+CNN_PARAMS, CNN_CHANNELS = 10753, 16
 COUPLING = {"stage": 0, "step": 1}
 PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 KERNEL_CLASSES = ("l1", "flags", "compact", "prep", "stage", "final", "other")
@@ -109,6 +110,21 @@ _SIGS = {
     "esbgk_batch_timing": (I, [P, ctypes.c_int32]),
     "esbgk_batch_timing_read": (I, [P, D, LL, ctypes.c_int32]),
     "esbgk_batch_last_error": (I, [P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_set_switch_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_switch_stats": (I, [P, LL, LL, LL, LL]),
+    "esbgk_features": (I, [P, P]),
+    "esbgk_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "esbgk_cnn_create": (I, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_size_t, P,
+                             ctypes.POINTER(P)]),
+    "esbgk_cnn_destroy": (None, [P]),
+    "esbgk_cnn_set_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_cnn_get_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_cnn_forward": (I, [P, P, ctypes.c_int32, P]),
+    "esbgk_cnn_gradient": (I, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_cnn_train_step": (I, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                 ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_cnn_sync": (I, [P]),
     "esbgk_kinetic_steps_noalloc": (I, [ctypes.POINTER(Grid), ctypes.POINTER(VMesh), ctypes.POINTER(Params),
                                         ctypes.c_double, ctypes.POINTER(Tableau), ctypes.c_int32, D, P, D, P]),
 }

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "esbgk.h"
+#include "cnn.h"
 #include "launch.h"
 
 using namespace esbgk;
@@ -34,12 +35,14 @@ const Launchers* launchers_for(int prec) {
 struct Layout {
   size_t F[3], ACC[3], Un, Us[2], Phi, eps, lamA, L1, stage5, red, tot;
   size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr;
+  // learned switch only: features, activations, logits, prediction, weights, statistics
+  size_t cx, ca1, ca2, logits, pred, cnnw, sctr;
   size_t total;
 };
 
 constexpr int kRedBlocks = 1024;
 
-Layout make_layout(int nc, int nvv, size_t elem) {
+Layout make_layout(int nc, int nvv, size_t elem, bool learned) {
   Layout L{};
   size_t p = 0;
   auto take = [&](size_t bytes) {
@@ -70,6 +73,15 @@ Layout make_layout(int nc, int nvv, size_t elem) {
   L.counts = take(4 * sizeof(int));
   L.err = take(sizeof(DevErr));
   L.ctr = take(2 * sizeof(long long));
+  if (learned) {
+    L.cx = take((size_t)nc * cnn::kCinPad * 2);
+    L.ca1 = take((size_t)nc * cnn::kHid * 2);
+    L.ca2 = take((size_t)nc * cnn::kHid * 2);
+    L.logits = take((size_t)nc * sizeof(float));
+    L.pred = take(nc);
+    L.cnnw = take(cnn::weights_bytes());
+    L.sctr = take(4 * sizeof(unsigned long long));
+  }
   L.total = p;
   return L;
 }
@@ -84,7 +96,7 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   if (v->nv < 2 || v->nv > 64 || !(v->vmax > 0)) return false;
   if (!(p->beta >= -0.5 && p->beta < 1.0) || !(p->tau > 0) || !(p->cweno_eps > 0)) return false;
   if (!(p->eta_factor >= 0) || !(p->delta >= 0)) return false;
-  if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN) return false;
+  if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN && p->sw != ESBGK_SWITCH_LEARNED) return false;
   if (p->coupling != ESBGK_COUPLE_STAGE && p->coupling != ESBGK_COUPLE_STEP) return false;
   return launchers_for(p->prec) != nullptr;
 }
@@ -126,6 +138,14 @@ struct esbgk_ctx {
   int cur;
   bool have_state, conv_pending;
   bool l1_fresh;  // L1 holds ||f^n - M_hat||_1 of the kinetic cells (from the last final combination)
+  // learned switch
+  __nv_bfloat16 *cx = nullptr, *ca1 = nullptr, *ca2 = nullptr;
+  float* logits = nullptr;
+  uint8_t* pred = nullptr;
+  cnn::Weights cw{};
+  unsigned long long* sctr = nullptr;
+  bool have_weights = false, have_pred = false;
+  bool criterion() const { return sw == ESBGK_SWITCH_PLAIN || sw == ESBGK_SWITCH_LEARNED; }
   long long steps;
   int status;
   long long bad_cell;
@@ -254,6 +274,19 @@ int regime_update(esbgk_ctx* X) {
     launch_flags(V, X->Un, X->L1, X->L1, X->lamA, X->flags, X->stream);
   }
   if ((r = after_launch(X, "flags kernel"))) return r;
+  if (X->sw == ESBGK_SWITCH_LEARNED) {
+    // the network's prediction for the next step joins the criterion's map;
+    // the previous prediction is judged against the criterion
+    Timed t(X, ESBGK_K_OTHER);
+    const double d = X->g.dx < X->g.dy ? X->g.dx : X->g.dy;
+    cnn::launch_features(X->Un, X->eps, X->g.nc, d, X->cx, X->stream);
+    cnn::launch_forward(X->cw, X->cx, 1, X->g.ny, X->g.nx, X->ca1, X->ca2, X->logits, X->stream);
+    cnn::launch_judge(X->flags, X->pred, X->logits, X->g.nc, X->have_pred ? 1 : 0, X->sctr, X->stream);
+  }
+  if (X->sw == ESBGK_SWITCH_LEARNED) {
+    if ((r = after_launch(X, "learned switch"))) return r;
+    X->have_pred = true;
+  }
   if ((r = compact(X))) return r;
   X->conv_pending = true;
   return ESBGK_OK;
@@ -393,7 +426,7 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.kin_u_moments = 1;
     A.ctr = X->ctr;
     // the deviation ||f^{n+1} - M_hat||_1 the next regime update needs
-    A.l1_out = X->sw == ESBGK_SWITCH_PLAIN ? X->L1 : nullptr;
+    A.l1_out = X->criterion() ? X->L1 : nullptr;
     PL.new_cur = X->cur;
   } else {
     PL.new_cur = prev_buf;
@@ -477,7 +510,9 @@ int esbgk_version(void) { return kVersion; }
 
 size_t esbgk_workspace_bytes(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_params* params) {
   if (!valid_inputs(grid, vmesh, params)) return 0;
-  return make_layout(grid->nx * grid->ny, vmesh->nv * vmesh->nv, launchers_for(params->prec)->elem).total;
+  return make_layout(grid->nx * grid->ny, vmesh->nv * vmesh->nv, launchers_for(params->prec)->elem,
+                     params->sw == ESBGK_SWITCH_LEARNED)
+      .total;
 }
 
 int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_params* params, void* workspace,
@@ -487,7 +522,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   if (!valid_inputs(grid, vmesh, params) || !workspace) return ESBGK_E_ARG;
   const Launchers* L = launchers_for(params->prec);
   const Geo g = make_geo(grid, vmesh);
-  const Layout lay = make_layout(g.nc, g.nvv, L->elem);
+  const Layout lay = make_layout(g.nc, g.nvv, L->elem, params->sw == ESBGK_SWITCH_LEARNED);
   if (workspace_bytes < lay.total || ((uintptr_t)workspace % kAlign) != 0) return ESBGK_E_WORKSPACE;
   esbgk_ctx* X = new (std::nothrow) esbgk_ctx();
   if (!X) return ESBGK_E_ARG;
@@ -528,6 +563,15 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->counts = (int*)(w + lay.counts);
   X->err = (DevErr*)(w + lay.err);
   X->ctr = (long long*)(w + lay.ctr);
+  if (X->sw == ESBGK_SWITCH_LEARNED) {
+    X->cx = (__nv_bfloat16*)(w + lay.cx);
+    X->ca1 = (__nv_bfloat16*)(w + lay.ca1);
+    X->ca2 = (__nv_bfloat16*)(w + lay.ca2);
+    X->logits = (float*)(w + lay.logits);
+    X->pred = w + lay.pred;
+    cnn::carve_weights(w + lay.cnnw, X->cw);
+    X->sctr = (unsigned long long*)(w + lay.sctr);
+  }
   X->cur = 0;
   X->bad_cell = -1;
   int dev = 0, nsm = 0;
@@ -545,6 +589,8 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   if (!r) r = cuda_check(X, cudaMemsetAsync(X->Phi, 0, lay.stage5 - lay.Phi, X->stream), "clear arrays");
   // f of cells that are never kinetic is never written: start it at zero
   if (!r) r = cuda_check(X, cudaMemsetAsync(w + lay.F[0], 0, lay.Un - lay.F[0], X->stream), "clear f arrays");
+  if (!r && X->sctr)
+    r = cuda_check(X, cudaMemsetAsync(X->sctr, 0, 4 * sizeof(unsigned long long), X->stream), "clear statistics");
   if (r) {
     delete X;
     return r;
@@ -591,6 +637,7 @@ int esbgk_set_state(esbgk_ctx* X, const double* rho, const double* ux, const dou
   X->have_state = true;
   X->conv_pending = false;
   X->l1_fresh = false;
+  X->have_pred = false;
   return ESBGK_OK;
 }
 
@@ -635,7 +682,50 @@ int esbgk_get_f(esbgk_ctx* X, double* f) {
 int esbgk_regime_update(esbgk_ctx* X) {
   GUARD(X);
   NEED_STATE(X);
+  if (X->sw == ESBGK_SWITCH_LEARNED && !X->have_weights)
+    return fail(X, ESBGK_E_STATE, "regime update: learned switch without network parameters");
   return regime_update(X);
+}
+
+int esbgk_set_switch_params(esbgk_ctx* X, const float* theta) {
+  GUARD(X);
+  if (!theta) return ESBGK_E_ARG;
+  if (X->sw != ESBGK_SWITCH_LEARNED) return fail(X, ESBGK_E_STATE, "set_switch_params: not a learned-switch context");
+  int r = cuda_check(X, cudaMemcpyAsync(X->cw.theta, theta, cnn::kParams * sizeof(float), cudaMemcpyHostToDevice,
+                                        X->stream),
+                     "network parameters");
+  if (r) return r;
+  cnn::launch_pack(X->cw, X->stream);
+  if ((r = after_launch(X, "pack network parameters"))) return r;
+  if ((r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_switch_params sync"))) return r;
+  X->have_weights = true;
+  X->have_pred = false;
+  return ESBGK_OK;
+}
+
+int esbgk_switch_stats(esbgk_ctx* X, long long* judged_cells, long long* predicted, long long* missed,
+                       long long* extra) {
+  GUARD(X);
+  unsigned long long c[4] = {0, 0, 0, 0};
+  if (X->sctr) {
+    int r = cuda_check(X, cudaMemcpyAsync(c, X->sctr, sizeof c, cudaMemcpyDeviceToHost, X->stream), "stats copy");
+    if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "stats sync");
+    if (r) return r;
+  }
+  if (predicted) *predicted = (long long)c[0];
+  if (missed) *missed = (long long)c[1];
+  if (extra) *extra = (long long)c[2];
+  if (judged_cells) *judged_cells = (long long)c[3];
+  return ESBGK_OK;
+}
+
+int esbgk_features(esbgk_ctx* X, void* x) {
+  GUARD(X);
+  NEED_STATE(X);
+  if (!x || ((uintptr_t)x % 16) != 0) return ESBGK_E_ARG;
+  const double d = X->g.dx < X->g.dy ? X->g.dx : X->g.dy;
+  cnn::launch_features(X->Un, X->eps, X->g.nc, d, (__nv_bfloat16*)x, X->stream);
+  return after_launch(X, "features kernel");
 }
 
 int esbgk_set_flags(esbgk_ctx* X, const uint8_t* kinetic) {
@@ -682,7 +772,9 @@ int esbgk_step(esbgk_ctx* X, double dt, const esbgk_tableau* tab) {
   GUARD(X);
   NEED_STATE(X);
   if (!(dt > 0) || !std::isfinite(dt) || !valid_tableau(tab)) return fail(X, ESBGK_E_ARG, "step: bad dt or tableau");
-  if (X->sw == ESBGK_SWITCH_PLAIN) {
+  if (X->sw == ESBGK_SWITCH_LEARNED && !X->have_weights)
+    return fail(X, ESBGK_E_STATE, "step: learned switch without network parameters");
+  if (X->criterion()) {
     const int r = regime_update(X);
     if (r) return r;
   }
@@ -896,7 +988,9 @@ bool batch_layout(int n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes, co
   long long cells = 0;
   B.case_off.resize(n);
   for (int i = 0; i < n; ++i) {
-    if (!valid_inputs(&grids[i], &vmeshes[i], &params[i]) || params[i].prec != params[0].prec) return false;
+    if (!valid_inputs(&grids[i], &vmeshes[i], &params[i]) || params[i].prec != params[0].prec ||
+        params[i].sw == ESBGK_SWITCH_LEARNED)
+      return false;
     B.case_off[i] = p;
     p += up(esbgk_workspace_bytes(&grids[i], &vmeshes[i], &params[i]));
     cells += (long long)grids[i].nx * grids[i].ny;
@@ -950,7 +1044,7 @@ CaseRegime regime_of(esbgk_batch* b, int i) {
   R.clist = X->clist;
   R.counts = X->counts;
   R.l1_fresh = b->d_l1_fresh + i;
-  R.plain = X->sw == ESBGK_SWITCH_PLAIN;
+  R.plain = X->criterion();
   return R;
 }
 
@@ -1430,10 +1524,10 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
 
   noalloc_init_kernel<<<(g.nc + 255) / 256, 256, 0, X.stream>>>(X.klist, X.counts, X.err, X.ctr, g.nc);
   if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
-  if (nsteps == 0) {
-    L->moments(f, U, X.view(), X.grid_stage, X.stream);
-    if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
-  }
+  // U^n from f: the steps read it (reference velocity of the moment sums,
+  // the stage-start copy), and the caller's U is an output only
+  L->moments(f, U, X.view(), X.grid_stage, X.stream);
+  if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
   for (int n = 0; n < nsteps; ++n) {
     const int r = advance(&X, dt, tab);
     if (r) return r;

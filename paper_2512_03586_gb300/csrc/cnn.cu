@@ -1,0 +1,648 @@
+// cnn.cu -- the learned regime switch: a 3-layer convolutional network that
+// predicts from the macroscopic state of a 5 x 5 neighbourhood the flag the
+// criterion of Sec. 3.1.2 will give a cell at the next step.  Forward pass,
+// backward pass (input and weight gradients), class-weighted cross-entropy
+// and Adam, all hand-written.  The two 3 x 3 convolutions are implicit GEMMs
+// on the tensor cores (bf16 operands, float32 accumulation,
+// mma.sync.m16n8k16); the 1 x 1 head, the loss and the optimizer are float32
+// on the CUDA cores.
+//
+// Tiling: a CTA owns 8 x 16 output cells of one image; its 4 warps own two
+// rows of 16 cells each (one m16 tile per row) and all 32 output channels
+// (four n8 tiles).  The input halo (10 x 18 cells, channels contiguous, cell
+// stride padded by 8 bf16 so that the fragment loads of the 8 row groups
+// fall in distinct banks) and the whole weight matrix are staged in shared
+// memory; the GEMM depth runs over 9 taps x the input channels.
+#include "cnn.h"
+
+#include <string>
+
+#include "../../include/esbgk.h"
+
+namespace esbgk {
+namespace cnn {
+
+namespace {
+
+using bf = __nv_bfloat16;
+constexpr int TH = 8, TW = 16, HH = TH + 2, HW = TW + 2;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ uint32_t ld32(const bf* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t pack2(bf lo, bf hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// D += A (16x16, row) * B (16x8, col), bf16 in, float32 accumulate.
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Stage the (TH+2) x (TW+2) halo of an input tile ([img][H][W][CIN] bf16)
+// into shared memory with cell stride CS; zeros outside the image.
+template <int CIN, int CS>
+__device__ void load_halo(const bf* __restrict__ in, int img, int H, int W, int ty0, int tx0, bf* s) {
+  constexpr int P = CIN / 2;
+  for (int i = threadIdx.x; i < HH * HW * P; i += blockDim.x) {
+    const int cell = i / P, pr = i % P;
+    const int gy = ty0 + cell / HW - 1, gx = tx0 + cell % HW - 1;
+    uint32_t v = 0;
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = ld32(in + (((size_t)img * H + gy) * W + gx) * CIN + 2 * pr);
+    *reinterpret_cast<uint32_t*>(s + cell * CS + 2 * pr) = v;
+  }
+}
+
+enum { kFwd = 0, kDgrad = 1 };
+
+// out[cell][o] = sum_{tap, c} in[cell + off(tap)][c] * wk[o][tap*CIN + c]
+// (+ bias, relu) -- MODE kFwd: relu(acc + bias[o]); kDgrad: acc masked by
+// (mask[cell][o] > 0), the relu derivative of the layer below.
+template <int CIN, int MODE>
+__global__ void __launch_bounds__(kThreads) conv_kernel(const bf* __restrict__ in, const bf* __restrict__ wk,
+                                                        const float* __restrict__ bias, int H, int W,
+                                                        bf* __restrict__ out, const bf* __restrict__ mask) {
+  constexpr int CS = CIN + 8, K = 9 * CIN, KS = K + 8;
+  __shared__ __align__(16) bf s_in[HH * HW * CS];
+  __shared__ __align__(16) bf s_w[kHid * KS];
+  __shared__ float s_b[kHid];
+  const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH, img = blockIdx.z;
+  for (int i = threadIdx.x; i < kHid * K / 2; i += blockDim.x) {
+    const int o = i / (K / 2), k = 2 * (i % (K / 2));
+    *reinterpret_cast<uint32_t*>(s_w + o * KS + k) = ld32(wk + o * K + k);
+  }
+  if (threadIdx.x < kHid) s_b[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+  load_halo<CIN, CS>(in, img, H, W, ty0, tx0, s_in);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
+
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+    for (int kc = 0; kc < CIN / 16; ++kc) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int hrow = 2 * warp + m + ky;
+        const bf* p0 = s_in + (hrow * HW + g + kx) * CS + kc * 16 + 2 * q;
+        const bf* p1 = p0 + 8 * CS;
+        a[m][0] = ld32(p0);
+        a[m][1] = ld32(p1);
+        a[m][2] = ld32(p0 + 8);
+        a[m][3] = ld32(p1 + 8);
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const bf* pw = s_w + (n * 8 + g) * KS + tap * CIN + kc * 16 + 2 * q;
+        const uint32_t b[2] = {ld32(pw), ld32(pw + 8)};
+        mma16816(acc[0][n], a[0], b);
+        mma16816(acc[1][n], a[1], b);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int gy = ty0 + 2 * warp + m;
+    if (gy >= H) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gx = tx0 + g + 8 * h;
+      if (gx >= W) continue;
+      const size_t cell = ((size_t)img * H + gy) * W + gx;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const int o = n * 8 + 2 * q;
+        float v0 = acc[m][n][2 * h] + s_b[o], v1 = acc[m][n][2 * h + 1] + s_b[o + 1];
+        if (MODE == kFwd) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        } else {
+          const bf* mk = mask + cell * kHid + o;
+          if (!(__bfloat162float(mk[0]) > 0.f)) v0 = 0.f;
+          if (!(__bfloat162float(mk[1]) > 0.f)) v1 = 0.f;
+        }
+        *reinterpret_cast<uint32_t*>(out + cell * kHid + o) = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+      }
+    }
+  }
+}
+
+// Weight gradient of a 3 x 3 convolution, per CTA partial sums over the
+// tiles it owns (persistent loop):
+//   part[b][o][tap*CIN + c] = sum_cells dz[cell][o] * a[cell + off(tap)][c]
+//   part[b][32*9*CIN + o]   = sum_cells dz[cell][o]
+// GEMM with M = o (two m16 tiles), N = (tap, c), K = cells (a tile row of
+// 16 cells per k16 step); warp w owns the n8 tiles w, w+4, ...
+template <int CIN>
+__global__ void __launch_bounds__(kThreads) wgrad_kernel(const bf* __restrict__ dz, const bf* __restrict__ a, int N,
+                                                         int H, int W, float* __restrict__ part) {
+  constexpr int CS = CIN + 8, DS = kHid + 8;
+  constexpr int NT = 9 * CIN / 8, NPW = (NT + 3) / 4;
+  constexpr int LEN = kHid * 9 * CIN;
+  __shared__ __align__(16) bf s_a[HH * HW * CS];
+  __shared__ __align__(16) bf s_dz[TH * TW * DS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+  const int ntiles = tiles_x * tiles_y * N;
+  float acc[2][NPW][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NPW; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[m][j][e] = 0.f;
+  float dbias = 0.f;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int img = t / (tiles_x * tiles_y), r = t % (tiles_x * tiles_y);
+    const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
+    __syncthreads();  // the previous tile's reads are done
+    load_halo<CIN, CS>(a, img, H, W, ty0, tx0, s_a);
+    for (int i = threadIdx.x; i < TH * TW * (kHid / 2); i += blockDim.x) {
+      const int cell = i / (kHid / 2), pr = i % (kHid / 2);
+      const int gy = ty0 + cell / TW, gx = tx0 + cell % TW;
+      uint32_t v = 0;
+      if (gy < H && gx < W) v = ld32(dz + (((size_t)img * H + gy) * W + gx) * kHid + 2 * pr);
+      *reinterpret_cast<uint32_t*>(s_dz + cell * DS + 2 * pr) = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kHid)
+      for (int cell = 0; cell < TH * TW; ++cell) dbias += __bfloat162float(s_dz[cell * DS + threadIdx.x]);
+#pragma unroll 1
+    for (int kc = 0; kc < TH; ++kc) {  // tile row = k16 step
+      uint32_t af[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int o0 = 16 * m + g;
+        const bf* d0 = s_dz + (kc * TW + 2 * q) * DS;
+        af[m][0] = pack2(d0[o0], d0[DS + o0]);
+        af[m][1] = pack2(d0[o0 + 8], d0[DS + o0 + 8]);
+        af[m][2] = pack2(d0[8 * DS + o0], d0[9 * DS + o0]);
+        af[m][3] = pack2(d0[8 * DS + o0 + 8], d0[9 * DS + o0 + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < NPW; ++j) {
+        const int nt = warp + 4 * j;
+        if (nt < NT) {
+          const int n0 = 8 * nt, tap = n0 / CIN, c = n0 % CIN + g;
+          const int ky = tap / 3, kx = tap % 3;
+          const bf* h0 = s_a + ((kc + ky) * HW + 2 * q + kx) * CS + c;
+          const uint32_t b[2] = {pack2(h0[0], h0[CS]), pack2(h0[8 * CS], h0[9 * CS])};
+          mma16816(acc[0][j], af[0], b);
+          mma16816(acc[1][j], af[1], b);
+        }
+      }
+    }
+  }
+  float* P = part + (size_t)blockIdx.x * (LEN + kHid);
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NPW; ++j) {
+      const int nt = warp + 4 * j;
+      if (nt < NT) {
+        const int n = 8 * nt + 2 * q, o = 16 * m + g;
+        P[o * 9 * CIN + n] = acc[m][j][0];
+        P[o * 9 * CIN + n + 1] = acc[m][j][1];
+        P[(o + 8) * 9 * CIN + n] = acc[m][j][2];
+        P[(o + 8) * 9 * CIN + n + 1] = acc[m][j][3];
+      }
+    }
+  if (threadIdx.x < kHid) P[LEN + threadIdx.x] = dbias;
+}
+
+// Fixed-order sum of the per-CTA partials of layer L (1 or 2) into the
+// parameter-ordered gradient.
+template <int CIN>
+__global__ void reduce_wgrad_kernel(const float* __restrict__ part, int nparts, float* __restrict__ grad, int offW,
+                                    int offB, int cin_real) {
+  constexpr int LEN = kHid * 9 * CIN;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= LEN + kHid) return;
+  float s = 0.f;
+  for (int b = 0; b < nparts; ++b) s += part[(size_t)b * (LEN + kHid) + j];
+  if (j >= LEN) {
+    grad[offB + (j - LEN)] = s;
+    return;
+  }
+  const int o = j / (9 * CIN), r = j % (9 * CIN), tap = r / CIN, c = r % CIN;
+  if (c < cin_real) grad[offW + (o * 9 + tap) * cin_real + c] = s;
+}
+
+// 1 x 1 head: z = b3 + a2 . w3 per cell.  With labels: the class-weighted
+// cross-entropy w (softplus(z) - y z) / M, dz = w (sigmoid(z) - y) / M,
+// dL/da2 -> dz2 = dz w3 (a2 > 0) (bf16), and per-block partial sums of
+// dL/dw3 = dz a2, dL/db3 = dz and the loss.
+constexpr int kHeadThreads = 256, kHeadPart = kHid + 2;
+__global__ void __launch_bounds__(kHeadThreads) head_kernel(const bf* __restrict__ a2, const float* __restrict__ theta,
+                                                            int M, float* __restrict__ logits,
+                                                            const uint8_t* __restrict__ y, float pos_weight,
+                                                            float invM, bf* __restrict__ dz2, float* __restrict__ part) {
+  __shared__ float s_red[kHeadThreads / 32][kHeadPart];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* w3 = theta + kOffW3;
+  float av[kHid];
+  float z = 0.f, dz = 0.f, L = 0.f;
+  if (i < M) {
+    const uint4* src = reinterpret_cast<const uint4*>(a2 + (size_t)i * kHid);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint4 u = src[v];
+      const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        av[8 * v + 2 * k] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w4[k] & 0xffffu)));
+        av[8 * v + 2 * k + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w4[k] >> 16)));
+      }
+    }
+    z = theta[kOffB3];
+#pragma unroll
+    for (int c = 0; c < kHid; ++c) z = fmaf(av[c], w3[c], z);
+    logits[i] = z;
+    if (y) {
+      const float yy = y[i] ? 1.f : 0.f, w = y[i] ? pos_weight : 1.f;
+      const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));  // softplus, stable
+      const float sig = 1.f / (1.f + expf(-z));
+      L = w * (sp - yy * z) * invM;
+      dz = w * (sig - yy) * invM;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(dz2 + (size_t)i * kHid);
+#pragma unroll
+      for (int c = 0; c < kHid; c += 2) {
+        const float g0 = av[c] > 0.f ? dz * w3[c] : 0.f, g1 = av[c + 1] > 0.f ? dz * w3[c + 1] : 0.f;
+        dst[c / 2] = pack2(__float2bfloat16_rn(g0), __float2bfloat16_rn(g1));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kHid; ++c) av[c] = 0.f;
+  }
+  if (!y) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float vals[kHeadPart];
+#pragma unroll
+  for (int c = 0; c < kHid; ++c) vals[c] = dz * av[c];
+  vals[kHid] = dz;
+  vals[kHid + 1] = L;
+#pragma unroll
+  for (int c = 0; c < kHeadPart; ++c) {
+    float v = vals[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kHeadPart) {
+    float s = 0.f;
+    for (int w = 0; w < kHeadThreads / 32; ++w) s += s_red[w][threadIdx.x];
+    part[(size_t)blockIdx.x * kHeadPart + threadIdx.x] = s;
+  }
+}
+
+__global__ void reduce_head_kernel(const float* __restrict__ part, int nparts, float* __restrict__ grad,
+                                   float* __restrict__ loss) {
+  const int j = threadIdx.x;
+  if (j >= kHeadPart) return;
+  float s = 0.f;
+  for (int b = 0; b < nparts; ++b) s += part[(size_t)b * kHeadPart + j];
+  if (j < kHid)
+    grad[kOffW3 + j] = s;
+  else if (j == kHid)
+    grad[kOffB3] = s;
+  else
+    *loss = s;
+}
+
+// bf16 GEMM operands of the convolutions from the float32 parameters.
+__device__ __forceinline__ void pack_one(const Weights& w, int j, float v) {
+  if (j < kOffB1) {
+    const int o = j / (9 * kCin), r = j % (9 * kCin), tap = r / kCin, c = r % kCin;
+    w.w1f[o * kK1 + tap * kCinPad + c] = __float2bfloat16_rn(v);
+  } else if (j >= kOffW2 && j < kOffB2) {
+    const int jj = j - kOffW2, o = jj / (9 * kHid), r = jj % (9 * kHid), tap = r / kHid, c = r % kHid;
+    const bf b = __float2bfloat16_rn(v);
+    w.w2f[o * kK2 + tap * kHid + c] = b;
+    w.w2d[c * kK2 + (8 - tap) * kHid + o] = b;
+  }
+}
+
+__global__ void pack_kernel(Weights w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < kParams) pack_one(w, j, w.theta[j]);
+}
+
+// Adam (Kingma & Ba 2015) with bias correction c1 = 1/(1 - b1^t),
+// c2 = 1/(1 - b2^t) computed on the host; then the bf16 operands.
+__global__ void adam_kernel(Weights w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+                            float lr, float b1, float b2, float c1, float c2, float eps) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kParams) return;
+  const float gj = g[j];
+  const float mj = b1 * m[j] + (1.f - b1) * gj;
+  const float vj = b2 * v[j] + (1.f - b2) * gj * gj;
+  m[j] = mj;
+  v[j] = vj;
+  const float th = w.theta[j] - lr * (mj * c1) / (sqrtf(vj * c2) + eps);
+  w.theta[j] = th;
+  pack_one(w, j, th);
+}
+
+// Features of a cell: (log rho, s u_x, s u_y, log T, log10(eps s^2)) from
+// U, s = dx_ref / dx: the criterion of Sec. 3.1.2 (divided by eps) sees
+// velocity jumps over 2 dx and eps times squared temperature jumps over
+// 2 dx, so these channels present the same physical state identically on
+// every grid spacing.
+__global__ void features_kernel(const double* __restrict__ U, const double* __restrict__ eps, int nc, double scale,
+                                bf* __restrict__ x) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double rho = U[c], ux = U[nc + c] / rho, uy = U[2 * (size_t)nc + c] / rho;
+  const double T = (U[3 * (size_t)nc + c] - 0.5 * rho * (ux * ux + uy * uy)) / rho;
+  const float f[5] = {(float)log(rho), (float)(scale * ux), (float)(scale * uy), (float)log(T),
+                      (float)log10(eps[c] * scale * scale)};
+  uint32_t w[8];
+  w[0] = pack2(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
+  w[1] = pack2(__float2bfloat16_rn(f[2]), __float2bfloat16_rn(f[3]));
+  w[2] = pack2(__float2bfloat16_rn(f[4]), __float2bfloat16_rn(0.f));
+#pragma unroll
+  for (int k = 3; k < 8; ++k) w[k] = 0u;
+  uint4* dst = reinterpret_cast<uint4*>(x + (size_t)c * kCinPad);
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+__global__ void judge_kernel(uint8_t* __restrict__ flags, uint8_t* __restrict__ pred, const float* __restrict__ logits,
+                             int nc, int have_prev, unsigned long long* __restrict__ counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned p = 0, miss = 0, extra = 0, cells = 0;
+  if (c < nc) {
+    const uint8_t qf = flags[c];
+    const uint8_t nxt = logits[c] > 0.f ? 1 : 0;
+    if (have_prev) {
+      const uint8_t pp = pred[c];
+      p = pp;
+      miss = qf && !pp;
+      extra = pp && !qf;
+      cells = 1;
+    }
+    flags[c] = (qf || nxt) ? 1 : 0;
+    pred[c] = nxt;
+  }
+  const unsigned full = 0xffffffffu;
+  p = __reduce_add_sync(full, p);
+  miss = __reduce_add_sync(full, miss);
+  extra = __reduce_add_sync(full, extra);
+  cells = __reduce_add_sync(full, cells);
+  if ((threadIdx.x & 31) == 0 && cells) {
+    atomicAdd(counters + 0, (unsigned long long)p);
+    atomicAdd(counters + 1, (unsigned long long)miss);
+    atomicAdd(counters + 2, (unsigned long long)extra);
+    atomicAdd(counters + 3, (unsigned long long)cells);
+  }
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t weights_bytes() {
+  return up256(kParams * sizeof(float)) + up256(kHid * kK1 * 2) + 2 * up256(kHid * kK2 * 2);
+}
+
+size_t carve_weights(unsigned char* p, Weights& w) {
+  size_t o = 0;
+  w.theta = (float*)(p + o);
+  o += up256(kParams * sizeof(float));
+  w.w1f = (bf*)(p + o);
+  o += up256(kHid * kK1 * 2);
+  w.w2f = (bf*)(p + o);
+  o += up256(kHid * kK2 * 2);
+  w.w2d = (bf*)(p + o);
+  o += up256(kHid * kK2 * 2);
+  return o;
+}
+
+void launch_pack(const Weights& w, cudaStream_t s) {
+  cudaMemsetAsync(w.w1f, 0, kHid * kK1 * 2, s);  // padded input channels stay zero
+  pack_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(w);
+}
+
+void launch_features(const double* U, const double* eps, int nc, double dx, bf* x, cudaStream_t s) {
+  features_kernel<<<(nc + 255) / 256, 256, 0, s>>>(U, eps, nc, kDxRef / dx, x);
+}
+
+static dim3 conv_grid(int n, int H, int W) { return dim3((W + TW - 1) / TW, (H + TH - 1) / TH, n); }
+
+void launch_forward(const Weights& w, const bf* x, int n, int H, int W, bf* a1, bf* a2, float* logits,
+                    cudaStream_t s) {
+  conv_kernel<kCinPad, kFwd><<<conv_grid(n, H, W), kThreads, 0, s>>>(x, w.w1f, w.theta + kOffB1, H, W, a1, nullptr);
+  conv_kernel<kHid, kFwd><<<conv_grid(n, H, W), kThreads, 0, s>>>(a1, w.w2f, w.theta + kOffB2, H, W, a2, nullptr);
+  const int M = n * H * W;
+  head_kernel<<<(M + kHeadThreads - 1) / kHeadThreads, kHeadThreads, 0, s>>>(a2, w.theta, M, logits, nullptr, 0.f,
+                                                                            0.f, nullptr, nullptr);
+}
+
+void launch_judge(uint8_t* flags, uint8_t* pred, const float* logits, int nc, int have_prev,
+                  unsigned long long* counters, cudaStream_t s) {
+  judge_kernel<<<(nc + 255) / 256, 256, 0, s>>>(flags, pred, logits, nc, have_prev, counters);
+}
+
+}  // namespace cnn
+}  // namespace esbgk
+
+// ---------------------------------------------------------------------------
+// Training object (C ABI).
+
+using namespace esbgk::cnn;
+
+struct esbgk_cnn {
+  int max_n, H, W;
+  cudaStream_t stream;
+  Weights w;
+  float *m, *v, *grad, *logits, *part, *loss;
+  __nv_bfloat16 *a1, *a2, *dz2, *dz1;
+  int nparts;  // CTAs of the weight-gradient kernels
+  long long t;
+  std::string msg;
+};
+
+namespace {
+
+struct CnnLayout {
+  size_t w, m, v, grad, logits, part, loss, a1, a2, dz2, dz1, total;
+  int nparts;
+};
+
+bool cnn_layout(int max_n, int H, int W, CnnLayout& L) {
+  if (max_n < 1 || H < 1 || W < 1) return false;
+  const long long M = (long long)max_n * H * W;
+  if (M >= (1LL << 28)) return false;
+  L.nparts = 2 * 152;
+  size_t p = 0;
+  auto take = [&](size_t b) {
+    const size_t at = p;
+    p += up256(b);
+    return at;
+  };
+  L.w = take(weights_bytes());
+  L.m = take(kParams * 4);
+  L.v = take(kParams * 4);
+  L.grad = take(kParams * 4);
+  L.logits = take(M * 4);
+  const size_t head_parts = (size_t)((M + kHeadThreads - 1) / kHeadThreads) * kHeadPart;
+  const size_t wg_parts = (size_t)L.nparts * (kHid * kK2 + kHid);
+  L.part = take(4 * (head_parts > wg_parts ? head_parts : wg_parts));
+  L.loss = take(4);
+  L.a1 = take(M * kHid * 2);
+  L.a2 = take(M * kHid * 2);
+  L.dz2 = take(M * kHid * 2);
+  L.dz1 = take(M * kHid * 2);
+  L.total = p;
+  return true;
+}
+
+int cnn_check(esbgk_cnn* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return ESBGK_OK;
+  c->msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return ESBGK_E_CUDA;
+}
+
+// Forward and backward passes of n images: gradient into c->grad, loss
+// into c->loss (device).
+void backward_launches(esbgk_cnn* c, const __nv_bfloat16* x, const uint8_t* y, int n, float pos_weight) {
+  const int H = c->H, W = c->W, M = n * H * W;
+  cudaStream_t s = c->stream;
+  const dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
+  conv_kernel<kCinPad, kFwd><<<grid, kThreads, 0, s>>>(x, c->w.w1f, c->w.theta + kOffB1, H, W, c->a1, nullptr);
+  conv_kernel<kHid, kFwd><<<grid, kThreads, 0, s>>>(c->a1, c->w.w2f, c->w.theta + kOffB2, H, W, c->a2, nullptr);
+  const int hb = (M + kHeadThreads - 1) / kHeadThreads;
+  head_kernel<<<hb, kHeadThreads, 0, s>>>(c->a2, c->w.theta, M, c->logits, y, pos_weight, 1.f / M, c->dz2, c->part);
+  reduce_head_kernel<<<1, 64, 0, s>>>(c->part, hb, c->grad, c->loss);
+  wgrad_kernel<kHid><<<c->nparts, kThreads, 0, s>>>(c->dz2, c->a1, n, H, W, c->part);
+  reduce_wgrad_kernel<kHid><<<(kHid * kK2 + kHid + 255) / 256, 256, 0, s>>>(c->part, c->nparts, c->grad, kOffW2,
+                                                                            kOffB2, kHid);
+  conv_kernel<kHid, kDgrad><<<grid, kThreads, 0, s>>>(c->dz2, c->w.w2d, nullptr, H, W, c->dz1, c->a1);
+  wgrad_kernel<kCinPad><<<c->nparts, kThreads, 0, s>>>(c->dz1, x, n, H, W, c->part);
+  reduce_wgrad_kernel<kCinPad><<<(kHid * kK1 + kHid + 255) / 256, 256, 0, s>>>(c->part, c->nparts, c->grad, kOffW1,
+                                                                              kOffB1, kCin);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t esbgk_cnn_workspace_bytes(int32_t max_images, int32_t H, int32_t W) {
+  CnnLayout L;
+  return cnn_layout(max_images, H, W, L) ? L.total : 0;
+}
+
+int esbgk_cnn_create(int32_t max_images, int32_t H, int32_t W, void* workspace, size_t workspace_bytes, void* stream,
+                     esbgk_cnn** out) {
+  if (!out) return ESBGK_E_ARG;
+  *out = nullptr;
+  CnnLayout L;
+  if (!cnn_layout(max_images, H, W, L) || !workspace) return ESBGK_E_ARG;
+  if (workspace_bytes < L.total || ((uintptr_t)workspace % 256) != 0) return ESBGK_E_WORKSPACE;
+  esbgk_cnn* c = new (std::nothrow) esbgk_cnn();
+  if (!c) return ESBGK_E_ARG;
+  unsigned char* p = (unsigned char*)workspace;
+  c->max_n = max_images;
+  c->H = H;
+  c->W = W;
+  c->stream = (cudaStream_t)stream;
+  carve_weights(p + L.w, c->w);
+  c->m = (float*)(p + L.m);
+  c->v = (float*)(p + L.v);
+  c->grad = (float*)(p + L.grad);
+  c->logits = (float*)(p + L.logits);
+  c->part = (float*)(p + L.part);
+  c->loss = (float*)(p + L.loss);
+  c->a1 = (__nv_bfloat16*)(p + L.a1);
+  c->a2 = (__nv_bfloat16*)(p + L.a2);
+  c->dz2 = (__nv_bfloat16*)(p + L.dz2);
+  c->dz1 = (__nv_bfloat16*)(p + L.dz1);
+  c->nparts = L.nparts;
+  c->t = 0;
+  const cudaError_t e = cudaMemsetAsync(workspace, 0, L.total, c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return ESBGK_E_CUDA;
+  }
+  *out = c;
+  return ESBGK_OK;
+}
+
+void esbgk_cnn_destroy(esbgk_cnn* c) { delete c; }
+
+int esbgk_cnn_set_params(esbgk_cnn* c, const float* theta) {
+  if (!c || !theta) return ESBGK_E_ARG;
+  int r = cnn_check(c, cudaMemcpyAsync(c->w.theta, theta, kParams * 4, cudaMemcpyHostToDevice, c->stream), "params");
+  if (!r) r = cnn_check(c, cudaMemsetAsync(c->m, 0, kParams * 4, c->stream), "adam state");
+  if (!r) r = cnn_check(c, cudaMemsetAsync(c->v, 0, kParams * 4, c->stream), "adam state");
+  if (r) return r;
+  launch_pack(c->w, c->stream);
+  c->t = 0;
+  r = cnn_check(c, cudaGetLastError(), "pack");
+  return r ? r : cnn_check(c, cudaStreamSynchronize(c->stream), "set_params sync");
+}
+
+int esbgk_cnn_get_params(esbgk_cnn* c, float* theta) {
+  if (!c || !theta) return ESBGK_E_ARG;
+  int r = cnn_check(c, cudaMemcpyAsync(theta, c->w.theta, kParams * 4, cudaMemcpyDeviceToHost, c->stream), "params");
+  return r ? r : cnn_check(c, cudaStreamSynchronize(c->stream), "get_params sync");
+}
+
+int esbgk_cnn_forward(esbgk_cnn* c, const void* x, int32_t n, float* logits) {
+  if (!c || !x || !logits || n < 1 || n > c->max_n) return ESBGK_E_ARG;
+  launch_forward(c->w, (const __nv_bfloat16*)x, n, c->H, c->W, c->a1, c->a2, logits, c->stream);
+  return cnn_check(c, cudaGetLastError(), "cnn forward");
+}
+
+int esbgk_cnn_gradient(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n, float pos_weight, float* loss,
+                       float* grad) {
+  if (!c || !x || !y || n < 1 || n > c->max_n || !(pos_weight > 0.f)) return ESBGK_E_ARG;
+  backward_launches(c, (const __nv_bfloat16*)x, y, n, pos_weight);
+  int r = cnn_check(c, cudaGetLastError(), "cnn backward");
+  if (!r && grad)
+    r = cnn_check(c, cudaMemcpyAsync(grad, c->grad, kParams * 4, cudaMemcpyDeviceToHost, c->stream), "grad copy");
+  if (!r && loss) r = cnn_check(c, cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream), "loss copy");
+  return r ? r : cnn_check(c, cudaStreamSynchronize(c->stream), "gradient sync");
+}
+
+int esbgk_cnn_train_step(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n, float pos_weight, float lr,
+                         float* loss) {
+  if (!c || !x || !y || n < 1 || n > c->max_n || !(pos_weight > 0.f) || !(lr > 0.f)) return ESBGK_E_ARG;
+  backward_launches(c, (const __nv_bfloat16*)x, y, n, pos_weight);
+  c->t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 / (1.0 - pow(b1, (double)c->t))), c2 = (float)(1.0 / (1.0 - pow(b2, (double)c->t)));
+  adam_kernel<<<(kParams + 255) / 256, 256, 0, c->stream>>>(c->w, c->m, c->v, c->grad, lr, (float)b1, (float)b2, c1,
+                                                            c2, 1e-8f);
+  int r = cnn_check(c, cudaGetLastError(), "cnn train step");
+  if (!r && loss) {
+    r = cnn_check(c, cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream), "loss copy");
+    if (!r) r = cnn_check(c, cudaStreamSynchronize(c->stream), "train sync");
+  }
+  return r;
+}
+
+int esbgk_cnn_sync(esbgk_cnn* c) {
+  if (!c) return ESBGK_E_ARG;
+  return cnn_check(c, cudaStreamSynchronize(c->stream), "cnn sync");
+}
+
+}  // extern "C"

@@ -102,12 +102,40 @@ def test_features_closed_form():
     T = np.array([[2.0, 0.25]])
     U = np.stack([rho, rho * ux, rho * uy, 0.5 * rho * (ux ** 2 + uy ** 2) + rho * T])
     eps = np.array([[1e-2, 1e-4]])
+    # on the reference grid: (log rho, u, log T, log10 eps)
     F = C.features(U, eps, 1.0 / 128)
     np.testing.assert_allclose(F[..., 0], np.log(rho))
     np.testing.assert_allclose(F[..., 1], ux, atol=1e-15)
     np.testing.assert_allclose(F[..., 2], uy, atol=1e-15)
     np.testing.assert_allclose(F[..., 3], np.log(T), atol=1e-14)
-    np.testing.assert_allclose(F[..., 4], [[np.log10(1.28), np.log10(0.0128)]], atol=1e-14)
+    np.testing.assert_allclose(F[..., 4], [[-2.0, -4.0]], atol=1e-14)
+    # four times finer: velocities x 4, eps x 16
+    F4 = C.features(U, eps, 1.0 / 512)
+    np.testing.assert_allclose(F4[..., 1], 4 * ux, atol=1e-15)
+    np.testing.assert_allclose(F4[..., 4], [[np.log10(0.16), np.log10(0.0016)]], atol=1e-14)
+
+
+def test_features_see_the_criterion_the_same_on_every_grid():
+    """The criterion of Sec. 3.1.2 on a linear velocity and temperature
+    profile, sampled on two grids: the same physical state gives the same
+    neighbour differences of the scaled velocity channel and the same
+    eps-channel-weighted temperature term."""
+    def state(n):
+        x = (np.arange(n) + 0.5) / n
+        X = np.tile(x, (3, 1))
+        ux = 0.2 * X
+        T = 1.0 + 0.5 * X
+        rho = np.ones_like(X)
+        U = np.stack([rho, rho * ux, 0 * ux, 0.5 * rho * ux ** 2 + rho * T])
+        return C.features(U, np.full_like(X, 1e-3), 1.0 / n)
+    for n in (128, 512):
+        F = state(n)
+        dux = (F[1, 2, 1] - F[1, 0, 1]) / 2          # per-cell difference of s u_x
+        assert abs(dux - 0.2 / 128) <= 1e-12          # = dx_ref * du/dx on every grid
+        s2eps = 10 ** F[1, 1, 4]                      # eps s^2
+        dT = (np.exp(F[1, 2, 3]) - np.exp(F[1, 0, 3])) / 2
+        # eps (dT/dx)^2 in reference units: eps s^2 (per-cell dT)^2 / dx_ref^2
+        assert abs(s2eps * dT ** 2 * 128 ** 2 - 1e-3 * 0.25) <= 1e-9
 
 
 def test_adam_first_step_is_signed_lr():

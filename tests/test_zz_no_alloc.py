@@ -52,7 +52,8 @@ def test_noalloc_matches_workspace_entry_point_two_calls(scheme):
     tab = G.make_tableau(scheme)
     f = torch.tensor(f0, dtype=torch.float64, device="cuda").contiguous()
     eps = torch.tensor(fl["eps"].reshape(-1), dtype=torch.float64, device="cuda")
-    U = torch.empty((4, f0.shape[0] * f0.shape[1]), dtype=torch.float64, device="cuda")
+    # U is an output: start it with garbage so that a read before the first write shows
+    U = torch.full((4, f0.shape[0] * f0.shape[1]), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     done = 0
     for n in (n1, n2):

@@ -100,6 +100,20 @@ def gaussian_blob(nx=256, ny=256, nv=48, vmax=8.0, eps=1e-3, steps=100, cfl=0.5,
                     kin=np.ones(rho.shape, bool)))
 
 
+def learned_switch_case(nx=512, ny=512, nv=32, vmax=8.0, seed=0, steps=200, cfl=0.5, blob_amp=0.5,
+                        blob_width=0.1, blob_centre=(0.3, 0.7), scheme="ars233"):
+    """Learned-switch deployment: the four-quadrant Riemann data of
+    riemann_quadrants (same eps field, outflow, starting all fluid) with a
+    Gaussian density blob of amplitude blob_amp and width blob_width added at
+    blob_centre; 'learned' switch, ARS(2,3,3)."""
+    wl = riemann_quadrants(nx=nx, ny=ny, nv=nv, vmax=vmax, seed=seed, steps=steps, cfl=cfl, scheme=scheme)
+    X, Y = _centres(nx, ny, 0, 1, 0, 1)
+    bump = blob_amp * np.exp(-((X - blob_centre[0]) ** 2 + (Y - blob_centre[1]) ** 2) / blob_width ** 2)
+    wl["fields"]["rho"] = wl["fields"]["rho"] * (1.0 + bump)
+    wl["params"] = dict(wl["params"], switch="learned")
+    return wl
+
+
 def order_test(n=90, nv=32, vmax=5.0, L=6.0, eps=1e-2, seed=0, kin_fraction=0.5,
                coupling="stage"):
     """Test 1 (Sec. 4.1.1): [0,6]^2 periodic, rho = 1 + 0.1 exp(-3 d^2),
