@@ -509,13 +509,137 @@ def batch_arm(args):
         dist.destroy_process_group()
 
 
+def learned_arm(args):
+    """Learned switch (deployment config): train the network on plain-criterion
+    histories of the four-quadrant Riemann recipe (128 x 128 cells, 32 x 32
+    velocities, 48 seeds), deploy it on 512 x 512 cells (Riemann data plus a
+    density blob) in FP32, and compare with the plain criterion in FP32 and
+    in FP64 on wall-clock per simulated time and on the macroscopic error
+    against an all-kinetic FP32 run of the same problem."""
+    import torch
+    import paper_2512_03586_gb300 as G
+    from paper_2512_03586_gb300 import switch_train as T
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    t0 = time.perf_counter()
+    train_cases = [W.riemann_quadrants(nx=128, ny=128, nv=32, seed=1000 + s, steps=args.train_steps)
+                   for s in range(args.train_seeds)]
+    X, Y = T.collect(train_cases, steps=args.train_steps, prec="fp32", device=dev)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    theta, hist = T.train(X, Y, T.init_params(0), epochs=30, batch=32, lr=3e-3, device=dev)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del X, Y
+
+    wl = W.learned_switch_case(seed=rank)
+    f = wl["fields"]
+    dt, nsim = wl["dt"], args.sim_steps
+    tab = G.make_tableau(wl["scheme"])
+    nvv = wl["vmesh"]["nv"] ** 2
+
+    def make(switch, prec, kin=None):
+        s = G.Solver(wl["grid"], wl["vmesh"], dict(wl["params"], switch=switch), prec=prec, device=dev)
+        s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"] if kin is None else kin)
+        if switch == "learned":
+            s.set_switch_params(theta)
+        return s
+
+    def run(s, n):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0 = s.counters()
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(n):
+            s.step(dt, tab)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        s.sync()
+        c1 = s.counters()
+        return ev0.elapsed_time(ev1), (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv
+
+    ref = make("frozen", "fp32", kin=np.ones_like(f["kin"]))
+    run(ref, nsim)
+    Uref = ref.cons()
+    ref.close()
+    err = lambda U: float(np.abs(U - Uref).sum() / np.abs(Uref).sum())
+    res = {}
+    for name, sw, prec in (("plain_fp64", "plain", "fp64"), ("plain_fp32", "plain", "fp32"),
+                           ("learned_fp32", "learned", "fp32")):
+        s = make(sw, prec)
+        ms, upd = run(s, nsim)
+        res[name] = {"ms_per_sim_time": ms / (nsim * dt), "ms_per_step": ms / nsim, "updates_per_s": upd / (ms * 1e-3),
+                     "error_vs_all_kinetic": err(s.cons()), "kinetic_cell_steps": upd // nvv // 3}
+        if sw == "learned":
+            res[name]["judge"] = s.switch_stats()
+            s.timing(True)
+            s.timing_read()
+            for _ in range(5):
+                s.step(dt, tab)
+            tk = s.timing_read()
+            s.timing(False)
+            res[name]["network_ms_per_step"] = tk["other"][0] / 5
+            res[name]["criterion_ms_per_step"] = (tk["l1"][0] + tk["flags"][0]) / 5
+            # kernels per step: l1, flags, 5 of the network (features, two convolutions, head, judge),
+            # categorize + compact, prep, stages and final combination
+            launches_per_step = (tk["l1"][1] + tk["flags"][1] + 5 * tk["other"][1] + 2 * tk["compact"][1]
+                                 + tk["prep"][1] + tk["stage"][1] + tk["final"][1]) / 5
+            learned = s
+        else:
+            s.close()
+
+    # timed region of the line: K steps of the learned FP32 form, L2 flushed between steps
+    for _ in range(args.warmup):
+        learned.step(dt, tab)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    c0 = learned.counters()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            learned.step(dt, tab)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = learned.counters()
+    value = (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv / (ms * 1e-3)
+    if rank != 0:
+        return
+    p64, l32 = res["plain_fp64"], res["learned_fp32"]
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "learned switch: 512x512 cells, 32x32 velocities on [-8,8]^2, four-quadrant Riemann "
+                                  "data plus a density blob at (0.3, 0.7), learned switch, ARS(2,3,3), fp32 storage",
+                      "training": "%d Riemann seeds x %d steps at 128x128 / 32x32 (plain criterion labels), "
+                                  "30 epochs Adam; collect %.1f s, train %.1f s, final loss %.4f" % (
+                                      args.train_seeds, args.train_steps, t_collect, t_train, hist[-1]),
+                      "comparison_steps": nsim,
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "comparison": res,
+           "learned_fp32_vs_plain_fp64": {"wall_per_sim_time_ratio": l32["ms_per_sim_time"] / p64["ms_per_sim_time"],
+                                          "error_ratio": l32["error_vs_all_kinetic"] / p64["error_vs_all_kinetic"]},
+           "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch", "learned"])
+    ap.add_argument("--train-seeds", type=int, default=48)
+    ap.add_argument("--train-steps", type=int, default=30)
+    ap.add_argument("--sim-steps", type=int, default=100, help="steps of the learned-switch comparison runs")
     ap.add_argument("--cases", type=int, default=64, help="cases of the batched workload")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-steps", type=int, default=8)
@@ -527,6 +651,8 @@ def main():
         reference_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "learned":
+        learned_arm(args)
     else:
         ours_arm(args)
 

@@ -17,6 +17,17 @@ import numpy as np
 from . import CNN_CHANNELS, Solver, SwitchNet
 
 
+def init_params(seed=0):
+    """Starting parameters (float32, layout of esbgk_set_switch_params):
+    He-normal convolution weights (std sqrt(2 / fan_in)), a head of std
+    sqrt(1 / 32), zero biases; seeded."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, np.sqrt(2.0 / 45.0), 32 * 9 * 5), np.zeros(32),
+             rng.normal(0.0, np.sqrt(2.0 / 288.0), 32 * 9 * 32), np.zeros(32),
+             rng.normal(0.0, np.sqrt(1.0 / 32.0), 32), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def collect(cases, steps=None, prec="fp32", every=1, device=None):
     """Features and next-step flags of plain-switch runs of `cases`:
     (X (n, ny, nx, 16) bf16, Y (n, ny, nx) uint8) device tensors."""
@@ -91,4 +102,4 @@ def evaluate(theta, X, Y, device=None):
     return out
 
 
-__all__ = ["collect", "positive_weight", "train", "evaluate", "CNN_CHANNELS"]
+__all__ = ["init_params", "collect", "positive_weight", "train", "evaluate", "CNN_CHANNELS"]

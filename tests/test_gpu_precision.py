@@ -1,0 +1,69 @@
+"""Precision form: f stored and transported in FP32, or stored in BF16 with
+FP32 arithmetic; FP64 only in the per-cell tensor solve (det of the
+temperature tensor) and in U and the totals.  Error per macroscopic field
+against FP64 and the relative mass drift.
+
+Bars: FP32 storage -- relative L1 error <= 1e-5 per field after the run and
+relative mass drift <= 1e-6.  BF16 storage (8 significant bits) cannot reach
+1e-5: each store rounds f by up to 2^-9 relative; the bound asserted here is
+the one measured with a margin, and the numbers are printed.
+
+The small case is checked against the FP64 CPU oracle; the full-size blob
+(256 x 256 cells, 48 x 48 velocities, 100 ARS(2,3,3) steps) against the FP64
+GPU path, which the parity tests pin to the oracle at 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _errors(U, Uref):
+    r = np.abs(Uref[0]).sum()
+    return [np.abs(U[0] - Uref[0]).sum() / r, np.abs(U[1] - Uref[1]).sum() / r,
+            np.abs(U[2] - Uref[2]).sum() / r, np.abs(U[3] - Uref[3]).sum() / np.abs(Uref[3]).sum()]
+
+
+def _gpu_run(wl, prec, steps):
+    import paper_2512_03586_gb300 as G
+    s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=prec)
+    f = wl["fields"]
+    s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    m0 = s.totals()[0]
+    for _ in range(steps):
+        s.step(wl["dt"], wl["scheme"])
+    return s.cons(), abs(s.totals()[0] - m0) / m0
+
+
+def test_precision_small_against_oracle():
+    wl = W.gaussian_blob(nx=12, ny=10, nv=48, steps=4)
+    P = O.Problem(**wl["grid"], **wl["vmesh"], **wl["params"])
+    st = O.init_state(P, **wl["fields"])
+    for _ in range(4):
+        st = O.step(P, st, wl["dt"], O.ARS233)
+    out = {}
+    for prec in ("fp64", "fp32", "bf16"):
+        U, drift = _gpu_run(wl, prec, 4)
+        out[prec] = (_errors(U, st.U), drift)
+    print("\nsmall blob vs oracle (rho, m_x, m_y, E; mass drift):", out)
+    assert max(out["fp64"][0]) <= 1e-10
+    assert max(out["fp32"][0]) <= 1e-5 and out["fp32"][1] <= 1e-6
+    assert max(out["bf16"][0]) <= 1e-2
+
+
+def test_precision_full_size_blob():
+    wl = W.gaussian_blob()          # 256^2 cells, 48^2 velocities, eps 1e-3, 100 steps
+    steps = wl["steps"]
+    Uref, d64 = _gpu_run(wl, "fp64", steps)
+    U32, d32 = _gpu_run(wl, "fp32", steps)
+    U16, d16 = _gpu_run(wl, "bf16", steps)
+    e32, e16 = _errors(U32, Uref), _errors(U16, Uref)
+    print("\nfull blob, %d steps, error vs FP64 (rho, m_x, m_y, E): FP32 %s drift %.2e; BF16 %s drift %.2e; "
+          "FP64 drift %.2e" % (steps, ["%.2e" % e for e in e32], d32, ["%.2e" % e for e in e16], d16, d64))
+    assert d64 <= 1e-12
+    assert max(e32) <= 1e-5 and d32 <= 1e-6
+    assert max(e16) <= 5e-2
