@@ -220,6 +220,8 @@ def ours_arm(args):
 
     wl = make_workload(args.workload, rank)
     f = wl["fields"]
+    # a non-default stream: repeated steps replay as CUDA graphs
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
     s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=args.prec, device=dev)
     s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
     tab = G.make_tableau(wl["scheme"])

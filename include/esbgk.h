@@ -158,9 +158,17 @@ int esbgk_get_indicators(esbgk_ctx* ctx, double* lamA, double* L1);
  * (Remark rem_coupling), final combination Eqs. RKEuler_2/RKEI2.  dt > 0. */
 int esbgk_advance(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
 
-/* One full step of Algorithm 1: esbgk_regime_update (PLAIN switch only) then
- * esbgk_advance.  Enqueued on the stream; does not wait. */
+/* One full step of Algorithm 1: esbgk_regime_update (PLAIN and LEARNED
+ * switches) then esbgk_advance.  Enqueued on the stream; does not wait.
+ * On a stream other than the legacy default stream, with timing off, a step
+ * whose launch arguments equal the previous step's is captured once into a
+ * CUDA graph; later steps with the same arguments replay it (the context
+ * keeps up to three graphs).  Results are identical either way. */
 int esbgk_step(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
+
+/* Enable (default) or disable graph replay in esbgk_step; drops the graphs
+ * kept so far.  Synchronises the stream. */
+int esbgk_graphs(esbgk_ctx* ctx, int32_t enable);
 
 /* Macroscopic fields of every cell (moments of f in kinetic cells, the Euler
  * solution elsewhere), each [N_c] float64; any pointer may be NULL. */

@@ -217,6 +217,10 @@ class Solver:
                                              ctypes.byref(b)), "counters")
         return dict(kinetic_cell_updates=u.value, steps=s.value, kinetic_cells=k.value, buffer_fills=b.value)
 
+    def graphs(self, enable=True):
+        """Enable or disable CUDA-graph replay of repeated steps."""
+        self._check(self._abi.esbgk_graphs(self._ctx, int(bool(enable))), "graphs")
+
     def timing(self, enable=True):
         """Bracket every library kernel with CUDA events on the stream."""
         self._check(self._abi.esbgk_timing(self._ctx, int(bool(enable))), "timing")

@@ -146,6 +146,23 @@ struct esbgk_ctx {
   unsigned long long* sctr = nullptr;
   bool have_weights = false, have_pred = false;
   bool criterion() const { return sw == ESBGK_SWITCH_PLAIN || sw == ESBGK_SWITCH_LEARNED; }
+  // CUDA graphs of whole steps, keyed by the bytes of every launch argument
+  struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    long long used = 0;
+  };
+  GraphEntry graphs[3];
+  std::vector<unsigned char> last_key;  // key of the previous un-captured step
+  bool graphs_on = true;
+  void drop_graphs() {
+    for (auto& e : graphs) {
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+      e.exec = nullptr;
+      e.key.clear();
+    }
+    last_key.clear();
+  }
   long long steps;
   int status;
   long long bad_cell;
@@ -162,6 +179,8 @@ struct esbgk_ctx {
   long long t_n[ESBGK_K_COUNT] = {0};
 
   ~esbgk_ctx() {
+    for (auto& e : graphs)
+      if (e.exec) cudaGraphExecDestroy(e.exec);
     for (auto& r : recs) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -260,13 +279,15 @@ int compact(esbgk_ctx* X) {
   return after_launch(X, "compaction");
 }
 
-int regime_update(esbgk_ctx* X) {
+// The launches of the regime update (no host synchronisation): the L1
+// deviation when no fresh value exists, the criterion, the learned switch's
+// prediction and judge, the compaction.
+int regime_launches(esbgk_ctx* X, bool l1_needed, bool judge_prev) {
   const View V = X->view();
-  if (!X->l1_fresh) {
+  if (l1_needed) {
     Timed t(X, ESBGK_K_L1);
     X->L->l1(X->F[X->cur], X->Un, X->L1, V, X->grid_stage, X->stream);
   }
-  X->l1_fresh = false;
   int r = after_launch(X, "l1 kernel");
   if (r) return r;
   {
@@ -281,14 +302,23 @@ int regime_update(esbgk_ctx* X) {
     const double d = X->g.dx < X->g.dy ? X->g.dx : X->g.dy;
     cnn::launch_features(X->Un, X->eps, X->g.nc, d, X->cx, X->stream);
     cnn::launch_forward(X->cw, X->cx, 1, X->g.ny, X->g.nx, X->ca1, X->ca2, X->logits, X->stream);
-    cnn::launch_judge(X->flags, X->pred, X->logits, X->g.nc, X->have_pred ? 1 : 0, X->sctr, X->stream);
+    cnn::launch_judge(X->flags, X->pred, X->logits, X->g.nc, judge_prev ? 1 : 0, X->sctr, X->stream);
   }
-  if (X->sw == ESBGK_SWITCH_LEARNED) {
-    if ((r = after_launch(X, "learned switch"))) return r;
-    X->have_pred = true;
-  }
-  if ((r = compact(X))) return r;
+  if ((r = after_launch(X, "learned switch"))) return r;
+  return compact(X);
+}
+
+// Host state after a regime update.
+void regime_done(esbgk_ctx* X) {
+  X->l1_fresh = false;
+  if (X->sw == ESBGK_SWITCH_LEARNED) X->have_pred = true;
   X->conv_pending = true;
+}
+
+int regime_update(esbgk_ctx* X) {
+  const int r = regime_launches(X, !X->l1_fresh, X->have_pred);
+  if (r) return r;
+  regime_done(X);
   return ESBGK_OK;
 }
 
@@ -442,22 +472,103 @@ void finish_step(esbgk_ctx* X, const StepPlan& PL) {
   X->steps += 1;
 }
 
-int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
-  StepPlan PL;
-  int r = plan_step(X, dt, T, PL);
-  if (r) return r;
+// The launches of a planned step (no host synchronisation).
+int advance_launches(esbgk_ctx* X, const StepPlan& PL) {
   const View V = X->view();
   {
     Timed t(X, ESBGK_K_PREP);
     X->L->prep(PL.prep, V, X->grid_stage, X->stream);
   }
-  if ((r = after_launch(X, "prep kernel"))) return r;
+  int r = after_launch(X, "prep kernel");
+  if (r) return r;
   for (int q = 0; q < PL.n; ++q) {
     {
       Timed t(X, PL.fin[q] ? ESBGK_K_FINAL : ESBGK_K_STAGE);
       X->L->stage(PL.st[q], V, X->grid_stage, X->stream);
     }
     if ((r = after_launch(X, PL.fin[q] ? "final kernel" : "stage kernel"))) return r;
+  }
+  return ESBGK_OK;
+}
+
+int advance(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
+  StepPlan PL;
+  memset(&PL, 0, sizeof PL);
+  int r = plan_step(X, dt, T, PL);
+  if (r) return r;
+  if ((r = advance_launches(X, PL))) return r;
+  finish_step(X, PL);
+  return ESBGK_OK;
+}
+
+// A whole step (regime update when the switch applies, then Algorithm 1).
+// On a capturable stream, without per-launch timing, a step whose launch
+// arguments were seen at the previous step is captured into a CUDA graph,
+// and later steps with the same arguments replay it (up to three versions:
+// a tableau whose last stage is the result alternates f buffers).
+int step_all(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
+  const bool crit = X->criterion();
+  const bool l1_needed = crit && !X->l1_fresh, judge_prev = X->have_pred;
+  const bool use_graph = X->graphs_on && X->stream && !X->timing;
+  if (!use_graph) {
+    if (crit) {
+      const int r = regime_update(X);
+      if (r) return r;
+    }
+    return advance(X, dt, T);
+  }
+  // host state as the regime update leaves it, then the plan
+  const bool saved_fresh = X->l1_fresh, saved_conv = X->conv_pending, saved_pred = X->have_pred;
+  if (crit) regime_done(X);
+  StepPlan PL;
+  memset(&PL, 0, sizeof PL);
+  int r = plan_step(X, dt, T, PL);
+  if (r) {
+    X->l1_fresh = saved_fresh;
+    X->conv_pending = saved_conv;
+    X->have_pred = saved_pred;
+    return r;
+  }
+  std::vector<unsigned char> key(3 + sizeof PL);
+  key[0] = crit;
+  key[1] = l1_needed;
+  key[2] = judge_prev;
+  memcpy(key.data() + 3, &PL, sizeof PL);
+  esbgk_ctx::GraphEntry* hit = nullptr;
+  for (auto& e : X->graphs)
+    if (e.exec && e.key == key) hit = &e;
+  auto launches = [&]() -> int {
+    if (crit && (r = regime_launches(X, l1_needed, judge_prev))) return r;
+    return advance_launches(X, PL);
+  };
+  if (!hit && key == X->last_key) {
+    // second sighting: capture
+    esbgk_ctx::GraphEntry* slot = &X->graphs[0];
+    for (auto& e : X->graphs)
+      if (!e.exec || e.used < slot->used) slot = &e;
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    slot->exec = nullptr;
+    cudaGraph_t g = nullptr;
+    if ((r = cuda_check(X, cudaStreamBeginCapture(X->stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+      return r;
+    const int rl = launches();
+    const cudaError_t e = cudaStreamEndCapture(X->stream, &g);
+    if (rl || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rl ? rl : cuda_check(X, e, "end capture");
+    }
+    r = cuda_check(X, cudaGraphInstantiate(&slot->exec, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (r) return r;
+    slot->key = key;
+    hit = slot;
+  }
+  if (hit) {
+    hit->used = X->steps + 1;
+    if ((r = cuda_check(X, cudaGraphLaunch(hit->exec, X->stream), "graph launch"))) return r;
+  } else {
+    X->last_key = key;
+    if ((r = launches())) return r;
   }
   finish_step(X, PL);
   return ESBGK_OK;
@@ -774,11 +885,7 @@ int esbgk_step(esbgk_ctx* X, double dt, const esbgk_tableau* tab) {
   if (!(dt > 0) || !std::isfinite(dt) || !valid_tableau(tab)) return fail(X, ESBGK_E_ARG, "step: bad dt or tableau");
   if (X->sw == ESBGK_SWITCH_LEARNED && !X->have_weights)
     return fail(X, ESBGK_E_STATE, "step: learned switch without network parameters");
-  if (X->criterion()) {
-    const int r = regime_update(X);
-    if (r) return r;
-  }
-  return advance(X, dt, tab);
+  return step_all(X, dt, tab);
 }
 
 int esbgk_get_moments(esbgk_ctx* X, double* rho, double* ux, double* uy, double* T) {
@@ -830,6 +937,15 @@ int esbgk_counters(esbgk_ctx* X, long long* updates, long long* steps, long long
   if (steps) *steps = X->steps;
   if (kinetic_cells) *kinetic_cells = k[0];
   if (buffer_fills) *buffer_fills = c[1];
+  return ESBGK_OK;
+}
+
+int esbgk_graphs(esbgk_ctx* X, int32_t enable) {
+  GUARD(X);
+  const int r = cuda_check(X, cudaStreamSynchronize(X->stream), "graphs sync");
+  if (r) return r;
+  X->graphs_on = enable != 0;
+  X->drop_graphs();
   return ESBGK_OK;
 }
 
