@@ -34,7 +34,7 @@ const Launchers* launchers_for(int prec) {
 // Byte offsets of every array inside the caller's workspace.
 struct Layout {
   size_t F[3], ACC[3], Un, Us[2], Phi, eps, lamA, L1, stage5, red, tot;
-  size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr;
+  size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr, wq, blockc;
   // learned switch only: features, activations, logits, prediction, weights, statistics
   size_t cx, ca1, ca2, logits, pred, cnnw, sctr;
   size_t total;
@@ -73,6 +73,8 @@ Layout make_layout(int nc, int nvv, size_t elem, bool learned) {
   L.counts = take(4 * sizeof(int));
   L.err = take(sizeof(DevErr));
   L.ctr = take(2 * sizeof(long long));
+  L.wq = take((kMaxStages + 1) * sizeof(int));
+  L.blockc = take(4 * (size_t)categorize_blocks(nc) * sizeof(int));
   if (learned) {
     L.cx = take((size_t)nc * cnn::kCinPad * 2);
     L.ca1 = take((size_t)nc * cnn::kHid * 2);
@@ -135,6 +137,8 @@ struct esbgk_ctx {
   int *klist, *blist, *flist, *clist, *counts;
   DevErr* err;
   long long* ctr;
+  int* wq = nullptr;  // work counters of the stage launches of a step
+  int* blockc = nullptr;  // per-block category counts of the compaction
   int cur;
   bool have_state, conv_pending;
   bool l1_fresh;  // L1 holds ||f^n - M_hat||_1 of the kinetic cells (from the last final combination)
@@ -273,8 +277,8 @@ int compact(esbgk_ctx* X) {
   const View V = X->view();
   {
     Timed t(X, ESBGK_K_COMPACT);
-    launch_categorize(V, X->flags, X->flags_prev, X->cat, X->stream);
-    launch_compact(X->cat, X->g.nc, X->klist, X->blist, X->flist, X->clist, X->counts, X->stream);
+    launch_categorize_compact(V, X->flags, X->flags_prev, X->cat, X->blockc, X->klist, X->blist, X->flist, X->clist,
+                              X->counts, X->stream);
   }
   return after_launch(X, "compaction");
 }
@@ -430,6 +434,7 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.fill = (last && shortcut) ? 0 : 1;
     A.kin_u_moments = (A.hoc || (last && shortcut)) ? 1 : 0;
     A.ctr = X->ctr;
+    A.wq = X->wq ? X->wq + (PL.n - 1) : nullptr;
     prev_buf = outbuf;
   }
   if (!shortcut) {
@@ -457,10 +462,13 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.ctr = X->ctr;
     // the deviation ||f^{n+1} - M_hat||_1 the next regime update needs
     A.l1_out = X->criterion() ? X->L1 : nullptr;
+    A.wq = X->wq ? X->wq + (PL.n - 1) : nullptr;
     PL.new_cur = X->cur;
   } else {
     PL.new_cur = prev_buf;
   }
+  P.wq_zero = X->wq;
+  P.wq_n = X->wq ? PL.n : 0;
   return ESBGK_OK;
 }
 
@@ -674,6 +682,8 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->counts = (int*)(w + lay.counts);
   X->err = (DevErr*)(w + lay.err);
   X->ctr = (long long*)(w + lay.ctr);
+  X->wq = (int*)(w + lay.wq);
+  X->blockc = (int*)(w + lay.blockc);
   if (X->sw == ESBGK_SWITCH_LEARNED) {
     X->cx = (__nv_bfloat16*)(w + lay.cx);
     X->ca1 = (__nv_bfloat16*)(w + lay.ca1);

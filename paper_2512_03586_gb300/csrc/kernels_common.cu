@@ -106,12 +106,8 @@ void launch_flags(const View& V, const double* Un, const double* L1in, double* L
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
 // cross stencil of a kinetic cell, Remark rem_coupling), 2 other fluid; bit 2
 // (value 4) marks a kinetic cell that was fluid in the previous step.
-__device__ void categorize_cell(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
-                                uint8_t* cat, int c) {
-  if (flags[c]) {
-    cat[c] = prev[c] ? 0 : 4;
-    return;
-  }
+__device__ int category_of(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev, int c) {
+  if (flags[c]) return prev[c] ? 0 : 4;
   const int i = c % g.nx, j = c / g.nx;
   bool hit = false;
   const int d[4] = {-2, -1, 1, 2};
@@ -120,7 +116,12 @@ __device__ void categorize_cell(const Geo& g, const uint8_t* __restrict__ flags,
     hit |= flags[j * g.nx + nb(i + d[q], g.nx, g.bcx)] != 0;
     hit |= flags[nb(j + d[q], g.ny, g.bcy) * g.nx + i] != 0;
   }
-  cat[c] = hit ? 1 : 2;
+  return hit ? 1 : 2;
+}
+
+__device__ void categorize_cell(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
+                                uint8_t* cat, int c) {
+  cat[c] = (uint8_t)category_of(g, flags, prev, c);
 }
 
 __global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
@@ -226,6 +227,73 @@ void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* fli
                     cudaStream_t s) {
   compact_kernel<<<1, kScanThreads, 0, s>>>(cat, nc, klist, blist, flist, clist, counts);
 }
+
+// Categories and lists in two launches, in ascending cell order: kernel 1
+// writes each cell's category and the per-block counts of the four lists;
+// kernel 2 gives every block its offsets (sum of the counts of the blocks
+// before it), scans its cells and writes them.  Block b covers cells
+// [b * kCatBlock, (b + 1) * kCatBlock).
+constexpr int kCatBlock = 1024;
+
+__global__ void __launch_bounds__(kCatBlock) categorize_count_kernel(Geo g, const uint8_t* __restrict__ flags,
+                                                                     const uint8_t* __restrict__ prev, uint8_t* cat,
+                                                                     int* block_counts) {
+  __shared__ int sc[4];
+  if (threadIdx.x < 4) sc[threadIdx.x] = 0;
+  __syncthreads();
+  const int c = blockIdx.x * kCatBlock + threadIdx.x;
+  const int t = c < g.nc ? category_of(g, flags, prev, c) : -1;
+  if (c < g.nc) cat[c] = (uint8_t)t;
+  const unsigned full = 0xffffffffu;
+  const unsigned m[4] = {__ballot_sync(full, t == 0 || t == 4), __ballot_sync(full, t == 1),
+                         __ballot_sync(full, t == 2), __ballot_sync(full, t == 4)};
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (m[q]) atomicAdd(&sc[q], __popc(m[q]));
+  __syncthreads();
+  if (threadIdx.x < 4) block_counts[blockIdx.x * 4 + threadIdx.x] = sc[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kCatBlock) emit_lists_kernel(int nc, const uint8_t* __restrict__ cat,
+                                                               const int* __restrict__ block_counts, int nblocks,
+                                                               int* klist, int* blist, int* flist, int* clist,
+                                                               int* counts) {
+  __shared__ int base[4], tot[4];
+  __shared__ int sm[64];
+  if (threadIdx.x < 4) {
+    int s = 0, all = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      const int v = block_counts[b * 4 + threadIdx.x];
+      if (b < (int)blockIdx.x) s += v;
+      all += v;
+    }
+    base[threadIdx.x] = s;
+    tot[threadIdx.x] = all;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * kCatBlock + threadIdx.x;
+  const int t = c < nc ? cat[c] : -1;
+  int* lists[4] = {klist, blist, flist, clist};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int in = q == 0 ? (t == 0 || t == 4) : (q == 1 ? t == 1 : (q == 2 ? t == 2 : t == 4));
+    int total;
+    const int off = block_exclusive_scan(in, sm, total);
+    if (in) lists[q][base[q] + off] = c;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) counts[threadIdx.x] = tot[threadIdx.x];
+}
+
+void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
+                               int* block_counts, int* klist, int* blist, int* flist, int* clist, int* counts,
+                               cudaStream_t s) {
+  const int nb = (V.g.nc + kCatBlock - 1) / kCatBlock;
+  categorize_count_kernel<<<nb, kCatBlock, 0, s>>>(V.g, flags, flags_prev, cat, block_counts);
+  emit_lists_kernel<<<nb, kCatBlock, 0, s>>>(V.g.nc, cat, block_counts, nb, klist, blist, flist, clist, counts);
+}
+
+int categorize_blocks(int nc) { return (nc + kCatBlock - 1) / kCatBlock; }
 
 // (rho, u_x, u_y, T) from U.
 __global__ void prim_kernel(const double* __restrict__ Un, double* out, int nc) {

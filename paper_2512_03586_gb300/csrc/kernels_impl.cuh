@@ -84,6 +84,18 @@ struct VecIO<float, 4> {
   }
 };
 template <>
+struct VecIO<float, 2> {
+  static ESBGK_DEV void ld(const float* p, float (&v)[2]) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x, v[1] = t.y;
+  }
+  static ESBGK_DEV void ldc(const float* p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  }
+  static ESBGK_DEV void st(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+};
+template <>
 struct VecIO<double, 2> {
   static ESBGK_DEV void ld(const double* p, double (&v)[2]) {
     const double2 t = __ldg(reinterpret_cast<const double2*>(p));
@@ -129,6 +141,14 @@ struct SmemVec<float, 4> {
   static ESBGK_DEV void ld(const float* p, float (&v)[4]) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  }
+};
+template <>
+struct SmemVec<float, 2> {
+  static ESBGK_DEV void st(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+  static ESBGK_DEV void ld(const float* p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x, v[1] = t.y;
   }
 };
 template <>
@@ -230,7 +250,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
-#pragma unroll 2
+#pragma unroll 1
   for (; it.k < g.nvv; it.next())
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -720,7 +740,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
-#pragma unroll 2
+#pragma unroll 1
   for (; it.k < g.nvv; it.next()) {
     const unsigned k = it.k;
     const R vx0 = it.vx(), vy = it.vy();
@@ -807,7 +827,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
   const R inv1h = R(1) / (R(1) + h);
   NodeIter<R> jt(lane * W, g.nv, v0, dv, 32 * W);
-#pragma unroll 2
+#pragma unroll 1
   for (; jt.k < g.nvv; jt.next()) {
     const unsigned k = jt.k;
     R fs[W], pa[nacc > 0 ? nacc : 1][W], fn[W];
@@ -836,24 +856,36 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 
 // Writes f := M_hat[U] (the discrete Maxwellian, Eq. Coupling_FluKin) into
 // cell c of f, one warp.  Returns false for a non-realizable U.
-template <typename S>
+// W > 1: groups of W consecutive nodes of a row (N_v divisible by W, f 16-byte
+// aligned), one vector store per group.
+template <typename S, int W = 1>
 ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&U)[4]) {
   using R = typename Real<S>::T;
   double rho, ux, uy, T;
   prim_of(U, rho, ux, uy, T);
   CellPar<R> P;
-  if (!maxwell_params<R>(rho, ux, uy, T, P) || !project<R>(g, lane, P)) return false;
+  if (!maxwell_params<R>(rho, ux, uy, T, P) || !project<R, W>(g, lane, P)) return false;
   const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
   const size_t o0 = (size_t)c * g.nvv;
-  NodeIter<R> it(lane, g.nv, v0, dv);
-#pragma unroll 2
-  for (; it.k < g.nvv; it.next()) st(f + o0 + it.k, ghat(P, it.vx() - P.ux, it.vy() - P.uy));
+  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+#pragma unroll 1
+  for (; it.k < g.nvv; it.next()) {
+    if constexpr (W > 1) {
+      R v[W];
+      const R cy = it.vy() - P.uy, cx0 = it.vx() - P.ux;
+#pragma unroll
+      for (int j = 0; j < W; ++j) v[j] = ghat(P, cx0 + R(j) * dv, cy);
+      VecIO<S, W>::st(f + o0 + it.k, v);
+    } else {
+      st(f + o0 + it.k, ghat(P, it.vx() - P.ux, it.vy() - P.uy));
+    }
+  }
   return true;
 }
 
 // Buffer cell of a stage: Euler update (lane 0), then f := M_hat[U] over the
 // velocities when filling is on.
-template <typename S>
+template <typename S, int W = 1>
 ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
   using R = typename Real<S>::T;
   double Uc[4] = {0, 0, 0, 0};
@@ -865,7 +897,7 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) Uc[q] = A.Un[(size_t)q * V.g.nc + c];
   }
-  if (!fill_maxwell<S>((S*)A.f_out, V.g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
+  if (!fill_maxwell<S, W>((S*)A.f_out, V.g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
 }
 
 #ifndef ESBGK_STAGE_MIN_BLOCKS
@@ -882,7 +914,12 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
   const int nFc = (nF + 31) / 32;
   const int total = nK + nB + nFc;
   long long mine = 0, fills = 0;
-  for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
+  // first wave round-robin; later units claimed from the launch's counter, so
+  // a warp that drew a long unit (kinetic cell) does not also own a fixed
+  // share of the short ones (units are ordered kinetic, buffer, fluid)
+  const int first = gridDim.x * nwarps;
+  int u = blockIdx.x * nwarps + warp;
+  while (u < total) {
     if (u < nK) {
       if constexpr (W > 1)
         kinetic_cell_vec<S, M, W>(A, V, V.klist[u], lane, sfs);
@@ -890,7 +927,7 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
         kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
       ++mine;
     } else if (u < nK + nB) {
-      buffer_cell<S>(A, V, V.blist[u - nK], lane);
+      buffer_cell<S, W>(A, V, V.blist[u - nK], lane);
       fills += A.fill ? 1 : 0;
     } else {
       const int q = (u - nK - nB) * 32 + lane;
@@ -898,6 +935,13 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
         double Uc[4];
         euler_cell<R>(A, V, V.flist[q], Uc);
       }
+    }
+    if (A.wq) {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(A.wq, 1);
+      u = first + __shfl_sync(0xffffffffu, v, 0);
+    } else {
+      u += first;
     }
   }
   if (lane == 0 && A.ctr) {
@@ -917,13 +961,17 @@ __global__ void __launch_bounds__(kCellThreads) prep_kernel(PrepArgs P, View V) 
   const int nCopy = P.copy_to ? (g.nc + 31) / 32 : 0;
   const int total = n1 + n2 + nCopy;
   S* f = (S*)P.f;
+  if (blockIdx.x == 0 && (int)threadIdx.x < P.wq_n) P.wq_zero[threadIdx.x] = 0;
+  constexpr int kW = VecW<S>::value;
+  const bool vec = g.nv % kW == 0 && ((uintptr_t)f & 15u) == 0;
   for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
     if (u < n1 + n2) {
       const int c = u < n1 ? P.list1[u] : P.list2[u - n1];
       double Uc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + c];
-      if (!fill_maxwell<S>(f, g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
+      const bool ok = vec ? fill_maxwell<S, kW>(f, g, c, lane, Uc) : fill_maxwell<S>(f, g, c, lane, Uc);
+      if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
     } else {
       const int c = (u - n1 - n2) * 32 + lane;
       if (c < g.nc) {
@@ -945,7 +993,7 @@ ESBGK_DEV void load_moments(const S* f, const Geo& g, int c, int lane, typename 
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = R(0);
   NodeIter<R> it(lane, g.nv, v0, dv);
-#pragma unroll 2
+#pragma unroll 1
   for (; it.k < g.nvv; it.next()) {
     const R x = ld(f + o0 + it.k);
     if (sf) sf[it.k] = x;
@@ -988,7 +1036,7 @@ __global__ void __launch_bounds__(kCellThreads) l1_kernel(const void* fptr, cons
     }
     R s = R(0);
     NodeIter<R> it(lane, g.nv, v0, dv);
-#pragma unroll 2
+#pragma unroll 1
     for (; it.k < g.nvv; it.next()) s += rabs(sf[it.k] - ghat(P, it.vx() - P.ux, it.vy() - P.uy));
     s = warp_sum(s);
     if (lane == 0) L1[c] = g.w * (double)s;

@@ -58,6 +58,8 @@ struct StageArgs {
   int kin_u_moments;
   long long* ctr;
   double* l1_out;  // when set (final combination only): ||f - M_hat[f]||_L1 of the result per kinetic cell
+  int* wq;         // work counter of the launch (zeroed by the step's prep): units past the first wave are
+                   // claimed from it; null: static round-robin
 };
 
 // Start-of-step preparation: f := M_hat[U] in the cells of list1 and list2;
@@ -65,6 +67,8 @@ struct StageArgs {
 struct PrepArgs {
   void* f;
   const double* U;
+  int* wq_zero;  // work counters of the step's stage launches, zeroed here (wq_n of them)
+  int wq_n;
   const int* list1;
   const int* count1;
   const int* list2;
@@ -186,6 +190,12 @@ void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags
                        cudaStream_t s);
 void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* flist, int* clist, int* counts,
                     cudaStream_t s);
+// categories (into cat) and lists in ascending cell order, fully parallel;
+// block_counts holds 4 * categorize_blocks(nc) ints
+void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
+                               int* block_counts, int* klist, int* blist, int* flist, int* clist, int* counts,
+                               cudaStream_t s);
+int categorize_blocks(int nc);
 void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
 void launch_totals(const double* Un, int nc, double* partial /*[grid][4]*/, double* out, double dxdy, int grid,
                    cudaStream_t s);
