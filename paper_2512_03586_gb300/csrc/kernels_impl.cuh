@@ -367,7 +367,7 @@ ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c,
   const int i = c % g.nx, j = c / g.nx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) phi[q] = R(0);
-#pragma unroll
+#pragma unroll 1
   for (int d = 0; d < 2; ++d) {
     int cell[5];
 #pragma unroll
@@ -883,13 +883,10 @@ ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&
   return true;
 }
 
-// Buffer cell of a stage: Euler update (lane 0), then f := M_hat[U] over the
-// velocities when filling is on.
+// Second half of a buffer cell: f := M_hat[U] over the velocities (when
+// filling is on) from the Euler result Uc held by lane 0.
 template <typename S, int W = 1>
-ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
-  using R = typename Real<S>::T;
-  double Uc[4] = {0, 0, 0, 0};
-  if (lane == 0) euler_cell<R>(A, V, c, Uc);
+ESBGK_DEV void buffer_fill(const StageArgs& A, const View& V, int c, int lane, double (&Uc)[4]) {
   if (!A.fill) return;
 #pragma unroll
   for (int q = 0; q < 4; ++q) Uc[q] = __shfl_sync(0xffffffffu, Uc[q], 0);
@@ -898,6 +895,17 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
     for (int q = 0; q < 4; ++q) Uc[q] = A.Un[(size_t)q * V.g.nc + c];
   }
   if (!fill_maxwell<S, W>((S*)A.f_out, V.g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
+}
+
+
+// Buffer cell of a stage: Euler update (lane 0), then f := M_hat[U] over the
+// velocities when filling is on.
+template <typename S, int W = 1>
+ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
+  using R = typename Real<S>::T;
+  double Uc[4] = {0, 0, 0, 0};
+  if (lane == 0) euler_cell<R>(A, V, c, Uc);
+  buffer_fill<S, W>(A, V, c, lane, Uc);
 }
 
 #ifndef ESBGK_STAGE_MIN_BLOCKS
@@ -926,14 +934,17 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       else
         kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
       ++mine;
-    } else if (u < nK + nB) {
-      buffer_cell<S, W>(A, V, V.blist[u - nK], lane);
-      fills += A.fill ? 1 : 0;
     } else {
+      // a buffer cell (Euler update on lane 0, then the fill) or a chunk of
+      // 32 fluid cells (one per lane): one call site of the Euler update
+      const bool buf = u < nK + nB;
       const int q = (u - nK - nB) * 32 + lane;
-      if (q < nF) {
-        double Uc[4];
-        euler_cell<R>(A, V, V.flist[q], Uc);
+      const int ec = buf ? (lane == 0 ? V.blist[u - nK] : -1) : (q < nF ? V.flist[q] : -1);
+      double Uc[4] = {0, 0, 0, 0};
+      if (ec >= 0) euler_cell<R>(A, V, ec, Uc);
+      if (buf) {
+        buffer_fill<S, W>(A, V, V.blist[u - nK], lane, Uc);
+        fills += A.fill ? 1 : 0;
       }
     }
     if (A.wq) {
