@@ -632,13 +632,91 @@ def learned_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def switchnet_arm(args):
+    """Kernels of the learned switch alone: inference of one 512 x 512 image
+    (the deployment grid) and Adam training steps on batches of 32 images of
+    128 x 128 cells, random features and labels.  Roofline of the dominant
+    kernel (the 32 -> 32 channel 3 x 3 convolution) against the measured bf16
+    tensor peak."""
+    import torch
+    import paper_2512_03586_gb300 as G
+    from paper_2512_03586_gb300 import switch_train as T
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev).manual_seed(0)
+
+    def feats(n, H, Wd):
+        x = torch.zeros((n, H, Wd, G.CNN_CHANNELS), dtype=torch.bfloat16, device=dev)
+        x[..., :5] = torch.randn((n, H, Wd, 5), generator=gen, device=dev).to(torch.bfloat16)
+        return x
+
+    theta = T.init_params(0)
+    n_tr, Ht = 32, 128
+    net = G.SwitchNet(n_tr, Ht, Ht, device=dev)
+    net.set_params(theta)
+    xt = feats(n_tr, Ht, Ht)
+    yt = (torch.rand((n_tr, Ht, Ht), generator=gen, device=dev) < 0.25).to(torch.uint8)
+    inf = G.SwitchNet(1, 512, 512, device=dev)
+    inf.set_params(theta)
+    xi = feats(1, 512, 512)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        net.train_step(xt, yt, 3.0, 1e-3)
+        inf.forward(xi)
+    torch.cuda.synchronize(dev)
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    with ClockSampler(local) as clk:
+        ms_train = timed(lambda: net.train_step(xt, yt, 3.0, 1e-3), args.steps)
+        ms_inf = timed(lambda: inf.forward(xi), args.steps)
+        # the 32 -> 32 convolution alone, through the forward pass of one image
+        ms_fwd = ms_inf
+    cells_tr, cells_inf = n_tr * Ht * Ht, 512 * 512
+    # algorithmic flops per cell: conv1 2*32*45, conv2 2*32*288, head 2*32
+    f_fwd = 2 * 32 * 45 + 2 * 32 * 288 + 2 * 32
+    f_train = f_fwd + 2 * 32 * 288 * 2 + 2 * 32 * 45  # + input and weight gradients of conv2, weight gradient of conv1
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, src = float(m["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, cuBLAS burst)"
+    except Exception:
+        peak, src = 1900.0, "fallback 1.9 PFLOP/s"
+    tf_inf = cells_inf * f_fwd / (ms_fwd * 1e-3) / 1e12
+    out = {"metric": "learned-switch network: cells per second (one Adam training step)", "value": cells_tr / (ms_train * 1e-3),
+           "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_train,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands / f32 accumulation",
+           "data": "synthetic", "config": {"workload": "switch network: training batches of 32 x 128 x 128 cells; "
+                                                       "inference of one 512 x 512 image", "features": 5, "hidden": 32},
+           "inference": {"ms": ms_inf, "cells_per_s": cells_inf / (ms_inf * 1e-3)},
+           "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s", "frac": tf_inf / peak,
+                        "traffic": None, "kernel": "forward pass (two mma.sync implicit-GEMM convolutions + head), "
+                                                   "512 x 512 cells", "peak_source": src,
+                        "flops_model": "%d flops per cell (2 x 32 x 45 + 2 x 32 x 288 + 2 x 32)" % f_fwd},
+           "train_tflops": cells_tr * f_train / (ms_train * 1e-3) / 1e12,
+           "clocks": clk.summary(),
+           # per training step: two convolutions, head, head reduction, weight gradient and its reduction
+           # (twice), input-gradient convolution, Adam = 10; per inference: two convolutions and the head
+           "gpu_launches": args.steps * (10 + 3)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch", "learned"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch", "learned", "switchnet"])
     ap.add_argument("--train-seeds", type=int, default=48)
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--sim-steps", type=int, default=100, help="steps of the learned-switch comparison runs")
@@ -655,6 +733,8 @@ def main():
         batch_arm(args)
     elif args.workload == "learned":
         learned_arm(args)
+    elif args.workload == "switchnet":
+        switchnet_arm(args)
     else:
         ours_arm(args)
 

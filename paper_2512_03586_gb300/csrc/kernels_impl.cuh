@@ -197,7 +197,7 @@ ESBGK_DEV bool es_params(const R (&m)[6], R u0x, R u0y, R w, R beta, R h, bool r
   const R Tyy = (R(1) - beta) * T + beta * tyy;
   const double det = fma((double)Txx, (double)Tyy, -(double)Txy * (double)Txy);
   if (!(det > 0.0)) return false;
-  const R idet = R(1.0 / det);
+  const R idet = R(1) / R(det);  // det in float64 (cancellation); its inverse in the arithmetic type
   P.ux = u0x + dux;
   P.uy = u0y + duy;
   P.qxx = R(-0.5 * kLog2e) * Tyy * idet;
@@ -219,13 +219,14 @@ ESBGK_DEV bool es_params(const R (&m)[6], R u0x, R u0y, R w, R beta, R h, bool r
 template <typename R>
 ESBGK_DEV bool maxwell_params(double rho, double ux, double uy, double T, CellPar<R>& P) {
   if (!(rho > 0.0) || !(T > 0.0)) return false;
+  const R iT = R(1) / R(T);
   P.ux = R(ux);
   P.uy = R(uy);
-  P.qxx = R(-0.5 * kLog2e / T);
+  P.qxx = R(-0.5 * kLog2e) * iT;
   P.qxy = R(0);
   P.qyy = P.qxx;
-  P.pref = R(rho * 0.5 / (kPi * T));
-  P.isT = R(1.0 / sqrt(T));
+  P.pref = R(rho) * R(0.5 / kPi) * iT;
+  P.isT = R(1) / rsqrt_(R(T));
   P.t[0] = R(rho);
   P.t[1] = P.t[2] = R(0);
   P.t[3] = R(rho);
@@ -425,22 +426,25 @@ ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)
 // Primitive variables of U (Sec. 2): u = m/rho, T = (E - rho |u|^2/2)/rho.
 ESBGK_DEV void prim_of(const double (&U)[4], double& rho, double& ux, double& uy, double& T) {
   rho = U[0];
-  ux = U[1] / rho;
-  uy = U[2] / rho;
-  T = (U[3] - 0.5 * rho * (ux * ux + uy * uy)) / rho;
+  const double ir = 1.0 / rho;
+  ux = U[1] * ir;
+  uy = U[2] * ir;
+  T = (U[3] - 0.5 * rho * (ux * ux + uy * uy)) * ir;
 }
 
 // Reference velocity for the moment sums of cell c: the mean velocity held
 // in U (0 when U is not usable).
+// Only a centring point for the sums: computed in the arithmetic type.
 template <typename R>
 ESBGK_DEV void ref_velocity(const double* U, size_t nc, int c, R& u0x, R& u0y) {
   u0x = R(0);
   u0y = R(0);
   if (!U) return;
-  const double rho = U[c];
-  if (rho > 0.0) {
-    u0x = R(U[nc + c] / rho);
-    u0y = R(U[2 * nc + c] / rho);
+  const R rho = R(U[c]);
+  if (rho > R(0)) {
+    const R ir = R(1) / rho;
+    u0x = R(U[nc + c]) * ir;
+    u0y = R(U[2 * nc + c]) * ir;
   }
 }
 
@@ -633,9 +637,9 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
   }
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
-  double Uc[4];
-  cons_from_sums(m, u0x, u0y, g.w, Uc);
-  if (lane == 0) {
+  if (lane == 0) {  // U of the cell (float64), written by one lane
+    double Uc[4];
+    cons_from_sums(m, u0x, u0y, g.w, Uc);
     const size_t nc = g.nc;
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
@@ -652,8 +656,8 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
     return;
   }
 
-  const double nu_d = V.m.tau / V.eps[c];
-  const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
+  // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
+  const R nu = R(V.m.tau) / R(V.eps[c]), h = R(A.h_coef) * nu;
   CellPar<R> P;
   bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, relax, P);
   if (ok) ok = project<R>(g, lane, P);
@@ -798,9 +802,9 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   }
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
-  double Uc[4];
-  cons_from_sums(m, u0x, u0y, g.w, Uc);
-  if (lane == 0) {
+  if (lane == 0) {  // U of the cell (float64), written by one lane
+    double Uc[4];
+    cons_from_sums(m, u0x, u0y, g.w, Uc);
     const size_t nc = g.nc;
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.U_out[q * nc + c] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + c];
@@ -817,8 +821,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     return;
   }
 
-  const double nu_d = V.m.tau / V.eps[c];
-  const R nu = (R)nu_d, h = (R)(A.h_coef * nu_d);
+  // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
+  const R nu = R(V.m.tau) / R(V.eps[c]), h = R(A.h_coef) * nu;
   CellPar<R> P;
   bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, true, P);
   if (ok) ok = project<R, W>(g, lane, P);
