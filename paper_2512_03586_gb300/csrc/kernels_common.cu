@@ -50,35 +50,36 @@ __device__ __forceinline__ double sqrt_nr(double x) {
 // Gradients: central differences of cell-centre u and T, ghost cells by BC.
 // New flag (Eqs. crit:CompEuler, eqKintoFluid1):
 //   lambda_A > eta   or   (kinetic and ||f - M||_1 > delta).
-__device__ void flags_cell(const View& V, const double* __restrict__ Un, const double* __restrict__ L1in,
-                           double* L1out, double* lamA, uint8_t* flags_out, int c, bool plain) {
+__device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t nc, int cc, double& ux, double& uy,
+                                          double& T) {
+  const double rho = Un[cc], mx = Un[nc + cc], my = Un[2 * nc + cc], E = Un[3 * nc + cc];
+  const double ir = rcp_nr(rho);
+  ux = mx * ir;
+  uy = my * ir;
+  T = (E - 0.5 * rho * (ux * ux + uy * uy)) * ir;
+}
+
+// The criterion of cell c from the primitive variables of the cell (0) and
+// of its east, west, north and south neighbours.
+struct Prims {
+  double ux, uy, T;
+};
+__device__ __forceinline__ void flags_from_prims(const View& V, const double* __restrict__ L1in, double* L1out,
+                                                 double* lamA, uint8_t* flags_out, int c, bool plain,
+                                                 const Prims& P0, const Prims& PE, const Prims& PW, const Prims& PN,
+                                                 const Prims& PS) {
   const Geo& g = V.g;
-  const int i = c % g.nx, j = c / g.nx;
-  const size_t nc = g.nc;
-  auto prim = [&](int cc, double& ux, double& uy, double& T) {
-    const double rho = Un[cc], mx = Un[nc + cc], my = Un[2 * nc + cc], E = Un[3 * nc + cc];
-    const double ir = rcp_nr(rho);
-    ux = mx * ir;
-    uy = my * ir;
-    T = (E - 0.5 * rho * (ux * ux + uy * uy)) * ir;
-  };
-  double uxE, uyE, TE, uxW, uyW, TW, uxN, uyN, TN, uxS, uyS, TS, ux0, uy0, T0;
-  prim(j * g.nx + nb(i + 1, g.nx, g.bcx), uxE, uyE, TE);
-  prim(j * g.nx + nb(i - 1, g.nx, g.bcx), uxW, uyW, TW);
-  prim(nb(j + 1, g.ny, g.bcy) * g.nx + i, uxN, uyN, TN);
-  prim(nb(j - 1, g.ny, g.bcy) * g.nx + i, uxS, uyS, TS);
-  prim(c, ux0, uy0, T0);
   const double i2dx = 0.5 / g.dx, i2dy = 0.5 / g.dy;
-  const double dudx = (uxE - uxW) * i2dx, dudy = (uxN - uxS) * i2dy;
-  const double dvdx = (uyE - uyW) * i2dx, dvdy = (uyN - uyS) * i2dy;
-  const double dTdx = (TE - TW) * i2dx, dTdy = (TN - TS) * i2dy;
+  const double dudx = (PE.ux - PW.ux) * i2dx, dudy = (PN.ux - PS.ux) * i2dy;
+  const double dvdx = (PE.uy - PW.uy) * i2dx, dvdy = (PN.uy - PS.uy) * i2dy;
+  const double dTdx = (PE.T - PW.T) * i2dx, dTdy = (PN.T - PS.T) * i2dy;
   const double div = dudx + dvdy;
   const double Dxx = 2.0 * dudx - (2.0 / 3.0) * div;
   const double Dyy = 2.0 * dvdy - (2.0 / 3.0) * div;
   const double Dxy = dudy + dvdx;
   const double eps = V.eps[c];
   const double c1 = eps / (V.m.tau * (1.0 - V.m.beta));
-  const double kk = 2.5 * eps * rcp_nr(V.m.tau * sqrt_nr(T0));
+  const double kk = 2.5 * eps * rcp_nr(V.m.tau * sqrt_nr(P0.T));
   const double c2 = (2.0 / 3.0) * kk * kk;
   const double Xxx = c1 * Dxx + c2 * dTdx * dTdx;
   const double Xxy = c1 * Dxy + c2 * dTdx * dTdy;
@@ -92,15 +93,46 @@ __device__ void flags_cell(const View& V, const double* __restrict__ Un, const d
   if (plain) flags_out[c] = (lam > V.m.eta_factor * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
 }
 
-__global__ void flags_kernel(View V, const double* __restrict__ Un, const double* __restrict__ L1in,
-                             double* L1out, double* lamA, uint8_t* flags_out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < V.g.nc) flags_cell(V, Un, L1in, L1out, lamA, flags_out, c, true);
+__device__ void flags_cell(const View& V, const double* __restrict__ Un, const double* __restrict__ L1in,
+                           double* L1out, double* lamA, uint8_t* flags_out, int c, bool plain) {
+  const Geo& g = V.g;
+  const int i = c % g.nx, j = c / g.nx;
+  Prims P0, PE, PW, PN, PS;
+  prim_cell(Un, g.nc, j * g.nx + nb(i + 1, g.nx, g.bcx), PE.ux, PE.uy, PE.T);
+  prim_cell(Un, g.nc, j * g.nx + nb(i - 1, g.nx, g.bcx), PW.ux, PW.uy, PW.T);
+  prim_cell(Un, g.nc, nb(j + 1, g.ny, g.bcy) * g.nx + i, PN.ux, PN.uy, PN.T);
+  prim_cell(Un, g.nc, nb(j - 1, g.ny, g.bcy) * g.nx + i, PS.ux, PS.uy, PS.T);
+  prim_cell(Un, g.nc, c, P0.ux, P0.uy, P0.T);
+  flags_from_prims(V, L1in, L1out, lamA, flags_out, c, plain, P0, PE, PW, PN, PS);
+}
+
+// Tiled form: a CTA owns FX x FY cells and computes the primitive variables
+// of the tile and its one-cell halo once, in shared memory.
+constexpr int kFX = 32, kFY = 8;
+__global__ void __launch_bounds__(kFX* kFY) flags_tile_kernel(View V, const double* __restrict__ Un,
+                                                              const double* __restrict__ L1in, double* L1out,
+                                                              double* lamA, uint8_t* flags_out) {
+  constexpr int HX = kFX + 2, HY = kFY + 2;
+  __shared__ Prims sp[HX * HY];
+  const Geo& g = V.g;
+  const int i0 = blockIdx.x * kFX - 1, j0 = blockIdx.y * kFY - 1;
+  const int t = threadIdx.y * kFX + threadIdx.x;
+  for (int h = t; h < HX * HY; h += kFX * kFY) {
+    const int ci = nb(i0 + h % HX, g.nx, g.bcx), cj = nb(j0 + h / HX, g.ny, g.bcy);
+    prim_cell(Un, g.nc, cj * g.nx + ci, sp[h].ux, sp[h].uy, sp[h].T);
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kFX + threadIdx.x, j = blockIdx.y * kFY + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const int h0 = (threadIdx.y + 1) * HX + threadIdx.x + 1;
+  flags_from_prims(V, L1in, L1out, lamA, flags_out, j * g.nx + i, true, sp[h0], sp[h0 + 1], sp[h0 - 1], sp[h0 + HX],
+                   sp[h0 - HX]);
 }
 
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
                   uint8_t* flags_out, cudaStream_t s) {
-  flags_kernel<<<(V.g.nc + 127) / 128, 128, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+  const dim3 grid((V.g.nx + kFX - 1) / kFX, (V.g.ny + kFY - 1) / kFY);
+  flags_tile_kernel<<<grid, dim3(kFX, kFY), 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
 }
 
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
