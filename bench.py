@@ -514,10 +514,11 @@ def batch_arm(args):
 def learned_arm(args):
     """Learned switch (deployment config): train the network on plain-criterion
     histories of the four-quadrant Riemann recipe (128 x 128 cells, 32 x 32
-    velocities, 48 seeds), deploy it on 512 x 512 cells (Riemann data plus a
-    density blob) in FP32, and compare with the plain criterion in FP32 and
-    in FP64 on wall-clock per simulated time and on the macroscopic error
-    against an all-kinetic FP32 run of the same problem."""
+    velocities, 48 seeds) and of the deployment recipe on its 512 x 512 grid
+    (3 other seeds, cut into 128 x 128 tiles), deploy it on 512 x 512 cells
+    (Riemann data plus a density blob) in FP32, and compare with the plain
+    criterion in FP32 and in FP64 on wall-clock per simulated time and on the
+    macroscopic error against an all-kinetic FP32 run of the same problem."""
     import torch
     import paper_2512_03586_gb300 as G
     from paper_2512_03586_gb300 import switch_train as T
@@ -530,6 +531,14 @@ def learned_arm(args):
     train_cases = [W.riemann_quadrants(nx=128, ny=128, nv=32, seed=1000 + s, steps=args.train_steps)
                    for s in range(args.train_seeds)]
     X, Y = T.collect(train_cases, steps=args.train_steps, prec="fp32", device=dev)
+    # plus histories of the deployment recipe on its own grid (other seeds), cut into 128 x 128 tiles
+    fine = [W.learned_switch_case(seed=2000 + s, steps=args.train_steps) for s in range(3)]
+    for c in fine:
+        c["params"] = dict(c["params"], switch="plain")
+    Xf, Yf = T.collect(fine, steps=args.train_steps, prec="fp32", device=dev)
+    Xf, Yf = T.crop(Xf, Yf, 128)
+    X, Y = torch.cat([X, Xf]), torch.cat([Y, Yf])
+    del Xf, Yf
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
     theta, hist = T.train(X, Y, T.init_params(0), epochs=30, batch=32, lr=3e-3, device=dev)
@@ -620,8 +629,9 @@ def learned_arm(args):
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "learned switch: 512x512 cells, 32x32 velocities on [-8,8]^2, four-quadrant Riemann "
                                   "data plus a density blob at (0.3, 0.7), learned switch, ARS(2,3,3), fp32 storage",
-                      "training": "%d Riemann seeds x %d steps at 128x128 / 32x32 (plain criterion labels), "
-                                  "30 epochs Adam; collect %.1f s, train %.1f s, final loss %.4f" % (
+                      "training": "%d Riemann seeds x %d steps at 128x128 / 32x32 plus 3 seeds of this recipe at "
+                                  "512x512 cut into 128x128 tiles (plain criterion labels, next step), 30 epochs "
+                                  "Adam; collect %.1f s, train %.1f s, final loss %.4f" % (
                                       args.train_seeds, args.train_steps, t_collect, t_train, hist[-1]),
                       "comparison_steps": nsim,
                       "l2": "flushed (256 MB write) before every timed step"},

@@ -52,6 +52,17 @@ def collect(cases, steps=None, prec="fp32", every=1, device=None):
     return torch.stack(xs), torch.stack(ys)
 
 
+def crop(X, Y, size):
+    """Split (n, H, W, ...) histories into size x size tiles (H and W
+    multiples of size), so that histories of several grids train one
+    network batch shape."""
+    n, H, W = Y.shape
+    assert H % size == 0 and W % size == 0
+    Xt = X.reshape(n, H // size, size, W // size, size, X.shape[-1]).permute(0, 1, 3, 2, 4, 5)
+    Yt = Y.reshape(n, H // size, size, W // size, size).permute(0, 1, 3, 2, 4)
+    return (Xt.reshape(-1, size, size, X.shape[-1]).contiguous(), Yt.reshape(-1, size, size).contiguous())
+
+
 def positive_weight(Y):
     """Weight of the kinetic class: fluid cells / kinetic cells (>= 1)."""
     k = float(Y.float().mean().item())
@@ -102,4 +113,4 @@ def evaluate(theta, X, Y, device=None):
     return out
 
 
-__all__ = ["init_params", "collect", "positive_weight", "train", "evaluate", "CNN_CHANNELS"]
+__all__ = ["init_params", "collect", "crop", "positive_weight", "train", "evaluate", "CNN_CHANNELS"]
