@@ -103,6 +103,22 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   return launchers_for(p->prec) != nullptr;
 }
 
+// Derived and float copies of a geometry (for the FP32 arithmetic).
+void finish_geo(Geo& G) {
+  G.v0 = -G.vmax + 0.5 * G.dv;
+  G.fv0 = (float)G.v0;
+  G.fdv = (float)G.dv;
+  G.fw = (float)G.w;
+  G.fidx = (float)(1.0 / G.dx);
+  G.fidy = (float)(1.0 / G.dy);
+}
+
+void finish_model(Model& m) {
+  m.fbeta = (float)m.beta;
+  m.ftau = (float)m.tau;
+  m.feps_w = (float)m.eps_w;
+}
+
 Geo make_geo(const esbgk_grid* g, const esbgk_vmesh* v) {
   Geo G{};
   G.nx = g->nx;
@@ -117,6 +133,7 @@ Geo make_geo(const esbgk_grid* g, const esbgk_vmesh* v) {
   G.vmax = v->vmax;
   G.dv = 2.0 * v->vmax / v->nv;
   G.w = G.dv * G.dv;
+  finish_geo(G);
   return G;
 }
 
@@ -469,6 +486,15 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
   }
   P.wq_zero = X->wq;
   P.wq_n = X->wq ? PL.n : 0;
+  for (int q = 0; q < PL.n; ++q) {  // float copies of the coefficients for the FP32 arithmetic
+    StageArgs& A = PL.st[q];
+    A.f_star_cL = (float)A.star_cL;
+    A.f_h_coef = (float)A.h_coef;
+    for (int t = 0; t < 3; ++t) {
+      A.f_acc_cL[t] = (float)A.acc_cL[t];
+      A.f_acc_cQ[t] = (float)A.acc_cQ[t];
+    }
+  }
   return ESBGK_OK;
 }
 
@@ -651,6 +677,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->m.eps_w = params->cweno_eps;
   X->m.eta_factor = params->eta_factor;
   X->m.delta = params->delta;
+  finish_model(X->m);
   X->prec = params->prec;
   X->sw = params->sw;
   X->coupling = params->coupling;
@@ -1022,6 +1049,7 @@ int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv,
   g.dv = 2.0 * vmax / nv;
   g.w = g.dv * g.dv;
   g.dx = g.dy = 1.0;
+  finish_geo(g);
   if (L->setup(g) != cudaSuccess) return ESBGK_E_CUDA;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1617,6 +1645,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.m.eps_w = params->cweno_eps;
   X.m.eta_factor = params->eta_factor;
   X.m.delta = params->delta;
+  finish_model(X.m);
   X.prec = params->prec;
   X.sw = ESBGK_SWITCH_FROZEN;
   X.coupling = ESBGK_COUPLE_STAGE;

@@ -27,12 +27,28 @@ struct Geo {
   int bcx, bcy;        // 0 periodic, 1 outflow
   double dx, dy;       // cell sizes
   double vmax, dv, w;  // velocity bound, step, quadrature weight dv^2
+  double v0;           // first node, -vmax + dv/2
+  // float copies for the FP32 arithmetic (rounded once on the host)
+  float fv0, fdv, fw, fidx, fidy;
 };
 
-// Model constants (Sec. 2, 3.1).
+// Model constants (Sec. 2, 3.1), with float copies for the FP32 arithmetic.
 struct Model {
   double beta, tau, eps_w, eta_factor, delta;
+  float fbeta, ftau, feps_w;
 };
+
+// The double or the float copy of a constant, for arithmetic type R.
+template <typename R>
+ESBGK_DEV R pick(double d, float f);
+template <>
+ESBGK_DEV double pick<double>(double d, float) {
+  return d;
+}
+template <>
+ESBGK_DEV float pick<float>(double, float f) {
+  return f;
+}
 
 // Device error word: first error wins.
 struct DevErr {

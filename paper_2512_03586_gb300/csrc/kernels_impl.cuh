@@ -246,7 +246,7 @@ ESBGK_DEV R gauss_at(const CellPar<R>& P, R cx, R cy) {
 // After this G_hat = G (1 + a . psi) has w sum psi G_hat = t.
 template <typename R, int W = 1>
 ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   R s[15];
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
@@ -277,7 +277,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
     s[14] += Gyy * y * y;
   }
 #pragma unroll
-  for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * (R)g.w;
+  for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * pick<R>(g.w, g.fw);
   // H a = t - r by Gaussian elimination spread over lanes 0..5 (lane m holds
   // row m and its right-hand side; H is symmetric positive definite, so no
   // pivoting), pivot rows broadcast by shuffles.
@@ -410,7 +410,7 @@ ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)
   const size_t nc = V.g.nc;
   if (A.phi_store >= 0) {
     R phi[4];
-    euler_phi_cell<R>(V.g, A.U_prev, c, (R)V.m.eps_w, phi);
+    euler_phi_cell<R>(V.g, A.U_prev, c, pick<R>(V.m.eps_w, V.m.feps_w), phi);
 #pragma unroll
     for (int m = 0; m < 4; ++m) A.Phi[((size_t)A.phi_store * 4 + m) * nc + c] = (double)phi[m];
   }
@@ -499,14 +499,14 @@ ESBGK_DEV R transport_of(const R (&q)[7], R vx, R vy, R idx, R idy, R epsw) {
 template <typename R, int W>
 ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, const R* sf) {
   CellPar<R> P;
-  if (!es_params<R>(m, u0x, u0y, (R)g.w, R(0), R(0), false, P) || !project<R, W>(g, lane, P)) return R(-1);
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  if (!es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), R(0), R(0), false, P) || !project<R, W>(g, lane, P)) return R(-1);
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   R s = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
   for (; it.k < g.nvv; it.next())
 #pragma unroll
     for (int j = 0; j < W; ++j) s += rabs(sf[it.k + j] - ghat(P, it.vx() + R(j) * dv - P.ux, it.vy() - P.uy));
-  return warp_sum(s) * (R)g.w;
+  return warp_sum(s) * pick<R>(g.w, g.fw);
 }
 
 // Flag values of each compile-time stage shape (StageMode).
@@ -555,8 +555,9 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
   const S* sbase = (const S*)A.star_base;
   const bool has_src = GEN ? fsrc != nullptr : true;
   const bool base_is_src = GEN ? A.star_base == A.f_src : ModeT<M>::base_src;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
-  const R idx = (R)(1.0 / g.dx), idy = (R)(1.0 / g.dy), epsw = (R)V.m.eps_w, cL = (R)A.star_cL;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
+  const R idx = pick<R>(1.0 / g.dx, g.fidx), idy = pick<R>(1.0 / g.dy, g.fidy);
+  const R epsw = pick<R>(V.m.eps_w, V.m.feps_w), cL = pick<R>(A.star_cL, A.f_star_cL);
   const bool relax = GEN ? A.h_coef > 0.0 : ModeT<M>::relax;
   const bool proj = GEN ? (relax || A.need_q) : ModeT<M>::relax;
   S* fout = (S*)A.f_out;
@@ -571,8 +572,8 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
     ain[t] = t < nacc ? (const S*)A.acc_in[t] : nullptr;
     aout[t] = t < nacc ? (S*)A.acc_out[t] : nullptr;
     asrc[t] = t < nacc && (GEN ? ain[t] == fsrc : ModeT<M>::acc_src);
-    aL[t] = t < nacc ? (R)A.acc_cL[t] : R(0);
-    aQ[t] = t < nacc ? (R)A.acc_cQ[t] : R(0);
+    aL[t] = t < nacc ? pick<R>(A.acc_cL[t], A.f_acc_cL[t]) : R(0);
+    aQ[t] = t < nacc ? pick<R>(A.acc_cQ[t], A.f_acc_cQ[t]) : R(0);
   }
   R u0x, u0y;
   ref_velocity(A.U_prev, g.nc, c, u0x, u0y);
@@ -657,9 +658,9 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
   }
 
   // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
-  const R nu = R(V.m.tau) / R(V.eps[c]), h = R(A.h_coef) * nu;
+  const R nu = pick<R>(V.m.tau, V.m.ftau) / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
   CellPar<R> P;
-  bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, relax, P);
+  bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), h, relax, P);
   if (ok) ok = project<R>(g, lane, P);
   if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
 
@@ -721,8 +722,9 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   stencil_offsets(g, c, o);
   const S* fsrc = (const S*)A.f_src;
   const S* sbase = (const S*)A.star_base;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
-  const R idx = (R)(1.0 / g.dx), idy = (R)(1.0 / g.dy), epsw = (R)V.m.eps_w, cL = (R)A.star_cL;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
+  const R idx = pick<R>(1.0 / g.dx, g.fidx), idy = pick<R>(1.0 / g.dy, g.fidy);
+  const R epsw = pick<R>(V.m.eps_w, V.m.feps_w), cL = pick<R>(A.star_cL, A.f_star_cL);
   constexpr bool relax = MT::relax;
   constexpr int nacc = MT::nacc;
   S* fout = (S*)A.f_out;
@@ -733,8 +735,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   for (int t = 0; t < nacc; ++t) {
     ain[t] = (const S*)A.acc_in[t];
     aout[t] = (S*)A.acc_out[t];
-    aL[t] = (R)A.acc_cL[t];
-    aQ[t] = (R)A.acc_cQ[t];
+    aL[t] = pick<R>(A.acc_cL[t], A.f_acc_cL[t]);
+    aQ[t] = pick<R>(A.acc_cQ[t], A.f_acc_cQ[t]);
   }
   R u0x, u0y;
   ref_velocity(A.U_prev, g.nc, c, u0x, u0y);
@@ -822,9 +824,9 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   }
 
   // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
-  const R nu = R(V.m.tau) / R(V.eps[c]), h = R(A.h_coef) * nu;
+  const R nu = pick<R>(V.m.tau, V.m.ftau) / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
   CellPar<R> P;
-  bool ok = es_params<R>(m, u0x, u0y, (R)g.w, (R)V.m.beta, h, true, P);
+  bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), h, true, P);
   if (ok) ok = project<R, W>(g, lane, P);
   if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
 
@@ -869,7 +871,7 @@ ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&
   prim_of(U, rho, ux, uy, T);
   CellPar<R> P;
   if (!maxwell_params<R>(rho, ux, uy, T, P) || !project<R, W>(g, lane, P)) return false;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   const size_t o0 = (size_t)c * g.nvv;
   NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
 #pragma unroll 1
@@ -1003,7 +1005,7 @@ template <typename S>
 ESBGK_DEV void load_moments(const S* f, const Geo& g, int c, int lane, typename Real<S>::T u0x,
                             typename Real<S>::T u0y, typename Real<S>::T* sf, typename Real<S>::T (&m)[6]) {
   using R = typename Real<S>::T;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   const size_t o0 = (size_t)c * g.nvv;
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = R(0);
@@ -1035,7 +1037,7 @@ __global__ void __launch_bounds__(kCellThreads) l1_kernel(const void* fptr, cons
   R* sf = reinterpret_cast<R*>(dsm) + (size_t)warp * g.nvv;
   const S* f = (const S*)fptr;
   const int nK = V.counts[0];
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   for (int u = blockIdx.x * nwarps + warp; u < nK; u += gridDim.x * nwarps) {
     const int c = V.klist[u];
     R u0x, u0y, m[6];
@@ -1043,7 +1045,7 @@ __global__ void __launch_bounds__(kCellThreads) l1_kernel(const void* fptr, cons
     load_moments<S>(f, g, c, lane, u0x, u0y, sf, m);
     // Maxwellian of f's own moments: the ES tensor with beta = 0
     CellPar<R> P;
-    bool ok = es_params<R>(m, u0x, u0y, (R)g.w, R(0), R(0), false, P);
+    bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), R(0), R(0), false, P);
     if (ok) ok = project<R>(g, lane, P);
     if (!ok) {
       if (lane == 0) report_error(V.err, kErrNonRealizable, c);
@@ -1067,14 +1069,14 @@ __global__ void __launch_bounds__(kCellThreads) relax_cells_kernel(const S* fsta
   extern __shared__ __align__(16) unsigned char dsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   R* sf = reinterpret_cast<R*>(dsm) + (size_t)warp * g.nvv;
-  const R v0 = (R)(-g.vmax + 0.5 * g.dv), dv = (R)g.dv;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   for (int c = blockIdx.x * nwarps + warp; c < n; c += gridDim.x * nwarps) {
     const size_t o0 = (size_t)c * g.nvv;
     R m[6];
     load_moments<S>(fstar, g, c, lane, R(0), R(0), sf, m);
     const R hh = (R)h[c];
     CellPar<R> P;
-    bool ok = es_params<R>(m, R(0), R(0), (R)g.w, (R)beta, hh, true, P);
+    bool ok = es_params<R>(m, R(0), R(0), pick<R>(g.w, g.fw), (R)beta, hh, true, P);
     if (ok) ok = project<R>(g, lane, P);
     const R nan = R(__int_as_float(0x7fc00000));
     const R inv1h = R(1) / (R(1) + hh);

@@ -60,6 +60,8 @@ struct StageArgs {
   double* l1_out;  // when set (final combination only): ||f - M_hat[f]||_L1 of the result per kinetic cell
   int* wq;         // work counter of the launch (zeroed by the step's prep): units past the first wave are
                    // claimed from it; null: static round-robin
+  // float copies of the stage coefficients for the FP32 arithmetic
+  float f_star_cL, f_h_coef, f_acc_cL[3], f_acc_cQ[3];
 };
 
 // Start-of-step preparation: f := M_hat[U] in the cells of list1 and list2;
