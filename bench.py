@@ -201,6 +201,21 @@ def stored_traffic(prec, workload):
         return None
 
 
+def combine_ranks(ms, updates, device, world):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the sum of every rank's updates (the only collectives of a run; the data
+    path has none)."""
+    if world <= 1:
+        return ms, float(updates)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def ours_arm(args):
     import torch
     import torch.distributed as dist
@@ -252,14 +267,7 @@ def ours_arm(args):
     s.sync()
     c1 = s.counters()
     updates = (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv
-    if world > 1:
-        t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(mx[0]), float(t[1])
-    else:
-        ms_max, updates_all = ms, float(updates)
+    ms_max, updates_all = combine_ranks(ms, float(updates), dev, world)
     value = updates_all / (ms_max * 1e-3)
 
     # --- per-kernel device times (separate pass; events around each launch)
@@ -413,14 +421,7 @@ def batch_arm(args):
     b.sync()
     c1 = b.counters()
     updates = (c1["element_updates"] - c0["element_updates"]) * 1.0
-    if world > 1:
-        t = torch.tensor([ms, updates], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(mx[0]), float(t[1])
-    else:
-        ms_max, updates_all = ms, updates
+    ms_max, updates_all = combine_ranks(ms, updates, dev, world)
     value = updates_all / (ms_max * 1e-3)
 
     # per-kernel device times (plain launches with events)
