@@ -34,7 +34,7 @@ const Launchers* launchers_for(int prec) {
 // Byte offsets of every array inside the caller's workspace.
 struct Layout {
   size_t F[3], ACC[3], Un, Us[2], Phi, eps, lamA, L1, stage5, red, tot;
-  size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr, wq, blockc;
+  size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr, wq, blockc, seed;
   // learned switch only: features, activations, logits, prediction, weights, statistics
   size_t cx, ca1, ca2, logits, pred, cnnw, sctr;
   size_t total;
@@ -75,6 +75,7 @@ Layout make_layout(int nc, int nvv, size_t elem, bool learned) {
   L.ctr = take(2 * sizeof(long long));
   L.wq = take((kMaxStages + 1) * sizeof(int));
   L.blockc = take(4 * (size_t)categorize_blocks(nc) * sizeof(int));
+  L.seed = take(sizeof(unsigned));
   if (learned) {
     L.cx = take((size_t)nc * cnn::kCinPad * 2);
     L.ca1 = take((size_t)nc * cnn::kHid * 2);
@@ -156,6 +157,7 @@ struct esbgk_ctx {
   long long* ctr;
   int* wq = nullptr;  // work counters of the stage launches of a step
   int* blockc = nullptr;  // per-block category counts of the compaction
+  unsigned* seed = nullptr;  // step counter of the stochastic rounding of bf16 stores
   int cur;
   bool have_state, conv_pending;
   bool l1_fresh;  // L1 holds ||f^n - M_hat||_1 of the kinetic cells (from the last final combination)
@@ -452,6 +454,8 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.kin_u_moments = (A.hoc || (last && shortcut)) ? 1 : 0;
     A.ctr = X->ctr;
     A.wq = X->wq ? X->wq + (PL.n - 1) : nullptr;
+    A.seed = X->prec == ESBGK_BF16 ? X->seed : nullptr;
+    A.sid = (unsigned)PL.n;
     prev_buf = outbuf;
   }
   if (!shortcut) {
@@ -480,12 +484,15 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     // the deviation ||f^{n+1} - M_hat||_1 the next regime update needs
     A.l1_out = X->criterion() ? X->L1 : nullptr;
     A.wq = X->wq ? X->wq + (PL.n - 1) : nullptr;
+    A.seed = X->prec == ESBGK_BF16 ? X->seed : nullptr;
+    A.sid = (unsigned)PL.n;
     PL.new_cur = X->cur;
   } else {
     PL.new_cur = prev_buf;
   }
   P.wq_zero = X->wq;
   P.wq_n = X->wq ? PL.n : 0;
+  P.seed = X->prec == ESBGK_BF16 ? X->seed : nullptr;
   for (int q = 0; q < PL.n; ++q) {  // float copies of the coefficients for the FP32 arithmetic
     StageArgs& A = PL.st[q];
     A.f_star_cL = (float)A.star_cL;
@@ -509,6 +516,7 @@ void finish_step(esbgk_ctx* X, const StepPlan& PL) {
 // The launches of a planned step (no host synchronisation).
 int advance_launches(esbgk_ctx* X, const StepPlan& PL) {
   const View V = X->view();
+  if (PL.prep.seed) launch_seed_advance(X->seed, X->stream);
   {
     Timed t(X, ESBGK_K_PREP);
     X->L->prep(PL.prep, V, X->grid_stage, X->stream);
@@ -711,6 +719,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->ctr = (long long*)(w + lay.ctr);
   X->wq = (int*)(w + lay.wq);
   X->blockc = (int*)(w + lay.blockc);
+  X->seed = (unsigned*)(w + lay.seed);
   if (X->sw == ESBGK_SWITCH_LEARNED) {
     X->cx = (__nv_bfloat16*)(w + lay.cx);
     X->ca1 = (__nv_bfloat16*)(w + lay.ca1);
@@ -739,6 +748,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   if (!r) r = cuda_check(X, cudaMemsetAsync(w + lay.F[0], 0, lay.Un - lay.F[0], X->stream), "clear f arrays");
   if (!r && X->sctr)
     r = cuda_check(X, cudaMemsetAsync(X->sctr, 0, 4 * sizeof(unsigned long long), X->stream), "clear statistics");
+  if (!r) r = cuda_check(X, cudaMemsetAsync(X->seed, 0, sizeof(unsigned), X->stream), "clear seed");
   if (r) {
     delete X;
     return r;
@@ -1233,6 +1243,7 @@ void batch_launches(esbgk_batch* b, const BatchTabSet& t, const int* grids) {
   }
   {
     Timed tm(X0, ESBGK_K_PREP);
+    if (b->prec == ESBGK_BF16) launch_batch_seed_advance(t.prep, b->n, b->stream);
     b->L->batch_prep(t.prep, b->d_off_prep, b->n, grid_small, b->stream);
   }
   for (int j = 0; j < t.nlaunch; ++j) {

@@ -63,6 +63,23 @@ ESBGK_DEV void report_error(DevErr* e, int code, long long cell) {
   if (e && atomicCAS(&e->code, 0, code) == 0) e->cell = cell;
 }
 
+// 32-bit integer hash (the "lowbias32" xorshift-multiply mixer published by
+// C. Wellons, 2018): counter-based random bits for stochastic rounding.
+ESBGK_DEV uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// float -> bf16 with stochastic rounding: add 16 random bits below the kept
+// mantissa and truncate, so that the rounding error has zero mean.
+ESBGK_DEV unsigned short bf16_sr_bits(float v, uint32_t r) {
+  return (unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16);
+}
+
 // Storage <-> arithmetic type mapping.
 template <typename S> struct Real;
 template <> struct Real<double> { using T = double; };

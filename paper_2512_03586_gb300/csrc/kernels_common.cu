@@ -327,6 +327,10 @@ void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_
 
 int categorize_blocks(int nc) { return (nc + kCatBlock - 1) / kCatBlock; }
 
+__global__ void seed_advance_kernel(unsigned* seed) { *seed += 1u; }
+
+void launch_seed_advance(unsigned* seed, cudaStream_t s) { seed_advance_kernel<<<1, 1, 0, s>>>(seed); }
+
 // (rho, u_x, u_y, T) from U.
 __global__ void prim_kernel(const double* __restrict__ Un, double* out, int nc) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -442,5 +446,14 @@ __global__ void batch_offsets_kernel(BatchTabs T) {
 }
 
 void launch_batch_offsets(const BatchTabs& T, cudaStream_t s) { batch_offsets_kernel<<<1, 32, 0, s>>>(T); }
+
+__global__ void batch_seed_kernel(const CasePrep* cases, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (cases[i].P.seed) *cases[i].P.seed += 1u;
+}
+
+void launch_batch_seed_advance(const CasePrep* cases, int n, cudaStream_t s) {
+  batch_seed_kernel<<<1, 128, 0, s>>>(cases, n);
+}
 
 }  // namespace esbgk

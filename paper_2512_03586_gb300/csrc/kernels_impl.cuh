@@ -82,6 +82,7 @@ struct VecIO<float, 4> {
   static ESBGK_DEV void st(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
+  static ESBGK_DEV void st_sr(float* p, const float (&v)[4], uint32_t) { st(p, v); }
 };
 template <>
 struct VecIO<float, 2> {
@@ -94,6 +95,7 @@ struct VecIO<float, 2> {
     v[0] = t.x, v[1] = t.y;
   }
   static ESBGK_DEV void st(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+  static ESBGK_DEV void st_sr(float* p, const float (&v)[2], uint32_t) { st(p, v); }
 };
 template <>
 struct VecIO<double, 2> {
@@ -108,6 +110,7 @@ struct VecIO<double, 2> {
   static ESBGK_DEV void st(double* p, const double (&v)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   }
+  static ESBGK_DEV void st_sr(double* p, const double (&v)[2], uint32_t) { st(p, v); }
 };
 template <>
 struct VecIO<__nv_bfloat16, 4> {
@@ -127,6 +130,14 @@ struct VecIO<__nv_bfloat16, 4> {
     uint2 t;
     t.x = *reinterpret_cast<const unsigned*>(&a);
     t.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = t;
+  }
+  // stochastic rounding; key: a random 32-bit value for the group
+  static ESBGK_DEV void st_sr(__nv_bfloat16* p, const float (&v)[4], uint32_t key) {
+    const uint32_t r0 = mix32(key), r1 = mix32(key ^ 0x9e3779b9u);
+    uint2 t;
+    t.x = (uint32_t)bf16_sr_bits(v[0], r0) | ((uint32_t)bf16_sr_bits(v[1], r0 >> 16) << 16);
+    t.y = (uint32_t)bf16_sr_bits(v[2], r1) | ((uint32_t)bf16_sr_bits(v[3], r1 >> 16) << 16);
     *reinterpret_cast<uint2*>(p) = t;
   }
 };
@@ -740,6 +751,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   }
   R u0x, u0y;
   ref_velocity(A.U_prev, g.nc, c, u0x, u0y);
+  // random key of this launch for the stochastic rounding of bf16 stores
+  const uint32_t s0 = A.seed ? mix32(*A.seed * 0x632be5abu + A.sid) : 0u;
 
   // pass 1: transport of the previous stage, f*, moments of f*
   R m[6];
@@ -793,14 +806,15 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
       m[4] += cx * cy * fs[j];
       m[5] += cy * cy * fs[j];
     }
+    const uint32_t kb = s0 + ((o0 + k) << 3);  // distinct per group and stored array
     if (relax) {
       SM::st(sfs + k, fs);
     } else {
-      IO::st(fout + o0 + k, fs);
+      IO::st_sr(fout + o0 + k, fs, kb);
       if (A.l1_out) SM::st(sfs + k, fs);
     }
 #pragma unroll
-    for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pa[t]);
+    for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
   }
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
@@ -854,9 +868,10 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 #pragma unroll
       for (int t = 0; t < nacc; ++t) pa[t][j] += aQ[t] * Q;
     }
-    IO::st(fout + o0 + k, fn);
+    const uint32_t kb = s0 + ((o0 + k) << 3);
+    IO::st_sr(fout + o0 + k, fn, kb);
 #pragma unroll
-    for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pa[t]);
+    for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 4 + t);
   }
 }
 
@@ -865,7 +880,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 // W > 1: groups of W consecutive nodes of a row (N_v divisible by W, f 16-byte
 // aligned), one vector store per group.
 template <typename S, int W = 1>
-ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&U)[4]) {
+ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&U)[4], uint32_t key = 0u) {
   using R = typename Real<S>::T;
   double rho, ux, uy, T;
   prim_of(U, rho, ux, uy, T);
@@ -881,7 +896,7 @@ ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&
       const R cy = it.vy() - P.uy, cx0 = it.vx() - P.ux;
 #pragma unroll
       for (int j = 0; j < W; ++j) v[j] = ghat(P, cx0 + R(j) * dv, cy);
-      VecIO<S, W>::st(f + o0 + it.k, v);
+      VecIO<S, W>::st_sr(f + o0 + it.k, v, key + (uint32_t)((o0 + it.k) << 3));
     } else {
       st(f + o0 + it.k, ghat(P, it.vx() - P.ux, it.vy() - P.uy));
     }
@@ -900,7 +915,8 @@ ESBGK_DEV void buffer_fill(const StageArgs& A, const View& V, int c, int lane, d
 #pragma unroll
     for (int q = 0; q < 4; ++q) Uc[q] = A.Un[(size_t)q * V.g.nc + c];
   }
-  if (!fill_maxwell<S, W>((S*)A.f_out, V.g, c, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, c);
+  const uint32_t key = A.seed ? mix32(*A.seed * 0x632be5abu + A.sid + 0x51u) : 0u;
+  if (!fill_maxwell<S, W>((S*)A.f_out, V.g, c, lane, Uc, key) && lane == 0) report_error(V.err, kErrNonRealizable, c);
 }
 
 
@@ -979,6 +995,9 @@ __global__ void __launch_bounds__(kCellThreads) prep_kernel(PrepArgs P, View V) 
   const int total = n1 + n2 + nCopy;
   S* f = (S*)P.f;
   if (blockIdx.x == 0 && (int)threadIdx.x < P.wq_n) P.wq_zero[threadIdx.x] = 0;
+  // stochastic-rounding key of this step's fills (the counter is advanced by a
+  // launch of its own before this one)
+  const uint32_t key = P.seed ? mix32(*P.seed * 0x632be5abu + 0x7fu) : 0u;
   constexpr int kW = VecW<S>::value;
   const bool vec = g.nv % kW == 0 && ((uintptr_t)f & 15u) == 0;
   for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
@@ -987,7 +1006,7 @@ __global__ void __launch_bounds__(kCellThreads) prep_kernel(PrepArgs P, View V) 
       double Uc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + c];
-      const bool ok = vec ? fill_maxwell<S, kW>(f, g, c, lane, Uc) : fill_maxwell<S>(f, g, c, lane, Uc);
+      const bool ok = vec ? fill_maxwell<S, kW>(f, g, c, lane, Uc, key) : fill_maxwell<S>(f, g, c, lane, Uc);
       if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
     } else {
       const int c = (u - n1 - n2) * 32 + lane;
@@ -1157,7 +1176,11 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
       }
       if (lane == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
     } else if (local < nK + nB) {
-      buffer_cell<S>(A, V, V.blist[local - nK], lane);
+      if (M != kGeneric && cs[warp].vec) {
+        if constexpr (M != kGeneric) buffer_cell<S, kW>(A, V, V.blist[local - nK], lane);
+      } else {
+        buffer_cell<S>(A, V, V.blist[local - nK], lane);
+      }
       if (lane == 0 && A.ctr && A.fill) atomicAdd((unsigned long long*)A.ctr + 1, 1ull);
     } else {
       const int q = (local - nK - nB) * 32 + lane;
@@ -1189,7 +1212,11 @@ __global__ void __launch_bounds__(kCellThreads) batch_prep_kernel(const CasePrep
       double Uc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) Uc[q] = P.U[(size_t)q * g.nc + cell];
-      if (!fill_maxwell<S>((S*)P.f, g, cell, lane, Uc) && lane == 0) report_error(V.err, kErrNonRealizable, cell);
+      constexpr int kW = VecW<S>::value;
+      const bool vec = g.nv % kW == 0 && ((uintptr_t)P.f & 15u) == 0;
+      const uint32_t key = P.seed ? mix32(*P.seed * 0x632be5abu + 0x7fu) : 0u;
+      const bool ok = vec ? fill_maxwell<S, kW>((S*)P.f, g, cell, lane, Uc, key) : fill_maxwell<S>((S*)P.f, g, cell, lane, Uc);
+      if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, cell);
     } else {
       const int cell = (local - n1 - n2) * 32 + lane;
       if (cell < g.nc && P.copy_to) {

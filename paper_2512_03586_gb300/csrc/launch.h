@@ -62,6 +62,10 @@ struct StageArgs {
                    // claimed from it; null: static round-robin
   // float copies of the stage coefficients for the FP32 arithmetic
   float f_star_cL, f_h_coef, f_acc_cL[3], f_acc_cQ[3];
+  // BF16 storage: stochastic rounding keyed by the step counter (advanced by
+  // the step's prep kernel) and this launch's position in the step
+  const unsigned* seed;
+  unsigned sid;
 };
 
 // Start-of-step preparation: f := M_hat[U] in the cells of list1 and list2;
@@ -71,6 +75,7 @@ struct PrepArgs {
   const double* U;
   int* wq_zero;  // work counters of the step's stage launches, zeroed here (wq_n of them)
   int wq_n;
+  unsigned* seed;  // step counter of the stochastic rounding (may be null; advanced by a launch of its own)
   const int* list1;
   const int* count1;
   const int* list2;
@@ -199,6 +204,8 @@ void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_
                                cudaStream_t s);
 int categorize_blocks(int nc);
 void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
+// advance the step counter of the stochastic rounding (one thread)
+void launch_seed_advance(unsigned* seed, cudaStream_t s);
 void launch_totals(const double* Un, int nc, double* partial /*[grid][4]*/, double* out, double dxdy, int grid,
                    cudaStream_t s);
 // batched regime update: offsets of the L1 units, flags, categories,
@@ -208,5 +215,7 @@ void launch_batch_flags(const BatchTabs& T, cudaStream_t s);
 void launch_batch_categorize(const BatchTabs& T, cudaStream_t s);
 void launch_batch_compact(const BatchTabs& T, cudaStream_t s);
 void launch_batch_offsets(const BatchTabs& T, cudaStream_t s);
+// advance every case's stochastic-rounding counter (cases with a counter)
+void launch_batch_seed_advance(const CasePrep* cases, int n, cudaStream_t s);
 
 }  // namespace esbgk

@@ -5,8 +5,11 @@ against FP64 and the relative mass drift.
 
 Bars: FP32 storage -- relative L1 error <= 1e-5 per field after the run and
 relative mass drift <= 1e-6.  BF16 storage (8 significant bits) cannot reach
-1e-5: each store rounds f by up to 2^-9 relative; the bound asserted here is
-the one measured with a margin, and the numbers are printed.
+1e-5: each store rounds f by up to 2^-8 relative.  BF16 stores round
+stochastically (unbiased), so the per-store errors average out in the
+moments instead of accumulating a bias; the bounds asserted here are the
+measured values (full size: <= 5.3e-4 per field, drift 9.8e-6) with a
+margin, and the numbers are printed.
 
 The small case is checked against the FP64 CPU oracle; the full-size blob
 (256 x 256 cells, 48 x 48 velocities, 100 ARS(2,3,3) steps) against the FP64
@@ -52,7 +55,7 @@ def test_precision_small_against_oracle():
     print("\nsmall blob vs oracle (rho, m_x, m_y, E; mass drift):", out)
     assert max(out["fp64"][0]) <= 1e-10
     assert max(out["fp32"][0]) <= 1e-5 and out["fp32"][1] <= 1e-6
-    assert max(out["bf16"][0]) <= 1e-2
+    assert max(out["bf16"][0]) <= 2e-3 and out["bf16"][1] <= 1e-4
 
 
 def test_precision_full_size_blob():
@@ -66,4 +69,4 @@ def test_precision_full_size_blob():
           "FP64 drift %.2e" % (steps, ["%.2e" % e for e in e32], d32, ["%.2e" % e for e in e16], d16, d64))
     assert d64 <= 1e-12
     assert max(e32) <= 1e-5 and d32 <= 1e-6
-    assert max(e16) <= 5e-2
+    assert max(e16) <= 2e-3 and d16 <= 5e-5
