@@ -45,7 +45,7 @@ typedef enum {
   ESBGK_E_CUDA = -3,           /* a CUDA runtime call failed; see esbgk_last_error   */
   ESBGK_E_NONREALIZABLE = -4,  /* rho <= 0, T <= 0, det(temperature tensor) <= 0 or a
                                   singular moment system in some cell                */
-  ESBGK_E_TIMEOUT = -5,        /* reserved: a bounded device wait expired           */
+  ESBGK_E_TIMEOUT = -5,        /* a bounded device wait (tensor cores) expired      */
   ESBGK_E_STATE = -6,          /* call out of order (e.g. step before set_state)    */
   ESBGK_E_TOO_LARGE = -7       /* problem exceeds the fixed scratch of
                                   esbgk_kinetic_steps_noalloc                        */

@@ -282,6 +282,10 @@ int sync_and_check(esbgk_ctx* X) {
   DevErr e{};
   r = cuda_check(X, cudaMemcpy(&e, X->err, sizeof(e), cudaMemcpyDeviceToHost), "read error word");
   if (r) return r;
+  if (e.code == kErrTimeout) {
+    X->bad_cell = -1;
+    return fail(X, ESBGK_E_TIMEOUT, "bounded wait for the tensor cores (learned switch) expired");
+  }
   if (e.code != 0) {
     X->bad_cell = e.cell;
     char buf[160];
@@ -324,7 +328,7 @@ int regime_launches(esbgk_ctx* X, bool l1_needed, bool judge_prev) {
     Timed t(X, ESBGK_K_OTHER);
     const double d = X->g.dx < X->g.dy ? X->g.dx : X->g.dy;
     cnn::launch_features(X->Un, X->eps, X->g.nc, d, X->cx, X->stream);
-    cnn::launch_forward(X->cw, X->cx, 1, X->g.ny, X->g.nx, X->ca1, X->ca2, X->logits, X->stream);
+    cnn::launch_forward(X->cw, X->cx, 1, X->g.ny, X->g.nx, X->ca1, X->ca2, X->logits, &X->err->code, X->stream);
     cnn::launch_judge(X->flags, X->pred, X->logits, X->g.nc, judge_prev ? 1 : 0, X->sctr, X->stream);
   }
   if ((r = after_launch(X, "learned switch"))) return r;

@@ -7,7 +7,11 @@
 // mma.sync.m16n8k16); the 1 x 1 head, the loss and the optimizer are float32
 // on the CUDA cores.
 //
-// Tiling: a CTA owns 8 x 16 output cells of one image; its 4 warps own two
+// The forward 32 -> 32 convolution runs on the 5th-generation tensor cores
+// (tcgen05.mma with a tensor-memory accumulator, conv32_tc_kernel); the other
+// convolutions use mma.sync.
+//
+// Tiling (mma.sync kernels): a CTA owns 8 x 16 output cells of one image; its 4 warps own two
 // rows of 16 cells each (one m16 tile per row) and all 32 output channels
 // (four n8 tiles).  The input halo (10 x 18 cells, channels contiguous, cell
 // stride padded by 8 bf16 so that the fragment loads of the 8 row groups
@@ -16,6 +20,8 @@
 #include "cnn.h"
 
 #include <string>
+
+#include "common.cuh"
 
 #include "../../include/esbgk.h"
 
@@ -139,6 +145,139 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(const bf* __restrict__ i
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 channel 3 x 3 convolution on the 5th-generation tensor cores
+// (tcgen05.mma, accumulator in tensor memory).  A CTA owns a row segment of
+// TC_M = 128 consecutive cells of one image row: D[128 cells][32 out] is the
+// sum of 18 MMAs of depth 16 (9 taps x 32 input channels),
+// A[128 cells][16] x B[16][32].
+// Shared-memory operands use the no-swizzle K-major layout of 8-row x
+// 16-byte core matrices:
+//   A: the input halo, 3 rows x (TC_M + 2) cells, stored as 4 planes of 8
+//      channels ([plane][row][cell][8]); the rows of a tap's A operand are
+//      consecutive cells of one halo row, so a core matrix (8 cells x 8
+//      channels) is 128 contiguous bytes, the next 8 cells follow at +128 B
+//      (stride byte offset) and the next 8 channels at +plane (leading byte
+//      offset); a tap is only a different start address.
+//   B: the weights as [k group of 8][32 out][8]: core matrices at +128 B
+//      along N and +512 B along K.
+constexpr int TC_M = 128, TC_HW = TC_M + 2, TC_PLANE = 3 * TC_HW * 16;  // bytes of one 8-channel plane
+constexpr int TC_WBYTES = kK2 / 8 * 512;                                  // 36 k groups x 512 B
+constexpr size_t kTcSmem = 4 * (size_t)TC_PLANE + TC_WBYTES;
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // start address, leading and stride byte offsets (all >> 4), descriptor
+  // version 1, base offset 0, no swizzle
+  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: bf16 A and B (both K-major), f32
+// accumulator, M = 128, N = 32.
+constexpr uint32_t kTcIdesc = (1u << 4)                // D format f32
+                              | (1u << 7) | (1u << 10)  // A, B bf16
+                              | ((32u >> 3) << 17)      // N >> 3
+                              | ((128u >> 4) << 24);    // M >> 4
+
+__global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ in, const bf* __restrict__ wk,
+                                                        const float* __restrict__ bias, int H, int W,
+                                                        bf* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* sa = tsm;                 // A halo, 4 planes
+  unsigned char* sb = tsm + 4 * TC_PLANE;  // B weights
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_b[kHid];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int segs = (W + TC_M - 1) / TC_M;
+  const int img = blockIdx.y, y = blockIdx.x / segs, x0 = (blockIdx.x % segs) * TC_M;
+
+  if (warp == 0) {  // 32 columns of tensor memory for the f32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    mbar_init_fence();
+  }
+  if (tid < kHid) s_b[tid] = bias[tid];
+  // weights W2f[o][k] (k = tap*32 + c) -> [k/8][o][k%8], 16-byte pieces
+  for (int i = tid; i < kHid * kK2 / 8; i += blockDim.x) {
+    const int o = i / (kK2 / 8), kg = i % (kK2 / 8);
+    *reinterpret_cast<uint4*>(sb + kg * 512 + o * 16) = *reinterpret_cast<const uint4*>(wk + (size_t)o * kK2 + kg * 8);
+  }
+  // halo rows y-1..y+1, cells x0-1..x0+TC_M, zeros outside the image
+  for (int i = tid; i < 3 * TC_HW * 4; i += blockDim.x) {
+    const int pl = i % 4, cell = i / 4, r = cell / TC_HW, cx = cell % TC_HW;
+    const int gy = y + r - 1, gx = x0 + cx - 1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+      v = *reinterpret_cast<const uint4*>(in + (((size_t)img * H + gy) * W + gx) * kHid + pl * 8);
+    *reinterpret_cast<uint4*>(sa + pl * TC_PLANE + (r * TC_HW + cx) * 16) = v;
+  }
+  // operands written by the threads are read by the tensor cores (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+#pragma unroll 1
+    for (int j = 0; j < 18; ++j) {  // depth step j: tap j/2, input channels (j%2)*16 .. +15
+      const int tap = j >> 1, ky = tap / 3, kx = tap % 3, cg = (j & 1) * 2;
+      const uint64_t ad = smem_desc(a0 + cg * TC_PLANE + (ky * TC_HW + kx) * 16, TC_PLANE, 128);
+      const uint64_t bd = smem_desc(b0 + (tap * 4 + cg) * 512, 512, 128);
+      const uint32_t acc = j > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&mbar))
+                 : "memory");
+  }
+  // bounded wait for the MMAs; every thread waits (acquire), the outcome is uniform
+  const bool done = __syncthreads_and(mbar_wait(&mbar, 0));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    if (tid == 0 && err) atomicCAS(err, 0, kErrTimeout);
+  } else {
+    // warp w reads tensor-memory lanes 32w..32w+31 (its cells), 32 columns (channels)
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int gx = x0 + 32 * warp + lane;
+    if (gx < W) {
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + (((size_t)img * H + y) * W + gx) * kHid);
+#pragma unroll
+      for (int o = 0; o < kHid; o += 2) {
+        const float a = fmaxf(__uint_as_float(v[o]) + s_b[o], 0.f);
+        const float b = fmaxf(__uint_as_float(v[o + 1]) + s_b[o + 1], 0.f);
+        dst[o / 2] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int H, int W, bf* out, int* err,
+                      cudaStream_t s) {
+  const int segs = (W + TC_M - 1) / TC_M;
+  conv32_tc_kernel<<<dim3(H * segs, n), 128, kTcSmem, s>>>(in, wk, bias, H, W, out, err);
 }
 
 // Weight gradient of a 3 x 3 convolution, per CTA partial sums over the
@@ -447,10 +586,10 @@ void launch_features(const double* U, const double* eps, int nc, double dx, bf* 
 
 static dim3 conv_grid(int n, int H, int W) { return dim3((W + TW - 1) / TW, (H + TH - 1) / TH, n); }
 
-void launch_forward(const Weights& w, const bf* x, int n, int H, int W, bf* a1, bf* a2, float* logits,
+void launch_forward(const Weights& w, const bf* x, int n, int H, int W, bf* a1, bf* a2, float* logits, int* err,
                     cudaStream_t s) {
   conv_kernel<kCinPad, kFwd><<<conv_grid(n, H, W), kThreads, 0, s>>>(x, w.w1f, w.theta + kOffB1, H, W, a1, nullptr);
-  conv_kernel<kHid, kFwd><<<conv_grid(n, H, W), kThreads, 0, s>>>(a1, w.w2f, w.theta + kOffB2, H, W, a2, nullptr);
+  launch_conv32_tc(a1, w.w2f, w.theta + kOffB2, n, H, W, a2, err, s);
   const int M = n * H * W;
   head_kernel<<<(M + kHeadThreads - 1) / kHeadThreads, kHeadThreads, 0, s>>>(a2, w.theta, M, logits, nullptr, 0.f,
                                                                             0.f, nullptr, nullptr);
@@ -476,6 +615,7 @@ struct esbgk_cnn {
   float *m, *v, *grad, *logits, *part, *loss;
   __nv_bfloat16 *a1, *a2, *dz2, *dz1;
   int nparts;  // CTAs of the weight-gradient kernels
+  int* err;    // device error word (kErrTimeout: a bounded wait for the tensor cores expired)
   long long t;
   std::string msg;
 };
@@ -483,7 +623,7 @@ struct esbgk_cnn {
 namespace {
 
 struct CnnLayout {
-  size_t w, m, v, grad, logits, part, loss, a1, a2, dz2, dz1, total;
+  size_t w, m, v, grad, logits, part, loss, a1, a2, dz2, dz1, err, total;
   int nparts;
 };
 
@@ -511,6 +651,7 @@ bool cnn_layout(int max_n, int H, int W, CnnLayout& L) {
   L.a2 = take(M * kHid * 2);
   L.dz2 = take(M * kHid * 2);
   L.dz1 = take(M * kHid * 2);
+  L.err = take(sizeof(int));
   L.total = p;
   return true;
 }
@@ -521,6 +662,20 @@ int cnn_check(esbgk_cnn* c, cudaError_t e, const char* where) {
   return ESBGK_E_CUDA;
 }
 
+// After a synchronisation: the device error word.
+int cnn_sync_check(esbgk_cnn* c, const char* where) {
+  int r = cnn_check(c, cudaStreamSynchronize(c->stream), where);
+  if (r) return r;
+  int e = 0;
+  r = cnn_check(c, cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost), "read error word");
+  if (r) return r;
+  if (e == esbgk::kErrTimeout) {
+    c->msg = "bounded wait for the tensor cores expired";
+    return ESBGK_E_TIMEOUT;
+  }
+  return ESBGK_OK;
+}
+
 // Forward and backward passes of n images: gradient into c->grad, loss
 // into c->loss (device).
 void backward_launches(esbgk_cnn* c, const __nv_bfloat16* x, const uint8_t* y, int n, float pos_weight) {
@@ -528,7 +683,7 @@ void backward_launches(esbgk_cnn* c, const __nv_bfloat16* x, const uint8_t* y, i
   cudaStream_t s = c->stream;
   const dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, n);
   conv_kernel<kCinPad, kFwd><<<grid, kThreads, 0, s>>>(x, c->w.w1f, c->w.theta + kOffB1, H, W, c->a1, nullptr);
-  conv_kernel<kHid, kFwd><<<grid, kThreads, 0, s>>>(c->a1, c->w.w2f, c->w.theta + kOffB2, H, W, c->a2, nullptr);
+  launch_conv32_tc(c->a1, c->w.w2f, c->w.theta + kOffB2, n, H, W, c->a2, c->err, s);
   const int hb = (M + kHeadThreads - 1) / kHeadThreads;
   head_kernel<<<hb, kHeadThreads, 0, s>>>(c->a2, c->w.theta, M, c->logits, y, pos_weight, 1.f / M, c->dz2, c->part);
   reduce_head_kernel<<<1, 64, 0, s>>>(c->part, hb, c->grad, c->loss);
@@ -575,6 +730,7 @@ int esbgk_cnn_create(int32_t max_images, int32_t H, int32_t W, void* workspace, 
   c->a2 = (__nv_bfloat16*)(p + L.a2);
   c->dz2 = (__nv_bfloat16*)(p + L.dz2);
   c->dz1 = (__nv_bfloat16*)(p + L.dz1);
+  c->err = (int*)(p + L.err);
   c->nparts = L.nparts;
   c->t = 0;
   const cudaError_t e = cudaMemsetAsync(workspace, 0, L.total, c->stream);
@@ -608,7 +764,7 @@ int esbgk_cnn_get_params(esbgk_cnn* c, float* theta) {
 
 int esbgk_cnn_forward(esbgk_cnn* c, const void* x, int32_t n, float* logits) {
   if (!c || !x || !logits || n < 1 || n > c->max_n) return ESBGK_E_ARG;
-  launch_forward(c->w, (const __nv_bfloat16*)x, n, c->H, c->W, c->a1, c->a2, logits, c->stream);
+  launch_forward(c->w, (const __nv_bfloat16*)x, n, c->H, c->W, c->a1, c->a2, logits, c->err, c->stream);
   return cnn_check(c, cudaGetLastError(), "cnn forward");
 }
 
@@ -620,7 +776,7 @@ int esbgk_cnn_gradient(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n,
   if (!r && grad)
     r = cnn_check(c, cudaMemcpyAsync(grad, c->grad, kParams * 4, cudaMemcpyDeviceToHost, c->stream), "grad copy");
   if (!r && loss) r = cnn_check(c, cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream), "loss copy");
-  return r ? r : cnn_check(c, cudaStreamSynchronize(c->stream), "gradient sync");
+  return r ? r : cnn_sync_check(c, "gradient sync");
 }
 
 int esbgk_cnn_train_step(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t n, float pos_weight, float lr,
@@ -635,14 +791,14 @@ int esbgk_cnn_train_step(esbgk_cnn* c, const void* x, const uint8_t* y, int32_t 
   int r = cnn_check(c, cudaGetLastError(), "cnn train step");
   if (!r && loss) {
     r = cnn_check(c, cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream), "loss copy");
-    if (!r) r = cnn_check(c, cudaStreamSynchronize(c->stream), "train sync");
+    if (!r) r = cnn_sync_check(c, "train sync");
   }
   return r;
 }
 
 int esbgk_cnn_sync(esbgk_cnn* c) {
   if (!c) return ESBGK_E_ARG;
-  return cnn_check(c, cudaStreamSynchronize(c->stream), "cnn sync");
+  return cnn_sync_check(c, "cnn sync");
 }
 
 }  // extern "C"

@@ -45,9 +45,11 @@ size_t carve_weights(unsigned char* p, Weights& w);
 // Launchers (all asynchronous on stream s).
 void launch_pack(const Weights& w, cudaStream_t s);  // bf16 operands from theta
 void launch_features(const double* U, const double* eps, int nc, double dx, __nv_bfloat16* x, cudaStream_t s);
-// logits of n images of H x W cells (a1, a2: scratch activations)
+// logits of n images of H x W cells (a1, a2: scratch activations); err:
+// device error word (first int: code), set to 2 when a bounded wait for the
+// tensor cores expired
 void launch_forward(const Weights& w, const __nv_bfloat16* x, int n, int H, int W, __nv_bfloat16* a1,
-                    __nv_bfloat16* a2, float* logits, cudaStream_t s);
+                    __nv_bfloat16* a2, float* logits, int* err, cudaStream_t s);
 // judge of the learned switch: flags (the criterion's map q) becomes
 // q | (logit > 0); counters[0..3] += judged cells' (predicted, missed,
 // extra, cells) against the previous prediction pred (when have_prev);

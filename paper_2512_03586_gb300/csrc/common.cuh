@@ -57,10 +57,45 @@ struct DevErr {
   long long cell;
 };
 
-enum : int { kErrNone = 0, kErrNonRealizable = 1 };
+enum : int { kErrNone = 0, kErrNonRealizable = 1, kErrTimeout = 2 };
 
 ESBGK_DEV void report_error(DevErr* e, int code, long long cell) {
   if (e && atomicCAS(&e->code, 0, code) == 0) e->cell = cell;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier helpers (shared-memory barriers that asynchronous units arrive on).
+
+ESBGK_DEV unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+ESBGK_DEV void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Make initialised barriers visible to the asynchronous proxy.
+ESBGK_DEV void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+ESBGK_DEV bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete, giving up after a
+// bounded number of polls (false: it did not complete).
+constexpr unsigned kWaitLimit = 1u << 20;
+ESBGK_DEV bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // 32-bit integer hash (the "lowbias32" xorshift-multiply mixer published by
