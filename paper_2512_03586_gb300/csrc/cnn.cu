@@ -181,8 +181,13 @@ constexpr uint32_t kTcIdesc = (1u << 4)                // D format f32
                               | ((32u >> 3) << 17)      // N >> 3
                               | ((128u >> 4) << 24);    // M >> 4
 
+// Persistent: a CTA stages the weights and allocates its accumulator once,
+// then loops over row segments (segment t: image t / (H * segs), row and
+// segment within it).  Per segment: stage the halo, one thread issues the
+// MMAs and commits to the mbarrier (phase = the CTA's segment count & 1),
+// every warp reads its 32 cells back.
 __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ in, const bf* __restrict__ wk,
-                                                        const float* __restrict__ bias, int H, int W,
+                                                        const float* __restrict__ bias, int n, int H, int W,
                                                         bf* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sa = tsm;                 // A halo, 4 planes
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
   __shared__ float s_b[kHid];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int segs = (W + TC_M - 1) / TC_M;
-  const int img = blockIdx.y, y = blockIdx.x / segs, x0 = (blockIdx.x % segs) * TC_M;
+  const int total = n * H * segs;
 
   if (warp == 0) {  // 32 columns of tensor memory for the f32 accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
@@ -208,45 +213,50 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
     const int o = i / (kK2 / 8), kg = i % (kK2 / 8);
     *reinterpret_cast<uint4*>(sb + kg * 512 + o * 16) = *reinterpret_cast<const uint4*>(wk + (size_t)o * kK2 + kg * 8);
   }
-  // halo rows y-1..y+1, cells x0-1..x0+TC_M, zeros outside the image
-  for (int i = tid; i < 3 * TC_HW * 4; i += blockDim.x) {
-    const int pl = i % 4, cell = i / 4, r = cell / TC_HW, cx = cell % TC_HW;
-    const int gy = y + r - 1, gx = x0 + cx - 1;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-      v = *reinterpret_cast<const uint4*>(in + (((size_t)img * H + gy) * W + gx) * kHid + pl * 8);
-    *reinterpret_cast<uint4*>(sa + pl * TC_PLANE + (r * TC_HW + cx) * 16) = v;
-  }
-  // operands written by the threads are read by the tensor cores (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-
-  if (tid == 0) {
-    const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
-#pragma unroll 1
-    for (int j = 0; j < 18; ++j) {  // depth step j: tap j/2, input channels (j%2)*16 .. +15
-      const int tap = j >> 1, ky = tap / 3, kx = tap % 3, cg = (j & 1) * 2;
-      const uint64_t ad = smem_desc(a0 + cg * TC_PLANE + (ky * TC_HW + kx) * 16, TC_PLANE, 128);
-      const uint64_t bd = smem_desc(b0 + (tap * 4 + cg) * 512, 512, 128);
-      const uint32_t acc = j > 0 ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+  bool ok = true;
+  unsigned phase = 0;
+  for (int t = blockIdx.x; t < total && ok; t += gridDim.x, phase ^= 1u) {
+    const int img = t / (H * segs), r0 = t % (H * segs), y = r0 / segs, x0 = (r0 % segs) * TC_M;
+    // halo rows y-1..y+1, cells x0-1..x0+TC_M, zeros outside the image
+    for (int i = tid; i < 3 * TC_HW * 4; i += blockDim.x) {
+      const int pl = i % 4, cell = i / 4, r = cell / TC_HW, cx = cell % TC_HW;
+      const int gy = y + r - 1, gx = x0 + cx - 1;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+        v = *reinterpret_cast<const uint4*>(in + (((size_t)img * H + gy) * W + gx) * kHid + pl * 8);
+      *reinterpret_cast<uint4*>(sa + pl * TC_PLANE + (r * TC_HW + cx) * 16) = v;
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(&mbar))
-                 : "memory");
-  }
-  // bounded wait for the MMAs; every thread waits (acquire), the outcome is uniform
-  const bool done = __syncthreads_and(mbar_wait(&mbar, 0));
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
-    if (tid == 0 && err) atomicCAS(err, 0, kErrTimeout);
-  } else {
+    // operands written by the threads are read by the tensor cores (async
+    // proxy); the previous segment's accumulator reads are complete
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+#pragma unroll 1
+      for (int j = 0; j < 18; ++j) {  // depth step j: tap j/2, input channels (j%2)*16 .. +15
+        const int tap = j >> 1, ky = tap / 3, kx = tap % 3, cg = (j & 1) * 2;
+        const uint64_t ad = smem_desc(a0 + cg * TC_PLANE + (ky * TC_HW + kx) * 16, TC_PLANE, 128);
+        const uint64_t bd = smem_desc(b0 + (tap * 4 + cg) * 512, 512, 128);
+        const uint32_t acc = j > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar))
+                   : "memory");
+    }
+    // bounded wait for the MMAs; every thread waits (acquire), the outcome is uniform
+    ok = __syncthreads_and(mbar_wait(&mbar, phase));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+      if (tid == 0 && err) atomicCAS(err, 0, kErrTimeout);
+      break;
+    }
     // warp w reads tensor-memory lanes 32w..32w+31 (its cells), 32 columns (channels)
     uint32_t v[32];
     asm volatile(
@@ -271,13 +281,21 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_base));
 }
 
 void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int H, int W, bf* out, int* err,
                       cudaStream_t s) {
-  const int segs = (W + TC_M - 1) / TC_M;
-  conv32_tc_kernel<<<dim3(H * segs, n), 128, kTcSmem, s>>>(in, wk, bias, H, W, out, err);
+  static int nsm = 0;  // SMs of the device (queried once)
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int total = n * H * ((W + TC_M - 1) / TC_M);
+  const int cap = nsm * 5;  // resident CTAs at 43 KB of shared memory each
+  conv32_tc_kernel<<<total < cap ? total : cap, 128, kTcSmem, s>>>(in, wk, bias, n, H, W, out, err);
 }
 
 // Weight gradient of a 3 x 3 convolution, per CTA partial sums over the

@@ -180,6 +180,17 @@ def test_riemann_full_size_first_steps():
     assert st.kin.sum() > 0
 
 
+@pytest.mark.parametrize("prec,nv", [("fp64", 10), ("fp32", 20), ("fp32", 12)])
+def test_vector_groups_straddling_zero_velocity(prec, nv):
+    """Velocity grids whose node groups of the vector form would straddle
+    v_x = 0 (N_v/2 not a multiple of the group width: 2 nodes in FP64, 4 in
+    FP32): these take the node-by-node form, with the upwind neighbours
+    chosen per node."""
+    wl = W.gaussian_blob(nx=12, ny=10, nv=nv, vmax=6.0, u0=(0.4, -0.2), steps=3)
+    worst, *_ = run_parity(wl, 3, prec)
+    assert worst.max() <= TOL[prec], worst
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 
