@@ -211,6 +211,15 @@ ESBGK_DEV R warp_sum(R v) {
   return v;
 }
 
+// Sum over a group of L lanes (L = 32: the warp; L = 16: a half-warp, mask
+// holding that half's lanes).
+template <int L, typename R>
+ESBGK_DEV R group_sum(R v, unsigned mask) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, L);
+  return v;
+}
+
 // Block-wide sum of N per-thread values (kThreads threads).  Result lands in
 // out[0..N) (shared memory, float64) after the call; red is shared scratch of
 // kWarps*N doubles.  Warp sums run in the arithmetic type R, the cross-warp

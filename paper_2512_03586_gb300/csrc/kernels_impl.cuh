@@ -255,13 +255,14 @@ ESBGK_DEV R gauss_at(const CellPar<R>& P, R cx, R cy) {
 // sums w sum G xi^p eta^q over the nodes, then H a = t - r with
 // H_mn = w sum G psi_m psi_n, r_m = w sum G psi_m, psi = (1, x, y, x^2, xy, y^2).
 // After this G_hat = G (1 + a . psi) has w sum psi G_hat = t.
-template <typename R, int W = 1>
-ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
+// L lanes per cell (32, or 16 for a half-warp; mask: the group's lanes).
+template <typename R, int W = 1, int L = 32>
+ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0xffffffffu) {
   const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   R s[15];
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
-  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
 #pragma unroll 1
   for (; it.k < g.nvv; it.next())
 #pragma unroll
@@ -288,7 +289,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
     s[14] += Gyy * y * y;
   }
 #pragma unroll
-  for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * pick<R>(g.w, g.fw);
+  for (int n = 0; n < 15; ++n) s[n] = group_sum<L>(s[n], mask) * pick<R>(g.w, g.fw);
   // H a = t - r by Gaussian elimination spread over lanes 0..5 (lane m holds
   // row m and its right-hand side; H is symmetric positive definite, so no
   // pivoting), pivot rows broadcast by shuffles.
@@ -316,7 +317,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
   for (int p = 0; p < 6; ++p) {
     R piv[7];
 #pragma unroll
-    for (int n = 0; n < 7; ++n) piv[n] = __shfl_sync(0xffffffffu, h[n], p);
+    for (int n = 0; n < 7; ++n) piv[n] = __shfl_sync(mask, h[n], p, L);
     ok = ok && piv[p] > R(0);
     const R fct = row > p ? h[p] / piv[p] : R(0);
 #pragma unroll
@@ -328,7 +329,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P) {
     R acc = h[6];
 #pragma unroll
     for (int n = p + 1; n < 6; ++n) acc -= h[n] * P.a[n];
-    const R ap = __shfl_sync(0xffffffffu, acc / h[p], p);
+    const R ap = __shfl_sync(mask, acc / h[p], p, L);
     P.a[p] = ap;
   }
   return ok;
@@ -507,17 +508,19 @@ ESBGK_DEV R transport_of(const R (&q)[7], R vx, R vy, R idx, R idy, R epsw) {
 // ||f - M_hat[f]||_{L1_v} of the cell whose node values are in sf and whose raw
 // moment sums about u0 are m (Eq. eqKintoFluid1), one warp; -1 if the
 // moments are not realizable.
-template <typename R, int W>
-ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, const R* sf) {
+template <typename R, int W, int L = 32>
+ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, const R* sf,
+                         unsigned mask = 0xffffffffu) {
   CellPar<R> P;
-  if (!es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), R(0), R(0), false, P) || !project<R, W>(g, lane, P)) return R(-1);
+  if (!es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), R(0), R(0), false, P) || !project<R, W, L>(g, lane, P, mask))
+    return R(-1);
   const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   R s = R(0);
-  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
   for (; it.k < g.nvv; it.next())
 #pragma unroll
     for (int j = 0; j < W; ++j) s += rabs(sf[it.k + j] - ghat(P, it.vx() + R(j) * dv - P.ux, it.vy() - P.uy));
-  return warp_sum(s) * pick<R>(g.w, g.fw);
+  return group_sum<L>(s, mask) * pick<R>(g.w, g.fw);
 }
 
 // Flag values of each compile-time stage shape (StageMode).
@@ -721,8 +724,11 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
 // consecutive nodes of one velocity row per iteration (one 16-byte load per
 // stencil array instead of W), which needs N_v divisible by 2W (a group never
 // straddles v_x = 0 or a row end) and 16-byte aligned arrays.
-template <typename S, int M, int W>
-ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs) {
+// L lanes per cell: 32 (the warp) or 16 (a half-warp; mask: its lanes; lane:
+// the index within the half) -- two cells per warp for small velocity grids.
+template <typename S, int M, int W, int L = 32>
+ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs,
+                                unsigned mask = 0xffffffffu) {
   using R = typename Real<S>::T;
   using IO = VecIO<S, W>;
   using SM = SmemVec<R, W>;
@@ -758,7 +764,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   R m[6];
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = R(0);
-  NodeIter<R> it(lane * W, g.nv, v0, dv, 32 * W);
+  NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
 #pragma unroll 1
   for (; it.k < g.nvv; it.next()) {
     const unsigned k = it.k;
@@ -817,7 +823,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
   }
 #pragma unroll
-  for (int n = 0; n < 6; ++n) m[n] = warp_sum(m[n]);
+  for (int n = 0; n < 6; ++n) m[n] = group_sum<L>(m[n], mask);
   if (lane == 0) {  // U of the cell (float64), written by one lane
     double Uc[4];
     cons_from_sums(m, u0x, u0y, g.w, Uc);
@@ -827,8 +833,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   }
   if (!relax) {
     if (A.l1_out) {
-      __syncwarp();
-      const R l1 = l1_deviation<R, W>(g, lane, m, u0x, u0y, sfs);
+      __syncwarp(mask);
+      const R l1 = l1_deviation<R, W, L>(g, lane, m, u0x, u0y, sfs, mask);
       if (lane == 0) {
         if (l1 < R(0)) report_error(V.err, kErrNonRealizable, c);
         A.l1_out[c] = (double)l1;
@@ -841,12 +847,12 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   const R nu = pick<R>(V.m.tau, V.m.ftau) / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
   CellPar<R> P;
   bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), h, true, P);
-  if (ok) ok = project<R, W>(g, lane, P);
+  if (ok) ok = project<R, W, L>(g, lane, P, mask);
   if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, c);
 
   // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
   const R inv1h = R(1) / (R(1) + h);
-  NodeIter<R> jt(lane * W, g.nv, v0, dv, 32 * W);
+  NodeIter<R> jt(lane * W, g.nv, v0, dv, L * W);
 #pragma unroll 1
   for (; jt.k < g.nvv; jt.next()) {
     const unsigned k = jt.k;
@@ -933,16 +939,22 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 #ifndef ESBGK_STAGE_MIN_BLOCKS
 #define ESBGK_STAGE_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
 #endif
-template <typename S, int M, int W>
+// PAIR (vector form, small velocity grids): a kinetic unit is two cells, one
+// per half-warp, so that twice as many cells are in flight when a cell has
+// only a few node groups per lane.
+template <typename S, int M, int W, bool PAIR = false>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
-  R* sfs = reinterpret_cast<R*>(dsm) + (proj ? (size_t)warp * V.g.nvv : 0);
+  constexpr int kPer = PAIR ? 2 : 1;  // cells per kinetic unit
+  const int half = PAIR ? lane >> 4 : 0;
+  R* sfs = reinterpret_cast<R*>(dsm) + (proj ? (size_t)(warp * kPer + half) * V.g.nvv : 0);
   const int nK = V.counts[0], nB = V.counts[1], nF = V.counts[2];
+  const int nKu = (nK + kPer - 1) / kPer;
   const int nFc = (nF + 31) / 32;
-  const int total = nK + nB + nFc;
+  const int total = nKu + nB + nFc;
   long long mine = 0, fills = 0;
   // first wave round-robin; later units claimed from the launch's counter, so
   // a warp that drew a long unit (kinetic cell) does not also own a fixed
@@ -950,22 +962,31 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
   const int first = gridDim.x * nwarps;
   int u = blockIdx.x * nwarps + warp;
   while (u < total) {
-    if (u < nK) {
-      if constexpr (W > 1)
+    if (u < nKu) {
+      if constexpr (PAIR) {
+        const int ci = 2 * u + half;  // this half's cell
+        if (ci < nK) {
+          kinetic_cell_vec<S, M, W, 16>(A, V, V.klist[ci], lane & 15, sfs, half ? 0xffff0000u : 0x0000ffffu);
+          ++mine;
+        }
+      } else if constexpr (W > 1) {
         kinetic_cell_vec<S, M, W>(A, V, V.klist[u], lane, sfs);
-      else
+        ++mine;
+      } else {
         kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
-      ++mine;
+        ++mine;
+      }
+      __syncwarp();
     } else {
       // a buffer cell (Euler update on lane 0, then the fill) or a chunk of
       // 32 fluid cells (one per lane): one call site of the Euler update
-      const bool buf = u < nK + nB;
-      const int q = (u - nK - nB) * 32 + lane;
-      const int ec = buf ? (lane == 0 ? V.blist[u - nK] : -1) : (q < nF ? V.flist[q] : -1);
+      const bool buf = u < nKu + nB;
+      const int q = (u - nKu - nB) * 32 + lane;
+      const int ec = buf ? (lane == 0 ? V.blist[u - nKu] : -1) : (q < nF ? V.flist[q] : -1);
       double Uc[4] = {0, 0, 0, 0};
       if (ec >= 0) euler_cell<R>(A, V, ec, Uc);
       if (buf) {
-        buffer_fill<S, W>(A, V, V.blist[u - nK], lane, Uc);
+        buffer_fill<S, W>(A, V, V.blist[u - nKu], lane, Uc);
         fills += A.fill ? 1 : 0;
       }
     }
@@ -977,10 +998,9 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       u += first;
     }
   }
-  if (lane == 0 && A.ctr) {
-    if (mine && A.f_src) atomicAdd((unsigned long long*)A.ctr, (unsigned long long)mine);
-    if (fills) atomicAdd((unsigned long long*)A.ctr + 1, (unsigned long long)fills);
-  }
+  if ((lane & (32 / kPer - 1)) == 0 && A.ctr && mine && A.f_src)  // one lane per cell group
+    atomicAdd((unsigned long long*)A.ctr, (unsigned long long)mine);
+  if (lane == 0 && A.ctr && fills) atomicAdd((unsigned long long*)A.ctr + 1, (unsigned long long)fills);
 }
 
 // ---------------------------------------------------------------------------
@@ -1305,7 +1325,17 @@ struct Launch {
   using StageFn = void (*)(StageArgs, View);
   static constexpr int kW = VecW<S>::value;
   // vec: the vector form (specialised modes only)
-  static StageFn stage_fn(int m, bool vec = false) {
+  // pair: two cells per warp (vector form only)
+  static StageFn stage_fn(int m, bool vec = false, bool pair = false) {
+    if (vec && pair) {
+      switch (m) {
+        case kFirstRelax2: return stage_kernel<S, kFirstRelax2, kW, true>;
+        case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1, kW, true>;
+        case kFinal: return stage_kernel<S, kFinal, kW, true>;
+        case kFirstRelax0: return stage_kernel<S, kFirstRelax0, kW, true>;
+        default: break;
+      }
+    }
     switch (m) {
       case kFirstRelax2: return vec ? stage_kernel<S, kFirstRelax2, kW> : stage_kernel<S, kFirstRelax2, 1>;
       case kLoadedRelax1: return vec ? stage_kernel<S, kLoadedRelax1, kW> : stage_kernel<S, kLoadedRelax1, 1>;
@@ -1314,6 +1344,10 @@ struct Launch {
       default: return stage_kernel<S, kGeneric, 1>;
     }
   }
+  // Two cells per warp when a cell gives each of 32 lanes at most this many
+  // nodes (few node groups per lane: per-cell latency dominates).
+  static constexpr int kPairNodesPerLane = 16;
+  static bool pair_ok(const Geo& g) { return g.nvv <= 32 * kPairNodesPerLane; }
   static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
   // The vector form applies when groups of kW nodes stay on one side of
   // v_x = 0 and inside a row, and every f-sized array is 16-byte aligned.
@@ -1340,9 +1374,9 @@ struct Launch {
     cudaError_t e;
     const int mx = max_smem();
     for (int m = 0; m < kNumModes; ++m)
-      for (int v = 0; v < 2; ++v)
-        if ((e = cudaFuncSetAttribute(stage_fn(m, v != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
-            cudaSuccess)
+      for (int v = 0; v < 3; ++v)
+        if ((e = cudaFuncSetAttribute(stage_fn(m, v != 0, v == 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      mx)) != cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
@@ -1367,10 +1401,12 @@ struct Launch {
   }
   static void stage(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
     const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
-    const int threads = 32 * warps_for(V.g, 1);
-    const size_t smem = proj ? smem_for(V.g, 1) : 0;
     const int mode = stage_mode(A);
-    const StageFn fn = stage_fn(mode, vector_ok(A, V.g, mode));
+    const bool vec = vector_ok(A, V.g, mode), pair = vec && pair_ok(V.g);
+    const int arrays = pair ? 2 : 1;  // f* arrays per warp
+    const int threads = 32 * warps_for(V.g, arrays);
+    const size_t smem = proj ? smem_for(V.g, arrays) : 0;
+    const StageFn fn = stage_fn(mode, vec, pair);
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {
