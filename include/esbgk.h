@@ -170,6 +170,14 @@ int esbgk_step(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
  * kept so far.  Synchronises the stream. */
 int esbgk_graphs(esbgk_ctx* ctx, int32_t enable);
 
+/* Per-cell form the specialised stage launches of this context take (the
+ * ARS(2,3,3) and IMEX-Euler stages): nodes per vector group along v_x (1:
+ * one node per lane and iteration; 2 or 4: one vector load of that many
+ * consecutive nodes, N_v divisible by it) and kinetic cells per warp (2 in
+ * the vector form for velocity grids of at most 512 nodes, one cell per
+ * half-warp; else 1).  Host only, no launch; any pointer may be NULL. */
+int esbgk_kinetic_form(const esbgk_ctx* ctx, int32_t* nodes_per_group, int32_t* cells_per_warp);
+
 /* Macroscopic fields of every cell (moments of f in kinetic cells, the Euler
  * solution elsewhere), each [N_c] float64; any pointer may be NULL. */
 int esbgk_get_moments(esbgk_ctx* ctx, double* rho, double* ux, double* uy, double* T);

@@ -221,6 +221,13 @@ class Solver:
         """Enable or disable CUDA-graph replay of repeated steps."""
         self._check(self._abi.esbgk_graphs(self._ctx, int(bool(enable))), "graphs")
 
+    def kinetic_form(self):
+        """(nodes per vector group, kinetic cells per warp) of the specialised
+        stage launches: the per-cell form chosen for this velocity grid."""
+        w, p = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._abi.esbgk_kinetic_form(self._ctx, ctypes.byref(w), ctypes.byref(p)), "kinetic form")
+        return w.value, p.value
+
     def timing(self, enable=True):
         """Bracket every library kernel with CUDA events on the stream."""
         self._check(self._abi.esbgk_timing(self._ctx, int(bool(enable))), "timing")

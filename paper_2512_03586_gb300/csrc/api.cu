@@ -1000,6 +1000,22 @@ int esbgk_graphs(esbgk_ctx* X, int32_t enable) {
   return ESBGK_OK;
 }
 
+int esbgk_kinetic_form(const esbgk_ctx* X, int32_t* nodes_per_group, int32_t* cells_per_warp) {
+  GUARD(X);
+  // a first stage without accumulators over the context's own f arrays
+  StageArgs A;
+  memset(&A, 0, sizeof A);
+  A.f_src = X->F[0];
+  A.star_base = X->F[0];
+  A.f_out = X->F[1];
+  A.h_coef = 1.0;
+  const int v = X->L->variant(A, X->g);
+  const int w = v == kVarScalar ? 1 : (v == kVarNarrowSx || v == kVarNarrowSxPair ? 2 : X->L->wide_nodes);
+  if (nodes_per_group) *nodes_per_group = w;
+  if (cells_per_warp) *cells_per_warp = variant_pairs(v) ? 2 : 1;
+  return ESBGK_OK;
+}
+
 int esbgk_timing(esbgk_ctx* X, int enable) {
   GUARD(X);
   X->timing = enable != 0;
@@ -1092,6 +1108,7 @@ struct BatchTabSet {
   std::vector<CaseStage> h_stage;
   std::vector<CasePrep> h_prep;
   bool valid = false, any_plain = false;
+  bool has_var[kNumVariants] = {false};  // variants with at least one case
   int nlaunch = 0;
   int modes[kMaxStages + 1] = {0};
   bool fin[kMaxStages + 1] = {false};
@@ -1107,7 +1124,8 @@ struct esbgk_batch {
   int n = 0, prec = 0;
   const Launchers* L = nullptr;
   cudaStream_t stream = nullptr;
-  int nsm = 0, total_cells = 0, max_nvv = 0, max_threads = 128;
+  int nsm = 0, total_cells = 0, max_threads = 128;
+  int max_nvv = 0;  // shared f nodes per warp of the batched kernels
   std::vector<esbgk_ctx*> cs;
   BatchTabSet sets[kTabSets];
   int* d_cell_off = nullptr;
@@ -1175,7 +1193,7 @@ bool batch_layout(int n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes, co
     B.prep[t] = take(n * sizeof(CasePrep));
   }
   B.cell_off = take((n + 1) * sizeof(int));
-  B.off_stage = take((n + 1) * sizeof(int));
+  B.off_stage = take((size_t)kNumVariants * (n + 1) * sizeof(int));
   B.off_prep = take((n + 1) * sizeof(int));
   B.off_l1 = take((n + 1) * sizeof(int));
   B.l1_fresh = take(n * sizeof(int));
@@ -1217,8 +1235,8 @@ CaseRegime regime_of(esbgk_batch* b, int i) {
 }
 
 // CTAs of a batched stage launch.
-int batch_stage_grid(esbgk_batch* b, int mode) {
-  const int occ = b->L->batch_stage_occupancy(mode, b->max_nvv, b->threads);
+int batch_stage_grid(esbgk_batch* b, int mode, int var) {
+  const int occ = b->L->batch_stage_occupancy(mode, var, b->max_nvv, b->threads);
   const int per_sm = b->ctas > 0 && b->ctas < occ ? b->ctas : occ;
   return b->nsm * per_sm;
 }
@@ -1250,10 +1268,14 @@ void batch_launches(esbgk_batch* b, const BatchTabSet& t, const int* grids) {
     if (b->prec == ESBGK_BF16) launch_batch_seed_advance(t.prep, b->n, b->stream);
     b->L->batch_prep(t.prep, b->d_off_prep, b->n, grid_small, b->stream);
   }
+  // one launch per stage and variant present (a variant's kernel sees the
+  // other variants' cases as empty)
   for (int j = 0; j < t.nlaunch; ++j) {
     Timed tm(X0, t.fin[j] ? ESBGK_K_FINAL : ESBGK_K_STAGE);
-    b->L->batch_stage(t.stage + (size_t)j * b->n, b->d_off_stage, b->n, t.modes[j], b->max_nvv, b->threads, grids[j],
-                      b->stream);
+    for (int v = 0; v < kNumVariants; ++v)
+      if (t.has_var[v])
+        b->L->batch_stage(t.stage + (size_t)j * b->n, b->d_off_stage + v * (b->n + 1), b->n, t.modes[j], v,
+                          b->max_nvv, b->threads, grids[j * kNumVariants + v], b->stream);
   }
 }
 
@@ -1280,14 +1302,20 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
   for (int i = 0; i < n; ++i) {
     esbgk_ctx* X = b->cs[i];
     const View V = X->view();
+    // the unit numbering is shared by the step's launches: a case keeps one
+    // variant for all of them (the scalar form unless every launch agrees)
+    int var = -1;
     for (int j = 0; j < nl; ++j) {
       CaseStage& c = st[(size_t)j * n + i];
       memset(&c, 0, sizeof c);
       c.V = V;
       c.A = plans[i].st[j];
-      c.vec = b->L->vector_ok(c.A, X->g) ? 1 : 0;
+      const int v = b->L->variant(c.A, X->g);
+      var = var < 0 || var == v ? v : kVarScalar;
       if (stage_mode(c.A) != modes[j]) return bfail(b, ESBGK_E_STATE, "batched cases disagree on a launch shape");
     }
+    if (var < 0) var = kVarScalar;
+    for (int j = 0; j < nl; ++j) st[(size_t)j * n + i].variant = var;
     memset(&pr[i], 0, sizeof(CasePrep));
     pr[i].V = V;
     pr[i].P = plans[i].prep;
@@ -1295,6 +1323,7 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
     rg[i].l1_next = (!plans[i].shortcut && rg[i].plain) ? 1 : 0;
     rg[i].prep_copy = plans[i].prep.copy_to != nullptr;
     rg[i].conv = plans[i].prep.list2 != nullptr;
+    rg[i].variant = st[i].variant;
   }
   // find the table set with these descriptors, else overwrite the least recently used
   BatchTabSet* t = nullptr;
@@ -1331,11 +1360,15 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
       t->modes[j] = modes[j];
       t->fin[j] = plans[0].fin[j];
     }
+    for (int v = 0; v < kNumVariants; ++v) t->has_var[v] = false;
+    for (int i = 0; i < n; ++i) t->has_var[rg[i].variant] = true;
     t->valid = true;
   }
   t->used = b->steps + 1;
-  int grids[kMaxStages + 1];
-  for (int j = 0; j < nl; ++j) grids[j] = batch_stage_grid(b, t->modes[j]);
+  int grids[(kMaxStages + 1) * kNumVariants] = {0};
+  for (int j = 0; j < nl; ++j)
+    for (int v = 0; v < kNumVariants; ++v)
+      if (t->has_var[v]) grids[j * kNumVariants + v] = batch_stage_grid(b, t->modes[j], v);
   if (use_graph && b->stream && !b->timing) {
     if (!t->gexec) {
       cudaGraph_t g = nullptr;
@@ -1397,7 +1430,9 @@ int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vm
     }
     b->cs.push_back(X);
     cell_off[i + 1] = cell_off[i] + X->g.nc;
-    if (X->g.nvv > b->max_nvv) b->max_nvv = X->g.nvv;
+    // shared f nodes per warp: two cells' worth where pairs may run
+    const int per_warp = X->g.nvv <= kPairMaxNodes ? 2 * X->g.nvv : X->g.nvv;
+    if (per_warp > b->max_nvv) b->max_nvv = per_warp;
   }
   b->total_cells = cell_off[n];
   for (int t = 0; t < kTabSets; ++t) {

@@ -426,22 +426,22 @@ __global__ void __launch_bounds__(kScanThreads) batch_compact_kernel(BatchTabs T
 
 void launch_batch_compact(const BatchTabs& T, cudaStream_t s) { batch_compact_kernel<<<T.n, kScanThreads, 0, s>>>(T); }
 
-// Stage units (kinetic cells, buffer cells, chunks of 32 fluid cells) and
-// start-of-step units per case; marks L1 fresh where this step's final
-// combination computes it.
+// Stage units (kinetic cells or pairs of them, buffer cells, chunks of 32
+// fluid cells) and start-of-step units per case; marks L1 fresh where this
+// step's final combination computes it.
 __global__ void batch_offsets_kernel(BatchTabs T) {
   if (threadIdx.x != 0) return;
-  int as = 0, ap = 0;
+  int as[kNumVariants] = {}, ap = 0;
   for (int c = 0; c < T.n; ++c) {
     const CaseRegime& R = T.reg[c];
     const int* k = R.counts;
-    T.off_stage[c] = as;
+    for (int v = 0; v < kNumVariants; ++v) T.off_stage[v * (T.n + 1) + c] = as[v];
     T.off_prep[c] = ap;
-    as += k[0] + k[1] + (k[2] + 31) / 32;
+    as[R.variant] += (variant_pairs(R.variant) ? (k[0] + 1) / 2 : k[0]) + k[1] + (k[2] + 31) / 32;
     ap += k[1] + (R.conv ? k[3] : 0) + (R.prep_copy ? (R.V.g.nc + 31) / 32 : 0);
     *R.l1_fresh = R.l1_next;
   }
-  T.off_stage[T.n] = as;
+  for (int v = 0; v < kNumVariants; ++v) T.off_stage[v * (T.n + 1) + T.n] = as[v];
   T.off_prep[T.n] = ap;
 }
 

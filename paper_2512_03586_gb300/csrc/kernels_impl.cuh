@@ -141,6 +141,25 @@ struct VecIO<__nv_bfloat16, 4> {
     *reinterpret_cast<uint2*>(p) = t;
   }
 };
+template <>
+struct VecIO<__nv_bfloat16, 2> {
+  static ESBGK_DEV void unpack(unsigned t, float (&v)[2]) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t));
+    v[0] = a.x, v[1] = a.y;
+  }
+  static ESBGK_DEV void ld(const __nv_bfloat16* p, float (&v)[2]) {
+    unpack(__ldg(reinterpret_cast<const unsigned*>(p)), v);
+  }
+  static ESBGK_DEV void ldc(const __nv_bfloat16* p, float (&v)[2]) { unpack(*reinterpret_cast<const unsigned*>(p), v); }
+  static ESBGK_DEV void st(__nv_bfloat16* p, const float (&v)[2]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    *reinterpret_cast<unsigned*>(p) = *reinterpret_cast<const unsigned*>(&a);
+  }
+  static ESBGK_DEV void st_sr(__nv_bfloat16* p, const float (&v)[2], uint32_t key) {
+    const uint32_t r = mix32(key);
+    *reinterpret_cast<unsigned*>(p) = (uint32_t)bf16_sr_bits(v[0], r) | ((uint32_t)bf16_sr_bits(v[1], r >> 16) << 16);
+  }
+};
 // shared-memory copies of f* in the arithmetic type
 template <typename R, int W>
 struct SmemVec;
@@ -721,12 +740,14 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
 }
 
 // Vector form of kinetic_cell for a specialised launch mode: each lane takes W
-// consecutive nodes of one velocity row per iteration (one 16-byte load per
-// stencil array instead of W), which needs N_v divisible by 2W (a group never
-// straddles v_x = 0 or a row end) and 16-byte aligned arrays.
+// consecutive nodes of one velocity row per iteration (one vector load per
+// stencil array instead of W), which needs N_v divisible by W (a group never
+// straddles a row end) and 16-byte aligned arrays.  SX (N_v/2 not a multiple
+// of W): the group holding v_x = 0 has nodes moving either way; it loads the
+// fourth x-neighbour too and takes each node's upwind stencil.
 // L lanes per cell: 32 (the warp) or 16 (a half-warp; mask: its lanes; lane:
 // the index within the half) -- two cells per warp for small velocity grids.
-template <typename S, int M, int W, int L = 32>
+template <typename S, int M, int W, int L = 32, bool SX = false>
 ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs,
                                 unsigned mask = 0xffffffffu) {
   using R = typename Real<S>::T;
@@ -760,6 +781,9 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   // random key of this launch for the stochastic rounding of bf16 stores
   const uint32_t s0 = A.seed ? mix32(*A.seed * 0x632be5abu + A.sid) : 0u;
 
+  // column of the group that straddles v_x = 0 (none: -1)
+  const int half_nv = g.nv >> 1, kz = SX ? half_nv - half_nv % W : -1;
+
   // pass 1: transport of the previous stage, f*, moments of f*
   R m[6];
 #pragma unroll
@@ -775,6 +799,20 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     IO::ld(fsrc + (px ? o[1] : o[2]) + k, ux);
     IO::ld(fsrc + (px ? o[2] : o[1]) + k, dx);
     IO::ld(fsrc + (px ? o[0] : o[3]) + k, fx);
+    if (SX && it.kx == kz) {
+      // first node v_x < 0 (loaded above), the last ones v_x > 0: upwind is
+      // the left neighbour, downwind the right one, far side two to the left
+      R l2[W];
+      IO::ld(fsrc + o[0] + k, l2);
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (vx0 + R(j) * dv > R(0)) {
+          const R t = ux[j];
+          ux[j] = dx[j];
+          dx[j] = t;
+          fx[j] = l2[j];
+        }
+    }
     IO::ld(fsrc + (py ? o[5] : o[6]) + k, uy);
     IO::ld(fsrc + (py ? o[6] : o[5]) + k, dy);
     IO::ld(fsrc + (py ? o[4] : o[7]) + k, fy);
@@ -942,7 +980,7 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 // PAIR (vector form, small velocity grids): a kinetic unit is two cells, one
 // per half-warp, so that twice as many cells are in flight when a cell has
 // only a few node groups per lane.
-template <typename S, int M, int W, bool PAIR = false>
+template <typename S, int M, int W, bool PAIR = false, bool SX = false>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -966,11 +1004,11 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       if constexpr (PAIR) {
         const int ci = 2 * u + half;  // this half's cell
         if (ci < nK) {
-          kinetic_cell_vec<S, M, W, 16>(A, V, V.klist[ci], lane & 15, sfs, half ? 0xffff0000u : 0x0000ffffu);
+          kinetic_cell_vec<S, M, W, 16, SX>(A, V, V.klist[ci], lane & 15, sfs, half ? 0xffff0000u : 0x0000ffffu);
           ++mine;
         }
       } else if constexpr (W > 1) {
-        kinetic_cell_vec<S, M, W>(A, V, V.klist[u], lane, sfs);
+        kinetic_cell_vec<S, M, W, 32, SX>(A, V, V.klist[u], lane, sfs);
         ++mine;
       } else {
         kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
@@ -1170,14 +1208,17 @@ static_assert(kCellWarps * sizeof(CaseStage) <= kBatchStaticSmem && sizeof(CaseS
 static_assert(kCellWarps * sizeof(CaseRegime) <= kBatchStaticSmem && sizeof(CaseRegime) % 4 == 0, "descriptor copies");
 static_assert(kCellWarps * sizeof(CasePrep) <= kBatchStaticSmem && sizeof(CasePrep) % 4 == 0, "descriptor copies");
 
-template <typename S, int M>
+// One variant of the per-cell code (W, PAIR, SX as in stage_kernel); `off` is the
+// unit prefix of this variant, in which cases of other variants are empty.
+template <typename S, int M, int W, bool PAIR, bool SX>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
     batch_stage_kernel(const CaseStage* __restrict__ cases, const int* __restrict__ off, int n, int max_nvv) {
   using R = typename Real<S>::T;
-  constexpr int kW = VecW<S>::value;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) CaseStage cs[kCellWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  constexpr int kPer = PAIR ? 2 : 1;  // cells per kinetic unit
+  const int half = PAIR ? lane >> 4 : 0;
   R* sfs = reinterpret_cast<R*>(dsm) + (size_t)warp * max_nvv;
   const int total = off[n];
   for (int u = blockIdx.x * nwarps + warp; u < total; u += gridDim.x * nwarps) {
@@ -1188,22 +1229,29 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
     const StageArgs& A = cs[warp].A;
     const int local = u - off[c];
     const int nK = V.counts[0], nB = V.counts[1], nF = V.counts[2];
-    if (local < nK) {
-      if (M != kGeneric && cs[warp].vec) {
-        if constexpr (M != kGeneric) kinetic_cell_vec<S, M, kW>(A, V, V.klist[local], lane, sfs);
+    const int nKu = (nK + kPer - 1) / kPer;
+    if (local < nKu) {
+      if constexpr (PAIR) {
+        // two cells, one per half-warp, each with its own f* array
+        const int ci = 2 * local + half;
+        if (ci < nK) {
+          kinetic_cell_vec<S, M, W, 16, SX>(A, V, V.klist[ci], lane & 15, sfs + half * V.g.nvv,
+                                            half ? 0xffff0000u : 0x0000ffffu);
+          if ((lane & 15) == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
+        }
+        __syncwarp();
       } else {
-        kinetic_cell<S, M>(A, V, V.klist[local], lane, sfs);
+        if constexpr (W > 1)
+          kinetic_cell_vec<S, M, W, 32, SX>(A, V, V.klist[local], lane, sfs);
+        else
+          kinetic_cell<S, M>(A, V, V.klist[local], lane, sfs);
+        if (lane == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
       }
-      if (lane == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
-    } else if (local < nK + nB) {
-      if (M != kGeneric && cs[warp].vec) {
-        if constexpr (M != kGeneric) buffer_cell<S, kW>(A, V, V.blist[local - nK], lane);
-      } else {
-        buffer_cell<S>(A, V, V.blist[local - nK], lane);
-      }
+    } else if (local < nKu + nB) {
+      buffer_cell<S, W>(A, V, V.blist[local - nKu], lane);
       if (lane == 0 && A.ctr && A.fill) atomicAdd((unsigned long long*)A.ctr + 1, 1ull);
     } else {
-      const int q = (local - nK - nB) * 32 + lane;
+      const int q = (local - nKu - nB) * 32 + lane;
       if (q < nF) {
         double Uc[4];
         euler_cell<R>(A, V, V.flist[q], Uc);
@@ -1324,49 +1372,67 @@ struct Launch {
 
   using StageFn = void (*)(StageArgs, View);
   static constexpr int kW = VecW<S>::value;
-  // vec: the vector form (specialised modes only)
-  // pair: two cells per warp (vector form only)
-  static StageFn stage_fn(int m, bool vec = false, bool pair = false) {
-    if (vec && pair) {
-      switch (m) {
-        case kFirstRelax2: return stage_kernel<S, kFirstRelax2, kW, true>;
-        case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1, kW, true>;
-        case kFinal: return stage_kernel<S, kFinal, kW, true>;
-        case kFirstRelax0: return stage_kernel<S, kFirstRelax0, kW, true>;
-        default: break;
-      }
+  // node groups of the variants: kW, or 2 (fewer nodes per group than kW
+  // when N_v is not a multiple of kW)
+  static constexpr int narrow_w() { return kW > 2 ? 2 : kW; }
+  template <int M>
+  static StageFn stage_variant(int var) {
+    switch (var) {
+      case kVarWide: return stage_kernel<S, M, kW>;
+      case kVarWidePair: return stage_kernel<S, M, kW, true>;
+      case kVarWideSx: return stage_kernel<S, M, kW, false, true>;
+      case kVarWideSxPair: return stage_kernel<S, M, kW, true, true>;
+      case kVarNarrowSx: return stage_kernel<S, M, narrow_w(), false, true>;
+      case kVarNarrowSxPair: return stage_kernel<S, M, narrow_w(), true, true>;
+      default: return stage_kernel<S, M, 1>;
     }
+  }
+  static StageFn stage_fn(int m, int var = kVarScalar) {
     switch (m) {
-      case kFirstRelax2: return vec ? stage_kernel<S, kFirstRelax2, kW> : stage_kernel<S, kFirstRelax2, 1>;
-      case kLoadedRelax1: return vec ? stage_kernel<S, kLoadedRelax1, kW> : stage_kernel<S, kLoadedRelax1, 1>;
-      case kFinal: return vec ? stage_kernel<S, kFinal, kW> : stage_kernel<S, kFinal, 1>;
-      case kFirstRelax0: return vec ? stage_kernel<S, kFirstRelax0, kW> : stage_kernel<S, kFirstRelax0, 1>;
+      case kFirstRelax2: return stage_variant<kFirstRelax2>(var);
+      case kLoadedRelax1: return stage_variant<kLoadedRelax1>(var);
+      case kFinal: return stage_variant<kFinal>(var);
+      case kFirstRelax0: return stage_variant<kFirstRelax0>(var);
       default: return stage_kernel<S, kGeneric, 1>;
     }
   }
-  // Two cells per warp when a cell gives each of 32 lanes at most this many
-  // nodes (few node groups per lane: per-cell latency dominates).
-  static constexpr int kPairNodesPerLane = 16;
-  static bool pair_ok(const Geo& g) { return g.nvv <= 32 * kPairNodesPerLane; }
   static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-  // The vector form applies when groups of kW nodes stay on one side of
-  // v_x = 0 and inside a row, and every f-sized array is 16-byte aligned.
-  static bool vector_ok(const StageArgs& A, const Geo& g, int mode) {
-    if (mode == kGeneric || g.nv % (2 * kW) != 0) return false;
-    if (!aligned16(A.f_src) || !aligned16(A.star_base) || !aligned16(A.f_out)) return false;
+  // Per-cell code of a stage launch: the vector form (specialised modes,
+  // every f-sized array 16-byte aligned, N_v divisible by the group size)
+  // with groups of kW nodes, else of 2, else the scalar form; two cells per
+  // warp when a cell has at most kPairMaxNodes nodes (few node groups per
+  // lane: per-cell latency dominates).
+  static int variant(const StageArgs& A, const Geo& g, int mode) {
+    if (mode == kGeneric) return kVarScalar;
+    if (!aligned16(A.f_src) || !aligned16(A.star_base) || !aligned16(A.f_out)) return kVarScalar;
     for (int t = 0; t < A.nacc; ++t)
-      if (!aligned16(A.acc_in[t]) || !aligned16(A.acc_out[t])) return false;
-    return true;
+      if (!aligned16(A.acc_in[t]) || !aligned16(A.acc_out[t])) return kVarScalar;
+    const int pair = g.nvv <= kPairMaxNodes ? 1 : 0;
+    if (g.nv % (2 * kW) == 0) return kVarWide + pair;
+    if (kW > 2 && g.nv % kW == 0) return kVarWideSx + pair;
+    if (g.nv % 2 == 0) return kVarNarrowSx + pair;  // N_v/2 odd when kW = 2
+    return kVarScalar;
   }
-
   using BatchFn = void (*)(const CaseStage*, const int*, int, int);
-  static BatchFn batch_fn(int m) {
+  template <int M>
+  static BatchFn batch_variant(int var) {
+    switch (var) {
+      case kVarWide: return batch_stage_kernel<S, M, kW, false, false>;
+      case kVarWidePair: return batch_stage_kernel<S, M, kW, true, false>;
+      case kVarWideSx: return batch_stage_kernel<S, M, kW, false, true>;
+      case kVarWideSxPair: return batch_stage_kernel<S, M, kW, true, true>;
+      case kVarNarrowSx: return batch_stage_kernel<S, M, narrow_w(), false, true>;
+      case kVarNarrowSxPair: return batch_stage_kernel<S, M, narrow_w(), true, true>;
+      default: return batch_stage_kernel<S, M, 1, false, false>;
+    }
+  }
+  static BatchFn batch_fn(int m, int var) {
     switch (m) {
-      case kFirstRelax2: return batch_stage_kernel<S, kFirstRelax2>;
-      case kLoadedRelax1: return batch_stage_kernel<S, kLoadedRelax1>;
-      case kFinal: return batch_stage_kernel<S, kFinal>;
-      case kFirstRelax0: return batch_stage_kernel<S, kFirstRelax0>;
-      default: return batch_stage_kernel<S, kGeneric>;
+      case kFirstRelax2: return batch_variant<kFirstRelax2>(var);
+      case kLoadedRelax1: return batch_variant<kLoadedRelax1>(var);
+      case kFinal: return batch_variant<kFinal>(var);
+      case kFirstRelax0: return batch_variant<kFirstRelax0>(var);
+      default: return batch_stage_kernel<S, kGeneric, 1, false, false>;
     }
   }
   static cudaError_t setup(const Geo& g) {
@@ -1374,17 +1440,19 @@ struct Launch {
     cudaError_t e;
     const int mx = max_smem();
     for (int m = 0; m < kNumModes; ++m)
-      for (int v = 0; v < 3; ++v)
-        if ((e = cudaFuncSetAttribute(stage_fn(m, v != 0, v == 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      mx)) != cudaSuccess)
+      for (int v = 0; v < kNumVariants; ++v)
+        if ((e = cudaFuncSetAttribute(stage_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+            cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
     // batched kernels: set here so that their launches can be graph-captured
     const int mb = mx - kBatchStaticSmem;
     for (int m = 0; m < kNumModes; ++m)
-      if ((e = cudaFuncSetAttribute(batch_fn(m), cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
-        return e;
+      for (int v = 0; v < kNumVariants; ++v)
+        if ((e = cudaFuncSetAttribute(batch_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) !=
+            cudaSuccess)
+          return e;
     if ((e = cudaFuncSetAttribute(batch_l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
       return e;
     return cudaFuncSetAttribute(relax_cells_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1401,12 +1469,11 @@ struct Launch {
   }
   static void stage(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
     const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
-    const int mode = stage_mode(A);
-    const bool vec = vector_ok(A, V.g, mode), pair = vec && pair_ok(V.g);
-    const int arrays = pair ? 2 : 1;  // f* arrays per warp
+    const int mode = stage_mode(A), var = variant(A, V.g, mode);
+    const int arrays = variant_pairs(var) ? 2 : 1;  // f* arrays per warp
     const int threads = 32 * warps_for(V.g, arrays);
     const size_t smem = proj ? smem_for(V.g, arrays) : 0;
-    const StageFn fn = stage_fn(mode, vec, pair);
+    const StageFn fn = stage_fn(mode, var);
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {
@@ -1423,12 +1490,12 @@ struct Launch {
     relax_cells_kernel<S><<<grid, threads, smem_for(g, 1), s>>>((const S*)fs, h, n, g, beta, (S*)fo, (S*)go);
   }
   static size_t batch_smem(int max_nvv, int threads) { return (size_t)(threads / 32) * max_nvv * sizeof(R); }
-  static int batch_stage_occupancy(int mode, int max_nvv, int threads) {
-    return occ((const void*)batch_fn(mode), threads, batch_smem(max_nvv, threads));
+  static int batch_stage_occupancy(int mode, int var, int max_nvv, int threads) {
+    return occ((const void*)batch_fn(mode, var), threads, batch_smem(max_nvv, threads));
   }
-  static void batch_stage(const CaseStage* cases, const int* off, int n, int mode, int max_nvv, int threads, int grid,
-                          cudaStream_t s) {
-    const BatchFn fn = batch_fn(mode);
+  static void batch_stage(const CaseStage* cases, const int* off, int n, int mode, int var, int max_nvv, int threads,
+                          int grid, cudaStream_t s) {
+    const BatchFn fn = batch_fn(mode, var);
     fn<<<grid, threads, batch_smem(max_nvv, threads), s>>>(cases, off, n, max_nvv);
   }
   static void batch_prep(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t s) {
@@ -1437,7 +1504,7 @@ struct Launch {
   static void batch_l1(const CaseRegime* cases, const int* off, int n, int max_nvv, int grid, cudaStream_t s) {
     batch_l1_kernel<S><<<grid, kCellThreads, kCellWarps * (size_t)max_nvv * sizeof(R), s>>>(cases, off, n, max_nvv);
   }
-  static bool vector_ok_public(const StageArgs& A, const Geo& g) { return vector_ok(A, g, stage_mode(A)); }
+  static int variant_public(const StageArgs& A, const Geo& g) { return variant(A, g, stage_mode(A)); }
   static void moments(const void* f, double* U, const View& V, int grid, cudaStream_t s) {
     moments_kernel<S><<<rescale(V.g, grid, (const void*)moments_kernel<S>, kCellThreads, 0), kCellThreads, 0, s>>>(
         f, U, V);
@@ -1449,6 +1516,6 @@ struct Launch {
                           &Launch<S>::stage,                  &Launch<S>::prep,         &Launch<S>::l1,            \
                           &Launch<S>::relax_cells,            &Launch<S>::moments,      &Launch<S>::batch_stage,   \
                           &Launch<S>::batch_prep,             &Launch<S>::batch_l1,                               \
-                          &Launch<S>::batch_stage_occupancy, &Launch<S>::vector_ok_public};
+                          &Launch<S>::batch_stage_occupancy, &Launch<S>::variant_public, VecW<S>::value};
 
 }  // namespace esbgk

@@ -96,6 +96,25 @@ enum StageMode : int {
   kNumModes = 5
 };
 
+// Per-cell code of a kinetic stage launch: the scalar form, or the vector
+// form with groups of the widest vector (16 bytes of f, at most 4 nodes) or
+// of 2 nodes, with one cell per warp or two (one per half-warp).  "Sx": one
+// group of each velocity row straddles v_x = 0 (N_v/2 not a multiple of the
+// group width); the other forms are compiled without that case.
+enum StageVariant : int {
+  kVarScalar = 0,
+  kVarWide = 1,
+  kVarWidePair = 2,
+  kVarWideSx = 3,
+  kVarWideSxPair = 4,
+  kVarNarrowSx = 5,
+  kVarNarrowSxPair = 6,
+  kNumVariants = 7
+};
+__host__ __device__ inline bool variant_pairs(int v) {
+  return v == kVarWidePair || v == kVarWideSxPair || v == kVarNarrowSxPair;
+}
+
 // Host-side choice of the specialisation for a launch.
 inline int stage_mode(const StageArgs& A) {
   const bool relax = A.h_coef > 0.0;
@@ -116,12 +135,15 @@ inline int stage_mode(const StageArgs& A) {
 // Shared memory the batched kernels reserve for their per-warp descriptor
 // copies; the dynamic f-sized arrays get the rest of the opt-in limit.
 constexpr int kBatchStaticSmem = 8 * 1024;
+// Vector-form stage kernels run two kinetic cells per warp (16 lanes each)
+// when the velocity grid has at most this many nodes.
+constexpr int kPairMaxNodes = 512;
 
 // One case of a batched stage launch (vec: the vector node-group form applies).
 struct CaseStage {
   View V;
   StageArgs A;
-  int vec;
+  int variant;  // StageVariant of the case (the same for every launch of the step)
   int pad;
 };
 
@@ -151,13 +173,15 @@ struct CaseRegime {
   int l1_next;            // the final combination of this step computes L1
   int prep_copy;          // the start-of-step launch copies U^n and flags (units of 32 cells)
   int conv;               // the start-of-step launch fills converted cells
+  int variant;            // StageVariant of the case's stage launches
+  int pad;
 };
 
 // Device tables of a batch.
 struct BatchTabs {
   const CaseRegime* reg;  // [n]
   const int* cell_off;    // [n+1] prefix of cells
-  int* off_stage;         // [n+1] prefix of stage units
+  int* off_stage;         // [kNumVariants][n+1] prefix of stage units (cases of other variants: none)
   int* off_prep;          // [n+1] prefix of start-of-step units
   int* off_l1;            // [n+1] prefix of L1 units
   int n;
@@ -176,12 +200,13 @@ struct Launchers {
                       int grid, cudaStream_t);
   void (*moments)(const void* f, double* U, const View&, int grid, cudaStream_t);
   // batched form; threads per CTA (multiple of 32, <= 128) and grid chosen by the caller
-  void (*batch_stage)(const CaseStage* cases, const int* off, int n, int mode, int max_nvv, int threads, int grid,
-                      cudaStream_t);
+  void (*batch_stage)(const CaseStage* cases, const int* off, int n, int mode, int var, int max_nvv, int threads,
+                      int grid, cudaStream_t);
   void (*batch_prep)(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t);
   void (*batch_l1)(const CaseRegime* cases, const int* off, int n, int max_nvv, int grid, cudaStream_t);
-  int (*batch_stage_occupancy)(int mode, int max_nvv, int threads);
-  bool (*vector_ok)(const StageArgs& A, const Geo& g);
+  int (*batch_stage_occupancy)(int mode, int var, int max_nvv, int threads);
+  int (*variant)(const StageArgs& A, const Geo& g);
+  int wide_nodes;  // nodes per group of the kVarWide variants
 };
 
 extern const Launchers kLaunchF64;

@@ -24,14 +24,17 @@ TOL_BATCH = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 1e-3}
 
 
 def _mixed_cases():
-    """Uneven sizes, N_v even/odd (vector form on/off), plain and frozen
-    switches, all-kinetic, hybrid and initially all-fluid maps.  Every
+    """Uneven sizes, N_v even/odd (every per-cell form: groups of 4 or 2
+    nodes, one or two cells per warp, scalar), plain and frozen switches,
+    all-kinetic, hybrid and initially all-fluid maps.  Every
     velocity grid resolves the thermal speed of its data (dv <= sqrt(T)
     in most cells), so that rounding differences are not amplified by an
     ill-conditioned moment system."""
     out = []
     out.append(W.riemann_quadrants(nx=24, ny=20, nv=16, seed=3))               # plain, starts fluid
     out += W.batched_cases(n_cases=2, seed0=11, sizes=[16, 24], nvs=[12, 16])  # plain, all kinetic
+    for k, nv in enumerate((18, 26, 20)):   # 2-node groups (two / one cell per warp), straddling 4-node groups
+        out += W.batched_cases(n_cases=1, seed0=30 + k, sizes=[12, 20], nvs=[nv])
     out.append(W.sine_periodic(nx=10, ny=14, nv=15, scheme="ars233"))        # frozen, odd N_v
     hyb = W.gaussian_blob(nx=18, ny=12, nv=8, vmax=4.0)
     rng = np.random.default_rng(5)

@@ -180,15 +180,41 @@ def test_riemann_full_size_first_steps():
     assert st.kin.sum() > 0
 
 
-@pytest.mark.parametrize("prec,nv", [("fp64", 10), ("fp32", 20), ("fp32", 12)])
-def test_vector_groups_straddling_zero_velocity(prec, nv):
-    """Velocity grids whose node groups of the vector form would straddle
-    v_x = 0 (N_v/2 not a multiple of the group width: 2 nodes in FP64, 4 in
-    FP32): these take the node-by-node form, with the upwind neighbours
-    chosen per node."""
+# (precision, N_v, expected form: nodes per group, cells per warp)
+STRADDLE = [("fp64", 10, (2, 2)), ("fp64", 26, (2, 1)), ("fp32", 12, (4, 2)), ("fp32", 20, (4, 2)),
+            ("fp32", 28, (4, 1)), ("fp32", 18, (2, 2)), ("fp32", 26, (2, 1)), ("fp32", 11, (1, 1))]
+
+
+@pytest.mark.parametrize("prec,nv,form", STRADDLE)
+def test_vector_groups_straddling_zero_velocity(prec, nv, form):
+    """Velocity grids whose node groups straddle v_x = 0 (N_v/2 not a
+    multiple of the group width): the group holding v_x = 0 takes the upwind
+    stencil node by node.  Covers groups of 4 and 2 nodes, one and two cells
+    per warp, and the scalar form (odd N_v)."""
     wl = W.gaussian_blob(nx=12, ny=10, nv=nv, vmax=6.0, u0=(0.4, -0.2), steps=3)
-    worst, *_ = run_parity(wl, 3, prec)
+    worst, g, *_ = run_parity(wl, 3, prec)
+    assert g.kinetic_form() == form
     assert worst.max() <= TOL[prec], worst
+
+
+@pytest.mark.parametrize("nv,form", [(18, (2, 2)), (30, (2, 1)), (20, (4, 2))])
+def test_bf16_narrow_and_straddling_groups(nv, form):
+    """BF16 storage in the 2-node and straddling 4-node forms: macroscopic
+    fields within the BF16 storage bound (2e-3 relative L1) of the FP64
+    oracle after 3 steps."""
+    wl = W.gaussian_blob(nx=12, ny=10, nv=nv, vmax=6.0, u0=(0.4, -0.2), steps=3)
+    g = gpu_solver(wl, "bf16")
+    assert g.kinetic_form() == form
+    P, st = oracle_pair(wl)
+    tab = tableau_of(wl["scheme"])
+    for _ in range(3):
+        g.step(wl["dt"], wl["scheme"])
+        st = O.step(P, st, wl["dt"], tab)
+    U = g.cons()
+    r = np.abs(st.U[0]).sum()
+    for q in range(4):
+        scale = np.abs(st.U[3]).sum() if q == 3 else r
+        assert np.abs(U[q] - st.U[q]).sum() / scale <= 2e-3, q
 
 
 # ---------------------------------------------------------------------------
