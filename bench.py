@@ -492,7 +492,8 @@ def batch_arm(args):
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic", "config": cfg,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                        "kernel": "batch_stage_kernel (all cases, fused IMEX stage + final combination)",
+                        "kernel": "batch_stage_kernel (all cases, fused IMEX stage + final combination; one "
+                                  "launch per per-cell form present, timed together per stage)",
                         "algorithmic_bytes_per_launch": algo_bytes / st_n if st_n else None,
                         "avg_launch_ms": st_ms / st_n if st_n else None, "peak_source": peak_src,
                         "bytes_model": "12 f-array accesses per element per step / 3 transport evaluations x %d B"
