@@ -319,7 +319,7 @@ int regime_launches(esbgk_ctx* X, bool l1_needed, bool judge_prev) {
   if (r) return r;
   {
     Timed t(X, ESBGK_K_FLAGS);
-    launch_flags(V, X->Un, X->L1, X->L1, X->lamA, X->flags, X->stream);
+    launch_flags(V, X->Un, X->L1, X->L1, X->lamA, X->flags, X->prec != ESBGK_FP64, X->stream);
   }
   if ((r = after_launch(X, "flags kernel"))) return r;
   if (X->sw == ESBGK_SWITCH_LEARNED) {
@@ -1155,6 +1155,7 @@ struct esbgk_batch {
     T.off_l1 = d_off_l1;
     T.n = n;
     T.total_cells = total_cells;
+    T.fp32 = prec != ESBGK_FP64 ? 1 : 0;
     return T;
   }
 };

@@ -42,6 +42,12 @@ __device__ __forceinline__ double sqrt_nr(double x) {
   return x * y;
 }
 
+// Reciprocal and square root in the criterion's arithmetic type.
+__device__ __forceinline__ double crit_rcp(double x) { return rcp_nr(x); }
+__device__ __forceinline__ float crit_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double crit_sqrt(double x) { return sqrt_nr(x); }
+__device__ __forceinline__ float crit_sqrt(float x) { return x > 0.0f ? sqrtf(x) : 0.0f; }
+
 // Regime criteria of Sec. 3.1.2 for one cell.  X = I - S_1 with
 //   S_1 = I - eps D(u) mu/(rho T) - 2/3 (eps kappa/(rho T^{3/2}))^2 grad T grad T^T,
 //   mu/(rho T) = 1/(tau (1-beta)),  kappa/(rho T^{3/2}) = 5/2 /(tau sqrt T),
@@ -50,54 +56,59 @@ __device__ __forceinline__ double sqrt_nr(double x) {
 // Gradients: central differences of cell-centre u and T, ghost cells by BC.
 // New flag (Eqs. crit:CompEuler, eqKintoFluid1):
 //   lambda_A > eta   or   (kinetic and ||f - M||_1 > delta).
-__device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t nc, int cc, double& ux, double& uy,
-                                          double& T) {
-  const double rho = Un[cc], mx = Un[nc + cc], my = Un[2 * nc + cc], E = Un[3 * nc + cc];
-  const double ir = rcp_nr(rho);
+// R: float64 for FP64 storage, float32 for FP32/BF16 storage (the decision is
+// then taken in the storage's working precision; GB300's FP64 pipe is narrow).
+template <typename R>
+__device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t nc, int cc, R& ux, R& uy, R& T) {
+  const R rho = (R)Un[cc], mx = (R)Un[nc + cc], my = (R)Un[2 * nc + cc], E = (R)Un[3 * nc + cc];
+  const R ir = crit_rcp(rho);
   ux = mx * ir;
   uy = my * ir;
-  T = (E - 0.5 * rho * (ux * ux + uy * uy)) * ir;
+  T = (E - R(0.5) * rho * (ux * ux + uy * uy)) * ir;
 }
 
 // The criterion of cell c from the primitive variables of the cell (0) and
 // of its east, west, north and south neighbours.
+template <typename R>
 struct Prims {
-  double ux, uy, T;
+  R ux, uy, T;
 };
+template <typename R>
 __device__ __forceinline__ void flags_from_prims(const View& V, const double* __restrict__ L1in, double* L1out,
                                                  double* lamA, uint8_t* flags_out, int c, bool plain,
-                                                 const Prims& P0, const Prims& PE, const Prims& PW, const Prims& PN,
-                                                 const Prims& PS) {
+                                                 const Prims<R>& P0, const Prims<R>& PE, const Prims<R>& PW,
+                                                 const Prims<R>& PN, const Prims<R>& PS) {
   const Geo& g = V.g;
-  const double i2dx = 0.5 / g.dx, i2dy = 0.5 / g.dy;
-  const double dudx = (PE.ux - PW.ux) * i2dx, dudy = (PN.ux - PS.ux) * i2dy;
-  const double dvdx = (PE.uy - PW.uy) * i2dx, dvdy = (PN.uy - PS.uy) * i2dy;
-  const double dTdx = (PE.T - PW.T) * i2dx, dTdy = (PN.T - PS.T) * i2dy;
-  const double div = dudx + dvdy;
-  const double Dxx = 2.0 * dudx - (2.0 / 3.0) * div;
-  const double Dyy = 2.0 * dvdy - (2.0 / 3.0) * div;
-  const double Dxy = dudy + dvdx;
-  const double eps = V.eps[c];
-  const double c1 = eps / (V.m.tau * (1.0 - V.m.beta));
-  const double kk = 2.5 * eps * rcp_nr(V.m.tau * sqrt_nr(P0.T));
-  const double c2 = (2.0 / 3.0) * kk * kk;
-  const double Xxx = c1 * Dxx + c2 * dTdx * dTdx;
-  const double Xxy = c1 * Dxy + c2 * dTdx * dTdy;
-  const double Xyy = c1 * Dyy + c2 * dTdy * dTdy;
-  const double mean = 0.5 * (Xxx + Xyy), half = 0.5 * (Xxx - Xyy);
-  const double lam = fabs(mean) + sqrt_nr(half * half + Xxy * Xxy);
+  const R i2dx = R(0.5 / g.dx), i2dy = R(0.5 / g.dy);
+  const R dudx = (PE.ux - PW.ux) * i2dx, dudy = (PN.ux - PS.ux) * i2dy;
+  const R dvdx = (PE.uy - PW.uy) * i2dx, dvdy = (PN.uy - PS.uy) * i2dy;
+  const R dTdx = (PE.T - PW.T) * i2dx, dTdy = (PN.T - PS.T) * i2dy;
+  const R div = dudx + dvdy;
+  const R Dxx = R(2) * dudx - R(2.0 / 3.0) * div;
+  const R Dyy = R(2) * dvdy - R(2.0 / 3.0) * div;
+  const R Dxy = dudy + dvdx;
+  const R eps = (R)V.eps[c];
+  const R c1 = eps / (R(V.m.tau) * (R(1) - R(V.m.beta)));
+  const R kk = R(2.5) * eps * crit_rcp(R(V.m.tau) * crit_sqrt(P0.T));
+  const R c2 = R(2.0 / 3.0) * kk * kk;
+  const R Xxx = c1 * Dxx + c2 * dTdx * dTdx;
+  const R Xxy = c1 * Dxy + c2 * dTdx * dTdy;
+  const R Xyy = c1 * Dyy + c2 * dTdy * dTdy;
+  const R mean = R(0.5) * (Xxx + Xyy), half = R(0.5) * (Xxx - Xyy);
+  const R lam = rabs(mean) + crit_sqrt(half * half + Xxy * Xxy);
   const uint8_t kin = V.flags[c];
   const double l1 = kin ? L1in[c] : 0.0;
-  lamA[c] = lam;
+  lamA[c] = (double)lam;
   L1out[c] = l1;
-  if (plain) flags_out[c] = (lam > V.m.eta_factor * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
+  if (plain) flags_out[c] = (lam > R(V.m.eta_factor) * eps) || (kin && l1 > V.m.delta) ? 1 : 0;
 }
 
+template <typename R>
 __device__ void flags_cell(const View& V, const double* __restrict__ Un, const double* __restrict__ L1in,
                            double* L1out, double* lamA, uint8_t* flags_out, int c, bool plain) {
   const Geo& g = V.g;
   const int i = c % g.nx, j = c / g.nx;
-  Prims P0, PE, PW, PN, PS;
+  Prims<R> P0, PE, PW, PN, PS;
   prim_cell(Un, g.nc, j * g.nx + nb(i + 1, g.nx, g.bcx), PE.ux, PE.uy, PE.T);
   prim_cell(Un, g.nc, j * g.nx + nb(i - 1, g.nx, g.bcx), PW.ux, PW.uy, PW.T);
   prim_cell(Un, g.nc, nb(j + 1, g.ny, g.bcy) * g.nx + i, PN.ux, PN.uy, PN.T);
@@ -108,12 +119,13 @@ __device__ void flags_cell(const View& V, const double* __restrict__ Un, const d
 
 // Tiled form: a CTA owns FX x FY cells and computes the primitive variables
 // of the tile and its one-cell halo once, in shared memory.
-constexpr int kFX = 32, kFY = 8;
+constexpr int kFX = 16, kFY = 8;
+template <typename R>
 __global__ void __launch_bounds__(kFX* kFY) flags_tile_kernel(View V, const double* __restrict__ Un,
                                                               const double* __restrict__ L1in, double* L1out,
                                                               double* lamA, uint8_t* flags_out) {
   constexpr int HX = kFX + 2, HY = kFY + 2;
-  __shared__ Prims sp[HX * HY];
+  __shared__ Prims<R> sp[HX * HY];
   const Geo& g = V.g;
   const int i0 = blockIdx.x * kFX - 1, j0 = blockIdx.y * kFY - 1;
   const int t = threadIdx.y * kFX + threadIdx.x;
@@ -130,9 +142,12 @@ __global__ void __launch_bounds__(kFX* kFY) flags_tile_kernel(View V, const doub
 }
 
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
-                  uint8_t* flags_out, cudaStream_t s) {
+                  uint8_t* flags_out, bool fp32, cudaStream_t s) {
   const dim3 grid((V.g.nx + kFX - 1) / kFX, (V.g.ny + kFY - 1) / kFY);
-  flags_tile_kernel<<<grid, dim3(kFX, kFY), 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+  if (fp32)
+    flags_tile_kernel<float><<<grid, dim3(kFX, kFY), 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+  else
+    flags_tile_kernel<double><<<grid, dim3(kFX, kFY), 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
 }
 
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
@@ -395,16 +410,20 @@ __global__ void batch_l1_offsets_kernel(BatchTabs T) {
 
 void launch_batch_l1_offsets(const BatchTabs& T, cudaStream_t s) { batch_l1_offsets_kernel<<<1, 32, 0, s>>>(T); }
 
+template <typename R>
 __global__ void batch_flags_kernel(BatchTabs T) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= T.total_cells) return;
   const int c = find_case(T.cell_off, T.n, u);
-  const CaseRegime& R = T.reg[c];
-  flags_cell(R.V, R.Un, R.L1, R.L1, R.lamA, R.flags, u - T.cell_off[c], R.plain != 0);
+  const CaseRegime& C = T.reg[c];
+  flags_cell<R>(C.V, C.Un, C.L1, C.L1, C.lamA, C.flags, u - T.cell_off[c], C.plain != 0);
 }
 
 void launch_batch_flags(const BatchTabs& T, cudaStream_t s) {
-  batch_flags_kernel<<<(T.total_cells + 127) / 128, 128, 0, s>>>(T);
+  if (T.fp32)
+    batch_flags_kernel<float><<<(T.total_cells + 127) / 128, 128, 0, s>>>(T);
+  else
+    batch_flags_kernel<double><<<(T.total_cells + 127) / 128, 128, 0, s>>>(T);
 }
 
 __global__ void batch_categorize_kernel(BatchTabs T) {

@@ -186,6 +186,7 @@ struct BatchTabs {
   int* off_l1;            // [n+1] prefix of L1 units
   int n;
   int total_cells;
+  int fp32;  // the criterion's arithmetic in float32 (FP32 and BF16 storage)
 };
 
 // Per-storage-type launchers (one table per precision).
@@ -216,8 +217,9 @@ extern const Launchers kLaunchBF16;
 // Precision-independent kernels (kernels_common.cu).
 void launch_init_state(const double* prim /*[5][nc] rho ux uy T eps*/, const uint8_t* kin_in, double* Un,
                        double* eps, uint8_t* flags, uint8_t* flags_prev, int nc, cudaStream_t s);
+// fp32: the criterion's arithmetic in float32 (FP32 and BF16 storage), else float64.
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
-                  uint8_t* flags_out, cudaStream_t s);
+                  uint8_t* flags_out, bool fp32, cudaStream_t s);
 void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
                        cudaStream_t s);
 void launch_compact(const uint8_t* cat, int nc, int* klist, int* blist, int* flist, int* clist, int* counts,
