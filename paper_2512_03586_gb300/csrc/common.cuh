@@ -190,6 +190,35 @@ ESBGK_DEV R cweno_face(R a, R b, R c, R epsw) {
   return fdiv(a0 * P0 + aL * PL + aR * PR, a0 + aL + aR);
 }
 
+// The same face value for two independent stencils at once, on the paired
+// FP32 instructions of sm_100-family GPUs (two lanes of float arithmetic per
+// issued instruction); the divisions stay per component.
+ESBGK_DEV float2 splat2(float a) { return make_float2(a, a); }
+ESBGK_DEV float2 cweno_face2(float2 a, float2 b, float2 c, float2 epsw) {
+  const float2 m1 = splat2(-1.0f);
+  const float2 dl = __ffma2_rn(a, m1, b);  // b - a
+  const float2 dr = __ffma2_rn(b, m1, c);  // c - b
+  const float2 d1 = __ffma2_rn(a, m1, c);  // c - a
+  const float2 D = __ffma2_rn(dl, m1, dr);
+  const float2 PL = __ffma2_rn(splat2(0.5f), dl, b);
+  const float2 PR = __ffma2_rn(splat2(0.5f), dr, b);
+  const float2 P0 = __ffma2_rn(splat2(0.25f), d1, __ffma2_rn(D, splat2(1.0f / 6.0f), b));
+  const float2 IS0 = __ffma2_rn(__fmul2_rn(splat2(13.0f / 3.0f), D), D, __fmul2_rn(__fmul2_rn(splat2(0.25f), d1), d1));
+  float2 sL = __ffma2_rn(dl, dl, epsw);
+  sL = __fmul2_rn(sL, sL);
+  float2 sR = __ffma2_rn(dr, dr, epsw);
+  sR = __fmul2_rn(sR, sR);
+  float2 s0 = __fadd2_rn(epsw, IS0);
+  s0 = __fmul2_rn(s0, s0);
+  const float2 a0 = __fmul2_rn(__fmul2_rn(splat2(0.5f), sL), sR);
+  const float2 q = __fmul2_rn(splat2(0.25f), s0);
+  const float2 aL = __fmul2_rn(q, sR);
+  const float2 aR = __fmul2_rn(q, sL);
+  const float2 num = __ffma2_rn(a0, P0, __ffma2_rn(aL, PL, __fmul2_rn(aR, PR)));
+  const float2 den = __fadd2_rn(__fadd2_rn(a0, aL), aR);
+  return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
 // Case of global work unit u: the largest c with off[c] <= u (off ascending,
 // off[0] = 0, n >= 1).
 ESBGK_DEV int find_case(const int* off, int n, int u) {

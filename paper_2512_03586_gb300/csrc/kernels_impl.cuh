@@ -14,6 +14,8 @@
 // lane per cell).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -785,9 +787,15 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   const int half_nv = g.nv >> 1, kz = SX ? half_nv - half_nv % W : -1;
 
   // pass 1: transport of the previous stage, f*, moments of f*
+  // (FP32 arithmetic with an even group: pairs of nodes on paired instructions)
+  constexpr bool kPacked = std::is_same<R, float>::value && W % 2 == 0;
   R m[6];
+  float2 m2[6];
 #pragma unroll
-  for (int n = 0; n < 6; ++n) m[n] = R(0);
+  for (int n = 0; n < 6; ++n) {
+    m[n] = R(0);
+    m2[n] = splat2(0.0f);
+  }
   NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
 #pragma unroll 1
   for (; it.k < g.nvv; it.next()) {
@@ -833,22 +841,55 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     }
     R fs[W], pa[nacc > 0 ? nacc : 1][W];
     const R ay = rabs(vy) * idy;
+    if constexpr (kPacked) {
+      // nodes j, j + 1 together on the paired FP32 instructions
+      const float2 e2 = splat2(epsw), m1 = splat2(-1.0f);
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const R vx = vx0 + R(j) * dv;
-      const R Lx = rabs(vx) * idx * (cweno_face(ux[j], q0[j], dx[j], epsw) - cweno_face(fx[j], ux[j], q0[j], epsw));
-      const R Ly = ay * (cweno_face(uy[j], q0[j], dy[j], epsw) - cweno_face(fy[j], uy[j], q0[j], epsw));
-      const R L = Lx + Ly;
-      fs[j] = bs[j] + cL * L;
+      for (int j = 0; j < W; j += 2) {
+        const float2 Q = make_float2(q0[j], q0[j + 1]);
+        const float2 Ux = make_float2(ux[j], ux[j + 1]), Uy = make_float2(uy[j], uy[j + 1]);
+        const float2 dFx = __ffma2_rn(cweno_face2(make_float2(fx[j], fx[j + 1]), Ux, Q, e2), m1,
+                                      cweno_face2(Ux, Q, make_float2(dx[j], dx[j + 1]), e2));
+        const float2 dFy = __ffma2_rn(cweno_face2(make_float2(fy[j], fy[j + 1]), Uy, Q, e2), m1,
+                                      cweno_face2(Uy, Q, make_float2(dy[j], dy[j + 1]), e2));
+        const float vxa = vx0 + R(j) * dv, vxb = vxa + dv;
+        const float2 Lf = __ffma2_rn(make_float2(rabs(vxa) * idx, rabs(vxb) * idx), dFx, __fmul2_rn(splat2(ay), dFy));
+        const float2 F = __ffma2_rn(splat2(cL), Lf, make_float2(bs[j], bs[j + 1]));
+        fs[j] = F.x;
+        fs[j + 1] = F.y;
 #pragma unroll
-      for (int t = 0; t < nacc; ++t) pa[t][j] = ai[t][j] + aL[t] * L;
-      const R cx = vx - u0x, cy = vy - u0y;
-      m[0] += fs[j];
-      m[1] += cx * fs[j];
-      m[2] += cy * fs[j];
-      m[3] += cx * cx * fs[j];
-      m[4] += cx * cy * fs[j];
-      m[5] += cy * cy * fs[j];
+        for (int t = 0; t < nacc; ++t) {
+          const float2 Pa = __ffma2_rn(splat2(aL[t]), Lf, make_float2(ai[t][j], ai[t][j + 1]));
+          pa[t][j] = Pa.x;
+          pa[t][j + 1] = Pa.y;
+        }
+        const float2 cx = make_float2(vxa - u0x, vxb - u0x), cy = splat2(vy - u0y);
+        const float2 xf = __fmul2_rn(cx, F), yf = __fmul2_rn(cy, F);
+        m2[0] = __fadd2_rn(m2[0], F);
+        m2[1] = __fadd2_rn(m2[1], xf);
+        m2[2] = __fadd2_rn(m2[2], yf);
+        m2[3] = __ffma2_rn(cx, xf, m2[3]);
+        m2[4] = __ffma2_rn(cy, xf, m2[4]);
+        m2[5] = __ffma2_rn(cy, yf, m2[5]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const R vx = vx0 + R(j) * dv;
+        const R Lx = rabs(vx) * idx * (cweno_face(ux[j], q0[j], dx[j], epsw) - cweno_face(fx[j], ux[j], q0[j], epsw));
+        const R Ly = ay * (cweno_face(uy[j], q0[j], dy[j], epsw) - cweno_face(fy[j], uy[j], q0[j], epsw));
+        const R Lf = Lx + Ly;
+        fs[j] = bs[j] + cL * Lf;
+#pragma unroll
+        for (int t = 0; t < nacc; ++t) pa[t][j] = ai[t][j] + aL[t] * Lf;
+        const R cx = vx - u0x, cy = vy - u0y;
+        m[0] += fs[j];
+        m[1] += cx * fs[j];
+        m[2] += cy * fs[j];
+        m[3] += cx * cx * fs[j];
+        m[4] += cx * cy * fs[j];
+        m[5] += cy * cy * fs[j];
+      }
     }
     const uint32_t kb = s0 + ((o0 + k) << 3);  // distinct per group and stored array
     if (relax) {
@@ -859,6 +900,10 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     }
 #pragma unroll
     for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
+  }
+  if constexpr (kPacked) {
+#pragma unroll
+    for (int n = 0; n < 6; ++n) m[n] = m2[n].x + m2[n].y;
   }
 #pragma unroll
   for (int n = 0; n < 6; ++n) m[n] = group_sum<L>(m[n], mask);
