@@ -284,6 +284,45 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0x
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
+  if constexpr (std::is_same<R, float>::value && W % 2 == 0) {
+    // pairs of nodes on the paired FP32 instructions (the pair shares v_y)
+    float2 s2[15];
+#pragma unroll
+    for (int n = 0; n < 15; ++n) s2[n] = splat2(0.0f);
+#pragma unroll 1
+    for (; it.k < g.nvv; it.next()) {
+      const float cy = it.vy() - P.uy, y = cy * P.isT;
+      const float2 y2 = splat2(y), qy = splat2(P.qyy * cy * cy), qc = splat2(P.qxy * cy);
+#pragma unroll
+      for (int j = 0; j < W; j += 2) {
+        const float cxa = it.vx() + R(j) * dv - P.ux;
+        const float2 cx = make_float2(cxa, cxa + dv);
+        const float2 e = __ffma2_rn(splat2(P.qxx), __fmul2_rn(cx, cx), __ffma2_rn(qc, cx, qy));
+        const float2 G = __fmul2_rn(splat2(P.pref), make_float2(exp2r(e.x), exp2r(e.y)));
+        const float2 x = __fmul2_rn(cx, splat2(P.isT));
+        const float2 Gx = __fmul2_rn(G, x), Gy = __fmul2_rn(G, y2);
+        const float2 Gxx = __fmul2_rn(Gx, x), Gxy = __fmul2_rn(Gx, y2), Gyy = __fmul2_rn(Gy, y2);
+        s2[0] = __fadd2_rn(s2[0], G);
+        s2[1] = __fadd2_rn(s2[1], Gx);
+        s2[2] = __fadd2_rn(s2[2], Gy);
+        s2[3] = __fadd2_rn(s2[3], Gxx);
+        s2[4] = __fadd2_rn(s2[4], Gxy);
+        s2[5] = __fadd2_rn(s2[5], Gyy);
+        s2[6] = __ffma2_rn(Gxx, x, s2[6]);
+        s2[7] = __ffma2_rn(Gxx, y2, s2[7]);
+        s2[8] = __ffma2_rn(Gxy, y2, s2[8]);
+        s2[9] = __ffma2_rn(Gyy, y2, s2[9]);
+        const float2 Gxxx = __fmul2_rn(Gxx, x), Gxxy = __fmul2_rn(Gxx, y2);
+        s2[10] = __ffma2_rn(Gxxx, x, s2[10]);
+        s2[11] = __ffma2_rn(Gxxx, y2, s2[11]);
+        s2[12] = __ffma2_rn(Gxxy, y2, s2[12]);
+        s2[13] = __ffma2_rn(__fmul2_rn(Gxy, y2), y2, s2[13]);
+        s2[14] = __ffma2_rn(__fmul2_rn(Gyy, y2), y2, s2[14]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 15; ++n) s[n] = s2[n].x + s2[n].y;
+  } else {
 #pragma unroll 1
   for (; it.k < g.nvv; it.next())
 #pragma unroll
@@ -308,6 +347,7 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0x
     s[12] += Gxx * y * y;
     s[13] += Gxy * y * y;
     s[14] += Gyy * y * y;
+  }
   }
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = group_sum<L>(s[n], mask) * pick<R>(g.w, g.fw);
@@ -944,18 +984,50 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 #pragma unroll
     for (int t = 0; t < nacc; ++t) IO::ldc(aout[t] + o0 + k, pa[t]);
     const R cy = jt.vy() - P.uy, cx0 = jt.vx() - P.ux;
+    if constexpr (kPacked) {
+      // pairs of nodes on the paired FP32 instructions; G_hat = G (c0 + c1 x + a3 x^2)
+      // with the y terms of 1 + a . psi folded into c0, c1 once per pair
+      const float y = cy * P.isT;
+      const float2 qy = splat2(P.qyy * cy * cy), qc = splat2(P.qxy * cy);
+      const float2 c0 = splat2(R(1) + P.a[0] + P.a[2] * y + P.a[5] * y * y), c1 = splat2(P.a[1] + P.a[4] * y);
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      R Q = R(0);
-      fn[j] = fs[j];
-      if (ok) {
-        const R Gh = ghat(P, cx0 + R(j) * dv, cy);
-        // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
-        fn[j] = (fs[j] + h * Gh) * inv1h;
-        Q = nu * (Gh - fs[j]) * inv1h;
+      for (int j = 0; j < W; j += 2) {
+        const float2 F = make_float2(fs[j], fs[j + 1]);
+        float2 Fn = F, Q = splat2(0.0f);
+        if (ok) {
+          const float cxa = cx0 + R(j) * dv;
+          const float2 cx = make_float2(cxa, cxa + dv);
+          const float2 e = __ffma2_rn(splat2(P.qxx), __fmul2_rn(cx, cx), __ffma2_rn(qc, cx, qy));
+          const float2 G = __fmul2_rn(splat2(P.pref), make_float2(exp2r(e.x), exp2r(e.y)));
+          const float2 x = __fmul2_rn(cx, splat2(P.isT));
+          const float2 Gh = __fmul2_rn(G, __ffma2_rn(__ffma2_rn(splat2(P.a[3]), x, c1), x, c0));
+          // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
+          Fn = __fmul2_rn(__ffma2_rn(splat2(h), Gh, F), splat2(inv1h));
+          Q = __fmul2_rn(splat2(nu * inv1h), __ffma2_rn(F, splat2(-1.0f), Gh));
+        }
+        fn[j] = Fn.x;
+        fn[j + 1] = Fn.y;
+#pragma unroll
+        for (int t = 0; t < nacc; ++t) {
+          const float2 Pa = __ffma2_rn(splat2(aQ[t]), Q, make_float2(pa[t][j], pa[t][j + 1]));
+          pa[t][j] = Pa.x;
+          pa[t][j + 1] = Pa.y;
+        }
       }
+    } else {
 #pragma unroll
-      for (int t = 0; t < nacc; ++t) pa[t][j] += aQ[t] * Q;
+      for (int j = 0; j < W; ++j) {
+        R Q = R(0);
+        fn[j] = fs[j];
+        if (ok) {
+          const R Gh = ghat(P, cx0 + R(j) * dv, cy);
+          // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
+          fn[j] = (fs[j] + h * Gh) * inv1h;
+          Q = nu * (Gh - fs[j]) * inv1h;
+        }
+#pragma unroll
+        for (int t = 0; t < nacc; ++t) pa[t][j] += aQ[t] * Q;
+      }
     }
     const uint32_t kb = s0 + ((o0 + k) << 3);
     IO::st_sr(fout + o0 + k, fn, kb);
