@@ -404,6 +404,24 @@ ESBGK_DEV R ghat(const CellPar<R>& P, R cx, R cy) {
   return G * (R(1) + P.a[0] + P.a[1] * x + P.a[2] * y + P.a[3] * x * x + P.a[4] * x * y + P.a[5] * y * y);
 }
 
+// G_hat at two nodes of one velocity row on the paired FP32 instructions:
+// G_hat = G (c0 + c1 x + a3 x^2), the row's y terms of 1 + a . psi folded into
+// c0 and c1, and the exponent's y terms into qy, qc, once per row.
+struct GhatRow {
+  float2 qy, qc, c0, c1;
+};
+ESBGK_DEV GhatRow ghat_row(const CellPar<float>& P, float cy) {
+  const float y = cy * P.isT;
+  return GhatRow{splat2(P.qyy * cy * cy), splat2(P.qxy * cy), splat2(1.0f + P.a[0] + P.a[2] * y + P.a[5] * y * y),
+                 splat2(P.a[1] + P.a[4] * y)};
+}
+ESBGK_DEV float2 ghat_pair(const CellPar<float>& P, const GhatRow& r, float2 cx) {
+  const float2 e = __ffma2_rn(splat2(P.qxx), __fmul2_rn(cx, cx), __ffma2_rn(r.qc, cx, r.qy));
+  const float2 G = __fmul2_rn(splat2(P.pref), make_float2(exp2r(e.x), exp2r(e.y)));
+  const float2 x = __fmul2_rn(cx, splat2(P.isT));
+  return __fmul2_rn(G, __ffma2_rn(__ffma2_rn(splat2(P.a[3]), x, r.c1), x, r.c0));
+}
+
 // Element offsets of the two-cell cross stencil of cell c (BC mapped):
 // o[0..3] = i-2, i-1, i+1, i+2 along x, o[4..7] the same along y.  Offsets
 // are 32-bit: the library limits N_c N_v^2 to below 2^31 elements.
@@ -578,9 +596,22 @@ ESBGK_DEV R l1_deviation(const Geo& g, int lane, const R (&m)[6], R u0x, R u0y, 
   const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
   R s = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
-  for (; it.k < g.nvv; it.next())
+  if constexpr (std::is_same<R, float>::value && W % 2 == 0) {
+    for (; it.k < g.nvv; it.next()) {
+      const GhatRow row = ghat_row(P, it.vy() - P.uy);
 #pragma unroll
-    for (int j = 0; j < W; ++j) s += rabs(sf[it.k + j] - ghat(P, it.vx() + R(j) * dv - P.ux, it.vy() - P.uy));
+      for (int j = 0; j < W; j += 2) {
+        const float cxa = it.vx() + R(j) * dv - P.ux;
+        const float2 d = __ffma2_rn(ghat_pair(P, row, make_float2(cxa, cxa + dv)), splat2(-1.0f),
+                                    *reinterpret_cast<const float2*>(sf + it.k + j));
+        s += rabs(d.x) + rabs(d.y);
+      }
+    }
+  } else {
+    for (; it.k < g.nvv; it.next())
+#pragma unroll
+      for (int j = 0; j < W; ++j) s += rabs(sf[it.k + j] - ghat(P, it.vx() + R(j) * dv - P.ux, it.vy() - P.uy));
+  }
   return group_sum<L>(s, mask) * pick<R>(g.w, g.fw);
 }
 
@@ -985,22 +1016,15 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     for (int t = 0; t < nacc; ++t) IO::ldc(aout[t] + o0 + k, pa[t]);
     const R cy = jt.vy() - P.uy, cx0 = jt.vx() - P.ux;
     if constexpr (kPacked) {
-      // pairs of nodes on the paired FP32 instructions; G_hat = G (c0 + c1 x + a3 x^2)
-      // with the y terms of 1 + a . psi folded into c0, c1 once per pair
-      const float y = cy * P.isT;
-      const float2 qy = splat2(P.qyy * cy * cy), qc = splat2(P.qxy * cy);
-      const float2 c0 = splat2(R(1) + P.a[0] + P.a[2] * y + P.a[5] * y * y), c1 = splat2(P.a[1] + P.a[4] * y);
+      // pairs of nodes on the paired FP32 instructions
+      const GhatRow row = ghat_row(P, cy);
 #pragma unroll
       for (int j = 0; j < W; j += 2) {
         const float2 F = make_float2(fs[j], fs[j + 1]);
         float2 Fn = F, Q = splat2(0.0f);
         if (ok) {
           const float cxa = cx0 + R(j) * dv;
-          const float2 cx = make_float2(cxa, cxa + dv);
-          const float2 e = __ffma2_rn(splat2(P.qxx), __fmul2_rn(cx, cx), __ffma2_rn(qc, cx, qy));
-          const float2 G = __fmul2_rn(splat2(P.pref), make_float2(exp2r(e.x), exp2r(e.y)));
-          const float2 x = __fmul2_rn(cx, splat2(P.isT));
-          const float2 Gh = __fmul2_rn(G, __ffma2_rn(__ffma2_rn(splat2(P.a[3]), x, c1), x, c0));
+          const float2 Gh = ghat_pair(P, row, make_float2(cxa, cxa + dv));
           // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f) = nu (G_hat - f*)/(1 + h)
           Fn = __fmul2_rn(__ffma2_rn(splat2(h), Gh, F), splat2(inv1h));
           Q = __fmul2_rn(splat2(nu * inv1h), __ffma2_rn(F, splat2(-1.0f), Gh));
@@ -1055,8 +1079,19 @@ ESBGK_DEV bool fill_maxwell(S* f, const Geo& g, int c, int lane, const double (&
     if constexpr (W > 1) {
       R v[W];
       const R cy = it.vy() - P.uy, cx0 = it.vx() - P.ux;
+      if constexpr (std::is_same<R, float>::value && W % 2 == 0) {
+        const GhatRow row = ghat_row(P, cy);
 #pragma unroll
-      for (int j = 0; j < W; ++j) v[j] = ghat(P, cx0 + R(j) * dv, cy);
+        for (int j = 0; j < W; j += 2) {
+          const float cxa = cx0 + R(j) * dv;
+          const float2 Gh = ghat_pair(P, row, make_float2(cxa, cxa + dv));
+          v[j] = Gh.x;
+          v[j + 1] = Gh.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = ghat(P, cx0 + R(j) * dv, cy);
+      }
       VecIO<S, W>::st_sr(f + o0 + it.k, v, key + (uint32_t)((o0 + it.k) << 3));
     } else {
       st(f + o0 + it.k, ghat(P, it.vx() - P.ux, it.vy() - P.uy));
