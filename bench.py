@@ -133,6 +133,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # sampling has started before the timed region does
         except Exception:
             self.proc = None
         return self
@@ -689,9 +690,14 @@ def switchnet_arm(args):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / k
 
+    # at least ~0.4 s of timed work per figure, so that the clock record has samples
+    est_tr = timed(lambda: net.train_step(xt, yt, 3.0, 1e-3), 3)
+    est_inf = timed(lambda: inf.forward(xi), 3)
+    k_tr = max(args.steps, int(400.0 / max(est_tr, 1e-3)))
+    k_inf = max(args.steps, int(400.0 / max(est_inf, 1e-3)))
     with ClockSampler(local) as clk:
-        ms_train = timed(lambda: net.train_step(xt, yt, 3.0, 1e-3), args.steps)
-        ms_inf = timed(lambda: inf.forward(xi), args.steps)
+        ms_train = timed(lambda: net.train_step(xt, yt, 3.0, 1e-3), k_tr)
+        ms_inf = timed(lambda: inf.forward(xi), k_inf)
         # the 32 -> 32 convolution alone, through the forward pass of one image
         ms_fwd = ms_inf
     cells_tr, cells_inf = n_tr * Ht * Ht, 512 * 512
@@ -705,13 +711,14 @@ def switchnet_arm(args):
         peak, src = 1900.0, "fallback 1.9 PFLOP/s"
     tf_inf = cells_inf * f_fwd / (ms_fwd * 1e-3) / 1e12
     out = {"metric": "learned-switch network: cells per second (one Adam training step)", "value": cells_tr / (ms_train * 1e-3),
-           "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_train,
+           "unit": "cells/s", "n_gpus": 1, "steps": k_tr, "warmup": args.warmup, "ms_per_step": ms_train,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands / f32 accumulation",
            "data": "synthetic", "config": {"workload": "switch network: training batches of 32 x 128 x 128 cells; "
                                                        "inference of one 512 x 512 image", "features": 5, "hidden": 32},
            "inference": {"ms": ms_inf, "cells_per_s": cells_inf / (ms_inf * 1e-3)},
            "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s", "frac": tf_inf / peak,
-                        "traffic": None, "kernel": "forward pass (two mma.sync implicit-GEMM convolutions + head), "
+                        "traffic": None, "kernel": "forward pass (5->32 convolution on mma.sync, 32->32 convolution "
+                                                   "on tcgen05.mma with a tensor-memory accumulator, head), "
                                                    "512 x 512 cells", "peak_source": src,
                         "flops_model": "%d flops per cell (2 x 32 x 45 + 2 x 32 x 288 + 2 x 32)" % f_fwd},
            "train_tflops": cells_tr * f_train / (ms_train * 1e-3) / 1e12,
