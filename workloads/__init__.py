@@ -48,6 +48,28 @@ def sine_periodic(nx=32, ny=32, nv=16, vmax=6.0, eps=1e-2, steps=10, cfl=0.5,
                     eps=np.full_like(rho, eps), kin=np.ones(rho.shape, bool)))
 
 
+def sod_tube(nx=21, ny=150, nv=32, vmax=8.0, eps=1e-6, initial="fluid", switch="plain", t_end=0.15):
+    """Test 2 (Sec. 4.1.2): Sod data along y on [0, 0.1] x [0, 1], uniform
+    along x (periodic in x, outflow in y): (rho, u, p) = (1, 0, 1) for
+    y <= 0.5, (1/8, 0, 1/32) above; T = p / rho.  eps = 1e-6, plain switch
+    with eta = eps, delta = 1e-3, all cells macroscopic at t = 0 (initial =
+    'fluid'; 'kinetic' for the full kinetic run).  dt = t_end / steps with
+    steps = ceil(t_end / (0.8 min(dx, dy) / vmax)): at most the rule's value."""
+    X, Y = _centres(nx, ny, 0, 0.1, 0, 1)
+    left = Y <= 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 1.0 / 32.0)
+    z = np.zeros_like(rho)
+    dx, dy = 0.1 / nx, 1.0 / ny
+    steps = int(np.ceil(t_end / (0.8 * min(dx, dy) / vmax)))
+    kin = np.zeros(rho.shape, bool) if initial == "fluid" else np.ones(rho.shape, bool)
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=0.0, x1=0.1, y0=0.0, y1=1.0, bc_x="periodic", bc_y="outflow"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS, switch=switch), scheme="ars233",
+        dt=t_end / steps, steps=steps,
+        fields=dict(rho=rho, ux=z, uy=z.copy(), T=p / rho, eps=np.full_like(rho, eps), kin=kin))
+
+
 def riemann_quadrants(nx=128, ny=128, nv=32, vmax=8.0, seed=0, steps=200, cfl=0.5,
                       t_range=(0.25, 3.0), scheme="ars233", initial="fluid"):
     """Coupled ES-BGK/Euler four-quadrant 2-D Riemann data on [0,1]^2, outflow.
