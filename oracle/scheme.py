@@ -13,7 +13,7 @@ import numpy as np
 
 from .kinetic import (velocity_grid, moments, cons_from_moments, cons_from_prim,
                       prim_from_cons, maxwellian_hat, es_gaussian_of, relax)
-from .transport import pad_cells, kinetic_transport, euler_phi
+from .transport import pad_cells, kinetic_transport, kinetic_face_fluxes, flux_moments, euler_phi
 
 
 @dataclass(frozen=True)
@@ -29,6 +29,12 @@ class Problem:
         criteria of Sec. 3.1.2 before every step (Algorithm 1).
     coupling: 'stage' couples at every stage (Algorithm 1), 'step' only at the
         end of the step (the LOC-hybrid of Sec. 3.5).
+    interface: 'own' -- every cell uses its own model's flux (Reading R11);
+        'conservative' -- at a face between a kinetic and a fluid cell the
+        fluid cell's Euler update takes the moments (1, v, |v|^2/2) of the
+        kinetic cell's numerical flux through that face, so that what leaves
+        one side enters the other and the totals are conserved (Sec. 3.5
+        states conservation without giving an interface flux; Reading R22).
     """
     nx: int
     ny: int
@@ -47,6 +53,7 @@ class Problem:
     cweno_eps: float = 1e-6
     switch: str = "frozen"
     coupling: str = "stage"
+    interface: str = "own"
 
     @property
     def dx(self):
@@ -226,6 +233,23 @@ def convert(prob, st, new_kin):
     return State(f=f, U=U, kin=new_kin.copy(), eps=st.eps)
 
 
+def _interface_fluxes(prob, f, kin, v, w):
+    """Face-flux overrides of the conservative interface (Reading R22): the
+    moments of the kinetic numerical flux at every face with a kinetic cell on
+    one side and a fluid cell on the other (the faces i-1/2 of the ghost-padded
+    map, as in the transport).  f must hold f in the kinetic and buffer cells,
+    which cover the stencils of those faces."""
+    Fx, Fy = kinetic_face_fluxes(f, v, prob.bc_x, prob.bc_y, prob.cweno_eps)
+    out = []
+    for F, axis, bc in ((Fx, 1, prob.bc_x), (Fy, 0, prob.bc_y)):
+        k = pad_cells(kin, axis, bc, n=1)
+        n = kin.shape[axis]
+        left = np.take(k, np.arange(0, n + 1), axis=axis)
+        right = np.take(k, np.arange(1, n + 2), axis=axis)
+        out.append((flux_moments(F, v, w), left != right))
+    return tuple(out)
+
+
 def advance(prob, st, dt, tab):
     """One step of Algorithm 1 with the regime map held fixed.
 
@@ -286,7 +310,10 @@ def advance(prob, st, dt, tab):
             U_i[:, kin] = U_n[:, kin]
             f_i[buf] = f_n[buf]
         Ls.append(kinetic_transport(f_i, v, *args))
-        Phis.append(euler_phi(U_i, *args))
+        if prob.interface == "conservative" and kin.any() and not kin.all():
+            Phis.append(euler_phi(U_i, *args, override=_interface_fluxes(prob, f_i, kin, v, w)))
+        else:
+            Phis.append(euler_phi(U_i, *args))
         Qs.append(Q_i)
 
     f_new = st.f.copy()

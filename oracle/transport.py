@@ -104,6 +104,19 @@ def _divergence(F, axis, h):
             - np.take(F, np.arange(0, n), axis=axis)) / h
 
 
+def kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w):
+    """The numerical fluxes of the kinetic transport at every face: Fx at the
+    faces i-1/2 (i = 0..nx) along x, Fy at j-1/2 along y, per velocity node
+    (the F of kinetic_transport, whose divergence is L(f))."""
+    vx = v[None, None, None, :]
+    vy = v[None, None, :, None]
+    qm, qp = _face_states(f, 1, bc_x, eps_w)
+    Fx = 0.5 * vx * (qm + qp) - 0.5 * np.abs(vx) * (qp - qm)
+    qm, qp = _face_states(f, 0, bc_y, eps_w)
+    Fy = 0.5 * vy * (qm + qp) - 0.5 * np.abs(vy) * (qp - qm)
+    return Fx, Fy
+
+
 def kinetic_transport(f, v, dx, dy, bc_x, bc_y, eps_w):
     """L(f), the discretisation of v . grad_x f (Eq. semidiscrete ES-BGK).
 
@@ -111,13 +124,17 @@ def kinetic_transport(f, v, dx, dy, bc_x, bc_y, eps_w):
     Lax-Friedrichs flux with the exact local speed,
     F = 1/2 v (q^- + q^+) - 1/2 |v| (q^+ - q^-), then L = dF/dx + dG/dy.
     """
-    vx = v[None, None, None, :]
-    vy = v[None, None, :, None]
-    qm, qp = _face_states(f, 1, bc_x, eps_w)
-    Fx = 0.5 * vx * (qm + qp) - 0.5 * np.abs(vx) * (qp - qm)
-    qm, qp = _face_states(f, 0, bc_y, eps_w)
-    Fy = 0.5 * vy * (qm + qp) - 0.5 * np.abs(vy) * (qp - qm)
+    Fx, Fy = kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w)
     return _divergence(Fx, 1, dx) + _divergence(Fy, 0, dy)
+
+
+def flux_moments(F, v, w):
+    """Moments w sum F (1, v_x, v_y, |v|^2/2) of a face flux per velocity node
+    (F: (..., nv, nv) indexed [vy, vx]); the conserved-variable flux it
+    carries."""
+    VX, VY = np.meshgrid(v, v)
+    psi = np.stack([np.ones_like(VX), VX, VY, 0.5 * (VX * VX + VY * VY)])
+    return w * np.einsum("...ab,qab->q...", F, psi)
 
 
 def euler_flux(U, d):
@@ -133,19 +150,25 @@ def euler_flux(U, d):
                      un * (E + P)]), np.abs(un) + np.sqrt(GAMMA * P / rho)
 
 
-def euler_phi(U, dx, dy, bc_x, bc_y, eps_w):
+def euler_phi(U, dx, dy, bc_x, bc_y, eps_w, override=None):
     """Phi(U), the discretisation of div_x F(U) (Eq. semidiscrete Euler).
 
     U: (4, ny, nx).  Component-wise CWENO3 face states and the local
     Lax-Friedrichs flux  F = 1/2 (F(U^-) + F(U^+)) - 1/2 a (U^+ - U^-),
     a = max over the two states of |u_n| + sqrt(gamma P / rho).
+    override: None, or ((Gx, mask_x), (Gy, mask_y)) -- face fluxes (4, ny,
+    nx+1) / (4, ny+1, nx) that replace the Euler flux where the boolean face
+    mask is set.
     """
     out = np.zeros_like(U)
-    for d, axis, h, bc in ((0, 2, dx, bc_x), (1, 1, dy, bc_y)):
+    for k, (d, axis, h, bc) in enumerate(((0, 2, dx, bc_x), (1, 1, dy, bc_y))):
         Um, Up = _face_states(U, axis, bc, eps_w)
         Fm, am = euler_flux(Um, d)
         Fp, ap = euler_flux(Up, d)
         a = np.maximum(am, ap)
         F = 0.5 * (Fm + Fp) - 0.5 * a[None] * (Up - Um)
+        if override is not None:
+            G, mask = override[k]
+            F = np.where(mask[None], G, F)
         out += _divergence(F, axis, h)
     return out

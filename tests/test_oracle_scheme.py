@@ -7,6 +7,8 @@ import os
 import numpy as np
 import pytest
 
+from dataclasses import replace
+
 import oracle as O
 import workloads as W
 
@@ -67,6 +69,56 @@ def test_periodic_single_model_conserves(kin_mode):
         st = O.step(prob, st, 2e-3, O.ARS233)
     t1 = O.totals(prob, st)
     assert np.allclose(t0, t1, rtol=0, atol=1e-13 * np.abs(t0).max())
+
+
+@pytest.mark.parametrize("coupling", ["stage", "step"])
+def test_conservative_interface_conserves_hybrid_totals(coupling):
+    """Reading R22: with the kinetic flux's moments on both sides of every
+    kinetic/fluid face, a periodic hybrid (random frozen map, flowing data)
+    conserves mass, momentum and energy to round-off, as the single-model runs
+    do; with each model's own flux (Reading R11) the same run drifts by orders
+    of magnitude more."""
+    prob = O.Problem(nx=12, ny=10, nv=12, vmax=6.0, switch="frozen", coupling=coupling)
+    rho, ux, uy, T = _random_kinetic_state(prob, 1)
+    kin = np.random.default_rng(3).random(rho.shape) < 0.5
+    drift = {}
+    for iface in ("own", "conservative"):
+        P = replace(prob, interface=iface)
+        st = O.init_state(P, rho, ux, uy, T, np.full_like(rho, 1e-2), kin)
+        t0 = O.totals(P, st)
+        for _ in range(3):
+            st = O.step(P, st, 2e-3, O.ARS233)
+        drift[iface] = np.abs(O.totals(P, st) - t0).max() / np.abs(t0).max()
+    assert drift["conservative"] <= 1e-13, drift
+    assert drift["own"] >= 1e4 * max(drift["conservative"], 1e-16), drift
+
+
+def test_conservative_interface_changes_nothing_without_interfaces():
+    """All-kinetic and all-fluid maps have no kinetic/fluid face: the two
+    interface readings give bit-identical steps."""
+    prob = O.Problem(nx=8, ny=6, nv=8, vmax=6.0, switch="frozen")
+    rho, ux, uy, T = _random_kinetic_state(prob, 2)
+    for k in (True, False):
+        kin = np.full(rho.shape, k)
+        out = []
+        for iface in ("own", "conservative"):
+            P = replace(prob, interface=iface)
+            out.append(O.step(P, O.init_state(P, rho, ux, uy, T, np.full_like(rho, 1e-2), kin), 2e-3, O.ARS233))
+        assert np.array_equal(out[0].U, out[1].U) and np.array_equal(out[0].f, out[1].f)
+
+
+def test_flux_moments_of_a_maxwellian_face_flux():
+    """The moments of the free-streaming flux v_x M of a Maxwellian with
+    u = 0 on a symmetric fine velocity grid: the mass and x-energy fluxes
+    vanish, the x-momentum flux is the pressure rho T (Sec. 2, gamma = 2)."""
+    from oracle.transport import flux_moments
+    v, w = O.velocity_grid(64, 10.0)
+    rho, T = 1.3, 0.7
+    VX, VY = np.meshgrid(v, v)
+    M = rho / (2 * np.pi * T) * np.exp(-(VX ** 2 + VY ** 2) / (2 * T))
+    G = flux_moments((VX * M)[None], v, w)[:, 0]
+    assert abs(G[0]) < 1e-12 and abs(G[2]) < 1e-12 and abs(G[3]) < 1e-12
+    assert abs(G[1] - rho * T) < 1e-10
 
 
 @pytest.mark.parametrize("kin_fraction", [1.0, 0.0, 0.5])
