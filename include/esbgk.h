@@ -55,6 +55,7 @@ typedef enum { ESBGK_FP64 = 0, ESBGK_FP32 = 1, ESBGK_BF16 = 2 } esbgk_prec;
 typedef enum { ESBGK_BC_PERIODIC = 0, ESBGK_BC_OUTFLOW = 1 } esbgk_bc;
 typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1, ESBGK_SWITCH_LEARNED = 2 } esbgk_switch;
 typedef enum { ESBGK_COUPLE_STAGE = 0, ESBGK_COUPLE_STEP = 1 } esbgk_coupling;
+typedef enum { ESBGK_INTERFACE_OWN = 0, ESBGK_INTERFACE_CONSERVATIVE = 1 } esbgk_interface;
 
 /* Cartesian grid of Sec. 3.2: N_x x N_y cells on [x0,x1] x [y0,y1]; two ghost
  * cells per side, periodic or outflow (copy of the edge cell). */
@@ -84,10 +85,17 @@ typedef struct {
  *             STEP only at step end (the LOC-hybrid of Sec. 3.5).
  *  prec       esbgk_prec of f storage and per-element arithmetic: FP64; FP32;
  *             BF16 storage with FP32 arithmetic.  Per-cell tensor solves,
- *             U and the totals are always FP64. */
+ *             U and the totals are always FP64.
+ *  interface_flux  esbgk_interface: OWN -- at a face between a kinetic and a
+ *             fluid cell each cell uses its own model's flux (Sec. 3.5 gives
+ *             no interface flux; the totals then drift at the interfaces);
+ *             CONSERVATIVE -- the fluid cell's Euler update takes, at that
+ *             face, the moments (1, v, |v|^2/2) of the kinetic numerical flux
+ *             the kinetic cell uses, so that mass, momentum and energy are
+ *             conserved to rounding.  Zero-initialised structs get OWN. */
 typedef struct {
   double beta, tau, eta_factor, delta, cweno_eps;
-  int32_t sw, coupling, prec;
+  int32_t sw, coupling, prec, interface_flux;
 } esbgk_params;
 
 /* IMEX tableaux (Sec. 3.4), 2 <= s <= 4 stages: explicit (At, bt) for the

@@ -101,6 +101,7 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   if (!(p->eta_factor >= 0) || !(p->delta >= 0)) return false;
   if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN && p->sw != ESBGK_SWITCH_LEARNED) return false;
   if (p->coupling != ESBGK_COUPLE_STAGE && p->coupling != ESBGK_COUPLE_STEP) return false;
+  if (p->interface_flux != ESBGK_INTERFACE_OWN && p->interface_flux != ESBGK_INTERFACE_CONSERVATIVE) return false;
   return launchers_for(p->prec) != nullptr;
 }
 
@@ -143,7 +144,7 @@ Geo make_geo(const esbgk_grid* g, const esbgk_vmesh* v) {
 struct esbgk_ctx {
   Geo g;
   Model m;
-  int prec, sw, coupling;
+  int prec, sw, coupling, iface;
   const Launchers* L;
   cudaStream_t stream;
   int grid_stage, grid_red;
@@ -454,6 +455,7 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.nphi = i;
     for (int j = 0; j < i; ++j) A.phi_coef[j] = dt * T_(T, i, j);
     A.hoc = X->coupling == ESBGK_COUPLE_STAGE ? 1 : 0;
+    A.iface = X->iface == ESBGK_INTERFACE_CONSERVATIVE ? 1 : 0;
     A.fill = (last && shortcut) ? 0 : 1;
     A.kin_u_moments = (A.hoc || (last && shortcut)) ? 1 : 0;
     A.ctr = X->ctr;
@@ -482,6 +484,7 @@ int plan_step(esbgk_ctx* X, double dt, const esbgk_tableau* T, StepPlan& PL) {
     A.nphi = s;
     for (int j = 0; j < s; ++j) A.phi_coef[j] = dt * T->bt[j];
     A.hoc = 1;
+    A.iface = X->iface == ESBGK_INTERFACE_CONSERVATIVE ? 1 : 0;
     A.fill = 0;
     A.kin_u_moments = 1;
     A.ctr = X->ctr;
@@ -693,6 +696,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->prec = params->prec;
   X->sw = params->sw;
   X->coupling = params->coupling;
+  X->iface = params->interface_flux;
   X->L = L;
   X->stream = (cudaStream_t)stream;
   unsigned char* w = (unsigned char*)workspace;
@@ -1700,6 +1704,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.prec = params->prec;
   X.sw = ESBGK_SWITCH_FROZEN;
   X.coupling = ESBGK_COUPLE_STAGE;
+  X.iface = ESBGK_INTERFACE_OWN;
   X.L = L;
   X.stream = (cudaStream_t)stream;
   X.grid_stage = nsm * L->blocks_per_sm(g);

@@ -454,8 +454,11 @@ ESBGK_DEV void euler_phys(const R (&U)[4], int d, R (&F)[4], R& a) {
 
 // Phi(U)(c): CWENO3 face states per component, local Lax-Friedrichs flux at
 // the four faces of the cell, divergence (Eq. semidiscrete Euler).
+// ovr/omask: faces whose flux is given (bit 2d: the face -1/2 along axis d,
+// bit 2d+1: the face +1/2; ovr[bit][component]).
 template <typename R>
-ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c, R epsw, R (&phi)[4]) {
+ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c, R epsw, R (&phi)[4],
+                              const R (*ovr)[4] = nullptr, int omask = 0) {
   const int i = c % g.nx, j = c / g.nx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) phi[q] = R(0);
@@ -487,8 +490,10 @@ ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c,
     const R ih = R(1) / (R)(d == 0 ? g.dx : g.dy);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const R Fm = R(0.5) * (FLm[m] + FRm[m]) - R(0.5) * am * (Rm[m] - Lm[m]);
-      const R Fp = R(0.5) * (FLp[m] + FRp[m]) - R(0.5) * ap * (Rp[m] - Lp[m]);
+      R Fm = R(0.5) * (FLm[m] + FRm[m]) - R(0.5) * am * (Rm[m] - Lm[m]);
+      R Fp = R(0.5) * (FLp[m] + FRp[m]) - R(0.5) * ap * (Rp[m] - Lp[m]);
+      if (omask & (1 << (2 * d))) Fm = ovr[2 * d][m];
+      if (omask & (2 << (2 * d))) Fp = ovr[2 * d + 1][m];
       phi[m] += (Fp - Fm) * ih;
     }
   }
@@ -497,11 +502,12 @@ ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c,
 // U^(i)(c) = U^n(c) - sum_j coef_j Phi_j(c) for a fluid cell, after storing
 // Phi_{i-1}(c) when requested (Eqs. RKEuler, RKEuler_2).
 template <typename R>
-ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)[4]) {
+ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)[4], const R (*ovr)[4] = nullptr,
+                          int omask = 0) {
   const size_t nc = V.g.nc;
   if (A.phi_store >= 0) {
     R phi[4];
-    euler_phi_cell<R>(V.g, A.U_prev, c, pick<R>(V.m.eps_w, V.m.feps_w), phi);
+    euler_phi_cell<R>(V.g, A.U_prev, c, pick<R>(V.m.eps_w, V.m.feps_w), phi, ovr, omask);
 #pragma unroll
     for (int m = 0; m < 4; ++m) A.Phi[((size_t)A.phi_store * 4 + m) * nc + c] = (double)phi[m];
   }
@@ -512,6 +518,64 @@ ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)
     A.U_out[m * nc + c] = u;
     Uc[m] = u;
   }
+}
+
+// Moments w sum F (1, v_x, v_y, |v|^2/2) of the kinetic numerical flux
+// through the face between cells a (low side) and b (high side) along axis d
+// (am below a, bp above b): F = v_d times the upwind CWENO3 face value, the
+// right face of a for v_d > 0 and the left face of b for v_d < 0 -- the same
+// face values, from the same arguments, as the kinetic cell's transport.
+// Warp-wide, one node per lane and iteration; every lane returns the sums.
+template <typename S>
+ESBGK_DEV void face_flux_moments(const S* __restrict__ f, const Geo& g, const Model& mdl, int am, int a, int b,
+                                 int bp, int d, int lane, typename Real<S>::T (&G)[4]) {
+  using R = typename Real<S>::T;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv), epsw = pick<R>(mdl.eps_w, mdl.feps_w);
+  const size_t n = g.nvv;
+  const S *fam = f + (size_t)am * n, *fa = f + (size_t)a * n, *fb = f + (size_t)b * n, *fbp = f + (size_t)bp * n;
+  R s[4] = {R(0), R(0), R(0), R(0)};
+  NodeIter<R> it(lane, g.nv, v0, dv);
+#pragma unroll 1
+  for (; it.k < g.nvv; it.next()) {
+    const unsigned k = it.k;
+    const R vx = it.vx(), vy = it.vy(), vn = d == 0 ? vx : vy;
+    const R q = vn > R(0) ? cweno_face(ld(fam + k), ld(fa + k), ld(fb + k), epsw)
+                          : cweno_face(ld(fbp + k), ld(fb + k), ld(fa + k), epsw);
+    const R F = vn * q;
+    s[0] += F;
+    s[1] += F * vx;
+    s[2] += F * vy;
+    s[3] += F * R(0.5) * (vx * vx + vy * vy);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) G[m] = warp_sum(s[m]) * pick<R>(g.w, g.fw);
+}
+
+// Conservative interface of buffer cell c (StageArgs::iface): the kinetic
+// flux moments at each face of c shared with a kinetic cell, computed from
+// f_src (f of the previous stage; filled in buffer cells, so every stencil
+// cell holds f).  Returns the face mask of euler_phi_cell.  Warp-wide.
+template <typename S>
+ESBGK_DEV int interface_fluxes(const StageArgs& A, const View& V, int c, int lane,
+                               typename Real<S>::T (&ovr)[4][4]) {
+  const Geo& g = V.g;
+  const S* f = (const S*)A.f_src;
+  const int i = c % g.nx, j = c / g.nx;
+  int mask = 0;
+#pragma unroll 1
+  for (int face = 0; face < 4; ++face) {
+    const int d = face >> 1, up = face & 1;  // axis; the face above (+1/2) or below (-1/2) c
+    auto cell = [&](int off) {
+      return d == 0 ? j * g.nx + nb(i + off, g.nx, g.bcx) : nb(j + off, g.ny, g.bcy) * g.nx + i;
+    };
+    const int other = cell(up ? 1 : -1);
+    if (other == c || !V.flags[other]) continue;
+    // the face between a (low side) and b (high side)
+    const int lo = up ? 0 : -1;
+    face_flux_moments<S>(f, g, V.m, cell(lo - 1), cell(lo), cell(lo + 1), cell(lo + 2), d, lane, ovr[face]);
+    mask |= 1 << face;
+  }
+  return mask;
 }
 
 // Primitive variables of U (Sec. 2): u = m/rho, T = (E - rho |u|^2/2)/rho.
@@ -1122,7 +1186,9 @@ template <typename S, int W = 1>
 ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
   using R = typename Real<S>::T;
   double Uc[4] = {0, 0, 0, 0};
-  if (lane == 0) euler_cell<R>(A, V, c, Uc);
+  R ovr[4][4];
+  const int omask = (A.iface && A.f_src && A.phi_store >= 0) ? interface_fluxes<S>(A, V, c, lane, ovr) : 0;
+  if (lane == 0) euler_cell<R>(A, V, c, Uc, ovr, omask);
   buffer_fill<S, W>(A, V, c, lane, Uc);
 }
 
@@ -1174,7 +1240,10 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       const int q = (u - nKu - nB) * 32 + lane;
       const int ec = buf ? (lane == 0 ? V.blist[u - nKu] : -1) : (q < nF ? V.flist[q] : -1);
       double Uc[4] = {0, 0, 0, 0};
-      if (ec >= 0) euler_cell<R>(A, V, ec, Uc);
+      R ovr[4][4];
+      const int omask =
+          (buf && A.iface && A.f_src && A.phi_store >= 0) ? interface_fluxes<S>(A, V, V.blist[u - nKu], lane, ovr) : 0;
+      if (ec >= 0) euler_cell<R>(A, V, ec, Uc, ovr, omask);
       if (buf) {
         buffer_fill<S, W>(A, V, V.blist[u - nKu], lane, Uc);
         fills += A.fill ? 1 : 0;

@@ -56,6 +56,8 @@ struct StageArgs {
   int hoc;
   int fill;
   int kin_u_moments;
+  int iface;  // conservative interface: a buffer cell's Euler flux at a face with a kinetic neighbour is the
+              // moments of the kinetic numerical flux there (computed from f_src)
   long long* ctr;
   double* l1_out;  // when set (final combination only): ||f - M_hat[f]||_L1 of the result per kinetic cell
   int* wq;         // work counter of the launch (zeroed by the step's prep): units past the first wave are
