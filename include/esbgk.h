@@ -45,7 +45,7 @@ typedef enum {
   ESBGK_E_CUDA = -3,           /* a CUDA runtime call failed; see esbgk_last_error   */
   ESBGK_E_NONREALIZABLE = -4,  /* rho <= 0, T <= 0, det(temperature tensor) <= 0 or a
                                   singular moment system in some cell                */
-  ESBGK_E_TIMEOUT = -5,        /* a bounded device wait (tensor cores) expired      */
+  ESBGK_E_TIMEOUT = -5,        /* a bounded device wait expired                     */
   ESBGK_E_STATE = -6,          /* call out of order (e.g. step before set_state)    */
   ESBGK_E_TOO_LARGE = -7       /* problem exceeds the fixed scratch of
                                   esbgk_kinetic_steps_noalloc                        */
@@ -177,6 +177,19 @@ int esbgk_step(esbgk_ctx* ctx, double dt, const esbgk_tableau* tab);
 /* Enable (default) or disable graph replay in esbgk_step; drops the graphs
  * kept so far.  Synchronises the stream. */
 int esbgk_graphs(esbgk_ctx* ctx, int32_t enable);
+
+/* Probe of the library's bounded device waits (failure detection without a
+ * fault): launches one CTA on `stream` (NULL: the legacy default stream) that
+ * waits on a shared-memory barrier with the same bounded poll loop the kernels
+ * use, limited to `polls` polls (1 .. 2^20; each poll may suspend the thread
+ * for a hardware-defined time), and synchronises the stream.  arrive != 0: the
+ * barrier receives its arrival and the call returns ESBGK_OK; arrive = 0: the
+ * arrival is withheld, the wait runs out, the kernel records the timeout in a
+ * device error word and returns normally, and the call returns
+ * ESBGK_E_TIMEOUT.  The CUDA context stays usable either way.  No device
+ * memory is allocated (the word is a static device variable); ESBGK_E_ARG for
+ * polls out of range, ESBGK_E_CUDA if the launch fails. */
+int esbgk_wait_probe(int32_t arrive, int32_t polls, void* stream);
 
 /* Per-cell form the specialised stage launches of this context take (the
  * ARS(2,3,3) and IMEX-Euler stages): nodes per vector group along v_x (1:

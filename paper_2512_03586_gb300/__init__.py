@@ -502,3 +502,14 @@ def relax_cells(fstar, h, vmax, beta=-0.5, prec="fp64", stream=None):
     if r != 0:
         raise Error(r, "esbgk_relax_cells")
     return f, g
+
+
+def wait_probe(arrive, polls=1 << 12, stream=None):
+    """esbgk_wait_probe: one CTA waits on a barrier with the library's bounded
+    wait; arrive=False withholds the arrival.  Returns the status code (0 =
+    OK; -5 = E_TIMEOUT when the wait ran out) -- failure detection without a
+    GPU fault."""
+    import torch
+    _abi = _lib()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(_abi.esbgk_wait_probe(int(bool(arrive)), int(polls), ctypes.c_void_p(st.cuda_stream)))

@@ -90,6 +90,7 @@ _SIGS = {
     "esbgk_counters": (I, [P, LL, LL, LL, LL]),
     "esbgk_graphs": (I, [P, ctypes.c_int32]),
     "esbgk_kinetic_form": (I, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_wait_probe": (I, [ctypes.c_int32, ctypes.c_int32, P]),
     "esbgk_timing": (I, [P, I]),
     "esbgk_timing_read": (I, [P, D, LL, ctypes.c_int32]),
     "esbgk_sync": (I, [P]),

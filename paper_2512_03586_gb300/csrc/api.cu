@@ -285,7 +285,8 @@ int sync_and_check(esbgk_ctx* X) {
   if (r) return r;
   if (e.code == kErrTimeout) {
     X->bad_cell = -1;
-    return fail(X, ESBGK_E_TIMEOUT, "bounded wait for the tensor cores (learned switch) expired");
+    return fail(X, ESBGK_E_TIMEOUT,
+                "a bounded device wait expired (tensor-core commit of the learned-switch network)");
   }
   if (e.code != 0) {
     X->bad_cell = e.cell;
@@ -1018,6 +1019,14 @@ int esbgk_kinetic_form(const esbgk_ctx* X, int32_t* nodes_per_group, int32_t* ce
   if (nodes_per_group) *nodes_per_group = w;
   if (cells_per_warp) *cells_per_warp = variant_pairs(v) ? 2 : 1;
   return ESBGK_OK;
+}
+
+int esbgk_wait_probe(int32_t arrive, int32_t polls, void* stream) {
+  if (polls < 1 || polls > (int32_t)kWaitLimit) return ESBGK_E_ARG;
+  int err = 0;
+  if (launch_wait_probe(arrive != 0, (unsigned)polls, &err, (cudaStream_t)stream) != cudaSuccess)
+    return ESBGK_E_CUDA;
+  return err == kErrTimeout ? ESBGK_E_TIMEOUT : ESBGK_OK;
 }
 
 int esbgk_timing(esbgk_ctx* X, int enable) {

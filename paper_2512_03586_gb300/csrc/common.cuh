@@ -92,8 +92,8 @@ ESBGK_DEV bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
 // Wait for the phase of the given parity to complete, giving up after a
 // bounded number of polls (false: it did not complete).
 constexpr unsigned kWaitLimit = 1u << 20;
-ESBGK_DEV bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
+ESBGK_DEV bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned limit = kWaitLimit) {
+  for (unsigned it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

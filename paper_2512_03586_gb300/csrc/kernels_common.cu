@@ -475,4 +475,35 @@ void launch_batch_seed_advance(const CasePrep* cases, int n, cudaStream_t s) {
   batch_seed_kernel<<<1, 128, 0, s>>>(cases, n);
 }
 
+// ---------------------------------------------------------------------------
+// Probe of the bounded device waits: one CTA waits on a shared-memory barrier
+// with the library's bounded wait; arrive = 0 leaves the barrier without its
+// arrival, so the wait runs out and records kErrTimeout in the word.
+__device__ int g_wait_probe_err;
+
+__global__ void wait_probe_kernel(int arrive, unsigned limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    g_wait_probe_err = 0;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) {
+      unsigned long long state;
+      asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&bar)) : "memory");
+    }
+    if (!mbar_wait(&bar, 0, limit)) g_wait_probe_err = kErrTimeout;
+  }
+}
+
+cudaError_t launch_wait_probe(int arrive, unsigned limit, int* err_out, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(arrive, limit);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(err_out, g_wait_probe_err, sizeof(int));
+  return e;
+}
+
 }  // namespace esbgk

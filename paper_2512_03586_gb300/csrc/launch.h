@@ -232,6 +232,9 @@ void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_
                                int* block_counts, int* klist, int* blist, int* flist, int* clist, int* counts,
                                cudaStream_t s);
 int categorize_blocks(int nc);
+// One CTA waiting on a barrier with the bounded wait (limit polls); arrive = 0
+// withholds the arrival.  *err_out: 0, or kErrTimeout when the wait ran out.
+cudaError_t launch_wait_probe(int arrive, unsigned limit, int* err_out, cudaStream_t s);
 void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
 // advance the step counter of the stochastic rounding (one thread)
 void launch_seed_advance(unsigned* seed, cudaStream_t s);
