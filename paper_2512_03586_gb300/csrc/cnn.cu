@@ -255,6 +255,10 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
       if (tid == 0 && err) atomicCAS(err, 0, kErrTimeout);
+      // the MMAs may still be in flight: wait for them once more (bounded)
+      // before the tensor memory they write is freed below
+      __syncthreads_and(mbar_wait(&mbar, phase));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       break;
     }
     // warp w reads tensor-memory lanes 32w..32w+31 (its cells), 32 columns (channels)
