@@ -32,7 +32,7 @@ from .kinetic import (velocity_grid, moments, macro_from_moments, gaussian,
                       projected_gaussian, maxwellian_hat, es_gaussian_of, relax,
                       cons_from_prim, prim_from_cons, cons_from_moments)
 from .transport import pad_cells, cweno3_faces, cweno3_indicators, kinetic_transport, euler_phi, euler_flux
-from .scheme import (Problem, State, ARS233, IMEX_EULER, Tableau, init_state,
+from .scheme import (Problem, State, ARS233, IMEX_EULER, ARS222, SSP2_332, Tableau, init_state,
                      regime_indicators, regime_update, convert, buffer_mask,
                      advance, step, totals, macro)
 from . import cnn

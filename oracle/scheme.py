@@ -104,6 +104,21 @@ ARS233 = Tableau(
 #: f^{n+1} = relax(f^n - dt L(f^n)).
 IMEX_EULER = Tableau(At=np.array([[0.0, 0.0], [1.0, 0.0]]), bt=np.array([1.0, 0.0]),
                      A=np.array([[0.0, 0.0], [0.0, 1.0]]), b=np.array([0.0, 1.0]))
+#: Other second-order IMEX tableaux (Sec. 3.4 admits any IMEX-RK pair):
+#: ARS(2,2,2) of Ascher, Ruuth and Spiteri (1997), gamma = 1 - 1/sqrt(2),
+#: delta = 1 - 1/(2 gamma), first stage explicit, L-stable implicit part.
+_g = 1.0 - 1.0 / np.sqrt(2.0)
+_d = 1.0 - 1.0 / (2.0 * _g)
+ARS222 = Tableau(At=np.array([[0.0, 0.0, 0.0], [_g, 0.0, 0.0], [_d, 1.0 - _d, 0.0]]),
+                 bt=np.array([_d, 1.0 - _d, 0.0]),
+                 A=np.array([[0.0, 0.0, 0.0], [0.0, _g, 0.0], [0.0, 1.0 - _g, _g]]),
+                 b=np.array([0.0, 1.0 - _g, _g]))
+#: IMEX-SSP2(3,3,2) of Pareschi and Russo (2005): SSP explicit part, implicit
+#: first stage (a_11 = 1/4), stiffly accurate implicit part.
+SSP2_332 = Tableau(At=np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.5, 0.5, 0.0]]),
+                   bt=np.array([1.0, 1.0, 1.0]) / 3.0,
+                   A=np.array([[0.25, 0.0, 0.0], [0.0, 0.25, 0.0], [1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0]]),
+                   b=np.array([1.0, 1.0, 1.0]) / 3.0)
 
 
 def _vgrid(prob):

@@ -50,11 +50,19 @@ ARS233 = dict(
     b=[0.0, 0.5, 0.5])
 #: First-order IMEX (Filbet-Jin) in ARS(1,1,1) form: f^{n+1} = relax(f^n - dt L(f^n)).
 IMEX_EULER = dict(At=[[0.0, 0.0], [1.0, 0.0]], bt=[1.0, 0.0], A=[[0.0, 0.0], [0.0, 1.0]], b=[0.0, 1.0])
-TABLEAUX = {"ars233": ARS233, "imex_euler": IMEX_EULER}
+#: Second-order pairs: ARS(2,2,2) (Ascher, Ruuth, Spiteri 1997; gamma = 1 - 1/sqrt 2,
+#: delta = 1 - 1/(2 gamma)) and IMEX-SSP2(3,3,2) (Pareschi, Russo 2005; implicit first stage).
+_GAMMA = 1.0 - 2.0 ** -0.5
+_DELTA = 1.0 - 0.5 / _GAMMA
+ARS222 = dict(At=[[0.0, 0.0, 0.0], [_GAMMA, 0.0, 0.0], [_DELTA, 1.0 - _DELTA, 0.0]], bt=[_DELTA, 1.0 - _DELTA, 0.0],
+              A=[[0.0, 0.0, 0.0], [0.0, _GAMMA, 0.0], [0.0, 1.0 - _GAMMA, _GAMMA]], b=[0.0, 1.0 - _GAMMA, _GAMMA])
+SSP2_332 = dict(At=[[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.5, 0.5, 0.0]], bt=[1.0 / 3.0] * 3,
+                A=[[0.25, 0.0, 0.0], [0.0, 0.25, 0.0], [1.0 / 3.0] * 3], b=[1.0 / 3.0] * 3)
+TABLEAUX = {"ars233": ARS233, "imex_euler": IMEX_EULER, "ars222": ARS222, "ssp2_332": SSP2_332}
 
 
 def make_tableau(t):
-    """esbgk_tableau from a name ('ars233', 'imex_euler') or a dict At, bt, A, b."""
+    """esbgk_tableau from a name ('ars233', 'imex_euler', 'ars222', 'ssp2_332') or a dict At, bt, A, b."""
     if isinstance(t, str):
         t = TABLEAUX[t]
     At, A = np.asarray(t["At"], float), np.asarray(t["A"], float)

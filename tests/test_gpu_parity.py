@@ -50,7 +50,7 @@ def f_error(f_gpu, f_ref, kin):
 
 
 def tableau_of(name):
-    return {"ars233": O.ARS233, "imex_euler": O.IMEX_EULER}[name]
+    return {"ars233": O.ARS233, "imex_euler": O.IMEX_EULER, "ars222": O.ARS222, "ssp2_332": O.SSP2_332}[name]
 
 
 def run_parity(wl, steps, prec="fp64", check_f=True, **over):

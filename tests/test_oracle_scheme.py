@@ -40,6 +40,41 @@ def test_ars233_satisfies_printed_coupled_order_conditions():
         assert np.isclose(np.sum(b * c1 * c2), 1.0 / 3.0)
 
 
+@pytest.mark.parametrize("name", ["ARS222", "SSP2_332"])
+def test_second_order_pairs_satisfy_coupled_conditions(name):
+    """The other IMEX pairs: every coupled condition up to p = 2 holds
+    (b.1 = 1, b.c = 1/2 for each part and across parts), and the third-order
+    condition b.c^2 = 1/3 fails for at least one part (second order only);
+    explicit part strictly lower triangular, implicit part lower triangular."""
+    T = getattr(O, name)
+    c, ct = T.A.sum(1), T.At.sum(1)
+    assert np.allclose(np.triu(T.At), 0) and np.allclose(np.triu(T.A, 1), 0)
+    for b in (T.b, T.bt):
+        assert np.isclose(b.sum(), 1.0)
+        for cc in (c, ct):
+            assert np.isclose(b @ cc, 0.5)
+    assert not all(np.isclose(np.sum(b * cc * cc), 1.0 / 3.0) for b in (T.b, T.bt) for cc in (c, ct))
+
+
+@pytest.mark.parametrize("name", ["ARS222", "SSP2_332"])
+def test_second_order_pairs_converge_at_second_order(name):
+    """The coupled hybrid (Test 1 data, random frozen map, per-stage
+    coupling) with the second-order pairs: Richardson order of the finest
+    pair of step sizes within 0.3 of 2."""
+    T = getattr(O, name)
+    wl = W.order_test(n=12, nv=12, eps=1e-2)
+    P = _prob(wl)
+    sols = []
+    for k in (4, 8, 16, 32):
+        st = O.init_state(P, **wl["fields"])
+        for _ in range(k):
+            st = O.step(P, st, 0.2 / k, T)
+        sols.append(st.U[0].copy())
+    err = [np.sqrt(np.sum((a - b) ** 2)) for a, b in zip(sols[:-1], sols[1:])]
+    order = np.log2(err[-2] / err[-1])
+    assert abs(order - 2.0) <= 0.3, order
+
+
 def test_imex_euler_is_first_order_only():
     T = O.IMEX_EULER
     assert np.isclose(T.b.sum(), 1) and np.isclose(T.bt.sum(), 1)
