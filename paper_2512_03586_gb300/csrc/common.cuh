@@ -190,6 +190,29 @@ ESBGK_DEV R cweno_face(R a, R b, R c, R epsw) {
   return fdiv(a0 * P0 + aL * PL + aR * PR, a0 + aL + aR);
 }
 
+// Compensated summation of FP32 moments.  comp_add: Neumaier's variant of
+// Kahan summation (the rounding error of s + x, exact, kept in c; valid in
+// either magnitude order).  group_sum_comp: the butterfly over L lanes with
+// the error-free two-sum of the partial sums at every level, compensations
+// added alongside; the result is s + c, identical in every lane (two-sum's
+// error term does not depend on the operand order).
+ESBGK_DEV void comp_add(float& s, float& c, float x) {
+  const float t = s + x;
+  c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+template <int L>
+ESBGK_DEV float group_sum_comp(float s, float c, unsigned mask) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) {
+    const float so = __shfl_xor_sync(mask, s, o, L), co = __shfl_xor_sync(mask, c, o, L);
+    const float t = s + so, bp = t - s;
+    c += co + ((s - (t - bp)) + (so - bp));
+    s = t;
+  }
+  return s + c;
+}
+
 // The same face value for two independent stencils at once, on the paired
 // FP32 instructions of sm_100-family GPUs (two lanes of float arithmetic per
 // issued instruction); the divisions stay per component.
