@@ -490,10 +490,7 @@ __global__ void wait_probe_kernel(int arrive, unsigned limit) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (arrive) {
-      unsigned long long state;
-      asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&bar)) : "memory");
-    }
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
     if (!mbar_wait(&bar, 0, limit)) g_wait_probe_err = kErrTimeout;
   }
 }
