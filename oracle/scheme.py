@@ -29,6 +29,11 @@ class Problem:
         criteria of Sec. 3.1.2 before every step (Algorithm 1).
     coupling: 'stage' couples at every stage (Algorithm 1), 'step' only at the
         end of the step (the LOC-hybrid of Sec. 3.5).
+    tau_model: 'constant' -- tau fixed (Reading R2); 'density' -- tau = tau *
+        rho (Sec. 2.1 lets tau depend on the macroscopic moments; Reading
+        R23): the collision rate of a kinetic cell is nu = tau rho / eps with
+        the density of its f* at each stage (which the relaxation conserves),
+        and the criterion's mu and kappa use tau rho.
     interface: 'own' -- every cell uses its own model's flux (Reading R11);
         'conservative' -- at a face between a kinetic and a fluid cell the
         fluid cell's Euler update takes the moments (1, v, |v|^2/2) of the
@@ -54,6 +59,7 @@ class Problem:
     switch: str = "frozen"
     coupling: str = "stage"
     interface: str = "own"
+    tau_model: str = "constant"
 
     @property
     def dx(self):
@@ -209,8 +215,9 @@ def regime_indicators(prob, st):
     D = gu + np.swapaxes(gu, -1, -2) - (2.0 / 3.0) * div[..., None, None] * np.eye(2)
     gT = np.stack([ddx(T), ddy(T)], axis=-1)
     eps = st.eps
-    c1 = eps / (prob.tau * (1.0 - prob.beta))
-    c2 = (2.0 / 3.0) * (2.5 * eps / (prob.tau * np.sqrt(T))) ** 2
+    tau = prob.tau * rho if prob.tau_model == "density" else prob.tau
+    c1 = eps / (tau * (1.0 - prob.beta))
+    c2 = (2.0 / 3.0) * (2.5 * eps / (tau * np.sqrt(T))) ** 2
     X = c1[..., None, None] * D + c2[..., None, None] * gT[..., :, None] * gT[..., None, :]
     lamA = np.max(np.abs(np.linalg.eigvalsh(X)), axis=-1)
     L1 = np.zeros_like(rho)
@@ -308,14 +315,17 @@ def advance(prob, st, dt, tab):
             for j in range(i):
                 fstar -= dt * tab.At[i, j] * Ls[j][kin]
                 fstar += dt * tab.A[i, j] * Qs[j][kin]
+            # collision rate of the stage (Reading R23: with tau = tau rho, the
+            # density of f*, equal to that of f^(i))
+            nu_i = nu[kin] * (_U_of_f(prob, fstar)[0] if prob.tau_model == "density" else 1.0)
             if tab.A[i, i] != 0.0:
-                f_i[kin], _ = relax(fstar, dt * tab.A[i, i] * nu[kin], prob.beta, v, w)
+                f_i[kin], _ = relax(fstar, dt * tab.A[i, i] * nu_i, prob.beta, v, w)
             else:
                 f_i[kin] = fstar
             needQ = tab.b[i] != 0.0 or np.any(tab.A[i + 1:, i] != 0.0)
             if needQ:
                 g = f_i[kin]
-                Q_i[kin] = nu[kin][:, None, None] * (es_gaussian_of(g, v, w, prob.beta) - g)
+                Q_i[kin] = nu_i[:, None, None] * (es_gaussian_of(g, v, w, prob.beta) - g)
         if prob.coupling == "stage":
             if kin.any():
                 U_i[:, kin] = _U_of_f(prob, f_i[kin])

@@ -75,6 +75,42 @@ def test_second_order_pairs_converge_at_second_order(name):
     assert abs(order - 2.0) <= 0.3, order
 
 
+def test_density_tau_equals_scaled_constant_tau_at_uniform_density():
+    """Reading R23: on a spatially uniform state (periodic, rho = 2 and the
+    same anisotropic non-equilibrium f in every cell, no flow) the transport
+    vanishes and the density stays 2, so
+    tau = tau rho must give exactly the run with constant tau doubled; and the
+    criterion's lambda_A with tau = tau rho equals the constant-tau one at
+    2 tau."""
+    prob = O.Problem(nx=6, ny=5, nv=12, vmax=6.0, switch="frozen")
+    X, Y = prob.centres()
+    rho = np.full(X.shape, 2.0)
+    T = np.full(X.shape, 1.2)
+    kin = np.ones(X.shape, bool)
+    eps = np.full(X.shape, 0.05)
+    st0 = O.init_state(prob, rho, 0 * rho, 0 * rho, T, eps, kin)
+    v, w = O.velocity_grid(prob.nv, prob.vmax)
+    VX, VY = np.meshgrid(v, v)
+    st0.f = st0.f * (1.0 + 0.1 * (VX ** 2 - VY ** 2) / (1.0 + VX ** 2 + VY ** 2))[None, None]
+    st0.f *= 2.0 / (w * st0.f.sum(axis=(-2, -1)))[..., None, None]  # keep rho = 2 exactly
+    st0.U = np.stack([w * np.einsum("jkab,ab->jk", st0.f, q) for q in
+                      (np.ones_like(VX), VX, VY, 0.5 * (VX ** 2 + VY ** 2))])
+    outs = []
+    for P in (replace(prob, tau_model="density", tau=0.7), replace(prob, tau=1.4)):
+        st = st0
+        for _ in range(3):
+            st = O.step(P, st, 1e-2, O.ARS233)
+        outs.append(st)
+    np.testing.assert_allclose(outs[0].f, outs[1].f, rtol=1e-12, atol=1e-15)
+    # the criterion on a shear flow with a temperature gradient at rho = 2
+    shear = O.init_state(prob, rho, 0.3 * np.sin(2 * np.pi * Y), 0 * rho, 1.0 + 0.2 * np.cos(2 * np.pi * X), eps,
+                         np.zeros(X.shape, bool))
+    lam_d, _ = O.regime_indicators(replace(prob, tau_model="density", tau=0.7), shear)
+    lam_c, _ = O.regime_indicators(replace(prob, tau=1.4), shear)
+    assert lam_c.max() > 1e-3
+    np.testing.assert_allclose(lam_d, lam_c, rtol=1e-12)
+
+
 def test_imex_euler_is_first_order_only():
     T = O.IMEX_EULER
     assert np.isclose(T.b.sum(), 1) and np.isclose(T.bt.sum(), 1)
