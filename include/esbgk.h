@@ -56,6 +56,7 @@ typedef enum { ESBGK_BC_PERIODIC = 0, ESBGK_BC_OUTFLOW = 1 } esbgk_bc;
 typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1, ESBGK_SWITCH_LEARNED = 2 } esbgk_switch;
 typedef enum { ESBGK_COUPLE_STAGE = 0, ESBGK_COUPLE_STEP = 1 } esbgk_coupling;
 typedef enum { ESBGK_INTERFACE_OWN = 0, ESBGK_INTERFACE_CONSERVATIVE = 1 } esbgk_interface;
+typedef enum { ESBGK_TAU_CONSTANT = 0, ESBGK_TAU_DENSITY = 1 } esbgk_tau_model;
 
 /* Cartesian grid of Sec. 3.2: N_x x N_y cells on [x0,x1] x [y0,y1]; two ghost
  * cells per side, periodic or outflow (copy of the edge cell). */
@@ -92,10 +93,15 @@ typedef struct {
  *             CONSERVATIVE -- the fluid cell's Euler update takes, at that
  *             face, the moments (1, v, |v|^2/2) of the kinetic numerical flux
  *             the kinetic cell uses, so that mass, momentum and energy are
- *             conserved to rounding.  Zero-initialised structs get OWN. */
+ *             conserved to rounding.  Zero-initialised structs get OWN.
+ *  tau_model  esbgk_tau_model: CONSTANT -- nu = tau / eps(x); DENSITY -- the
+ *             relaxation time scales with the density (Sec. 2.1 lets tau
+ *             depend on the macroscopic moments): nu = tau rho / eps(x), rho
+ *             of the cell's f* at each stage, and the criterion's viscosity
+ *             and conductivity use tau rho.  Zero-initialised: CONSTANT. */
 typedef struct {
   double beta, tau, eta_factor, delta, cweno_eps;
-  int32_t sw, coupling, prec, interface_flux;
+  int32_t sw, coupling, prec, interface_flux, tau_model;
 } esbgk_params;
 
 /* IMEX tableaux (Sec. 3.4), 2 <= s <= 4 stages: explicit (At, bt) for the

@@ -37,6 +37,7 @@ SWITCH = {"frozen": 0, "plain": 1, "learned": 2}
 CNN_PARAMS, CNN_CHANNELS = 10753, 16
 COUPLING = {"stage": 0, "step": 1}
 INTERFACE = {"own": 0, "conservative": 1}
+TAU_MODEL = {"constant": 0, "density": 1}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 
 __all__ = ["Solver", "BatchSolver", "SwitchNet", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
@@ -103,7 +104,7 @@ def _structs(_abi, grid, vmesh, params, prec):
     q = _abi.Params(float(p.get("beta", -0.5)), float(p.get("tau", 1.0)), float(p.get("eta_factor", 1.0)),
                     float(p.get("delta", 1e-3)), float(p.get("cweno_eps", 1e-6)),
                     SWITCH[p.get("switch", "frozen")], COUPLING[p.get("coupling", "stage")], PREC[prec],
-                    INTERFACE[p.get("interface", "own")])
+                    INTERFACE[p.get("interface", "own")], TAU_MODEL[p.get("tau_model", "constant")])
     return g, v, q
 
 
@@ -113,7 +114,8 @@ class Solver:
     grid: nx, ny, x0, x1, y0, y1, bc_x, bc_y ('periodic' | 'outflow')
     vmesh: nv, vmax
     params: beta, tau, eta_factor, delta, cweno_eps, switch ('frozen' | 'plain'),
-            coupling ('stage' | 'step'), interface ('own' | 'conservative');
+            coupling ('stage' | 'step'), interface ('own' | 'conservative'),
+            tau_model ('constant' | 'density');
             prec: 'fp64' | 'fp32' | 'bf16'.
     """
 

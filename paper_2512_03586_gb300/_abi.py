@@ -21,6 +21,7 @@ SWITCH = {"frozen": 0, "plain": 1, "learned": 2}
 CNN_PARAMS, CNN_CHANNELS = 10753, 16
 COUPLING = {"stage": 0, "step": 1}
 INTERFACE = {"own": 0, "conservative": 1}
+TAU_MODEL = {"constant": 0, "density": 1}
 PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 KERNEL_CLASSES = ("l1", "flags", "compact", "prep", "stage", "final", "other")
 
@@ -38,7 +39,8 @@ class VMesh(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("eta_factor", ctypes.c_double),
                 ("delta", ctypes.c_double), ("cweno_eps", ctypes.c_double), ("sw", ctypes.c_int32),
-                ("coupling", ctypes.c_int32), ("prec", ctypes.c_int32), ("interface_flux", ctypes.c_int32)]
+                ("coupling", ctypes.c_int32), ("prec", ctypes.c_int32), ("interface_flux", ctypes.c_int32),
+                ("tau_model", ctypes.c_int32)]
 
 
 class Tableau(ctypes.Structure):

@@ -102,6 +102,7 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN && p->sw != ESBGK_SWITCH_LEARNED) return false;
   if (p->coupling != ESBGK_COUPLE_STAGE && p->coupling != ESBGK_COUPLE_STEP) return false;
   if (p->interface_flux != ESBGK_INTERFACE_OWN && p->interface_flux != ESBGK_INTERFACE_CONSERVATIVE) return false;
+  if (p->tau_model != ESBGK_TAU_CONSTANT && p->tau_model != ESBGK_TAU_DENSITY) return false;
   return launchers_for(p->prec) != nullptr;
 }
 
@@ -690,6 +691,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->g = g;
   X->m.beta = params->beta;
   X->m.tau = params->tau;
+  X->m.tau_rho = params->tau_model == ESBGK_TAU_DENSITY ? 1 : 0;
   X->m.eps_w = params->cweno_eps;
   X->m.eta_factor = params->eta_factor;
   X->m.delta = params->delta;
@@ -1706,6 +1708,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.g = g;
   X.m.beta = params->beta;
   X.m.tau = params->tau;
+  X.m.tau_rho = params->tau_model == ESBGK_TAU_DENSITY ? 1 : 0;
   X.m.eps_w = params->cweno_eps;
   X.m.eta_factor = params->eta_factor;
   X.m.delta = params->delta;

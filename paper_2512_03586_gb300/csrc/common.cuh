@@ -36,6 +36,7 @@ struct Geo {
 struct Model {
   double beta, tau, eps_w, eta_factor, delta;
   float fbeta, ftau, feps_w;
+  int tau_rho;  // relaxation time tau * rho (else tau)
 };
 
 // The double or the float copy of a constant, for arithmetic type R.

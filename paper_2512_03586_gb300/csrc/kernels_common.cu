@@ -59,8 +59,10 @@ __device__ __forceinline__ float crit_sqrt(float x) { return x > 0.0f ? sqrtf(x)
 // R: float64 for FP64 storage, float32 for FP32/BF16 storage (the decision is
 // then taken in the storage's working precision; GB300's FP64 pipe is narrow).
 template <typename R>
-__device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t nc, int cc, R& ux, R& uy, R& T) {
-  const R rho = (R)Un[cc], mx = (R)Un[nc + cc], my = (R)Un[2 * nc + cc], E = (R)Un[3 * nc + cc];
+__device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t nc, int cc, R& rho, R& ux, R& uy,
+                                          R& T) {
+  rho = (R)Un[cc];
+  const R mx = (R)Un[nc + cc], my = (R)Un[2 * nc + cc], E = (R)Un[3 * nc + cc];
   const R ir = crit_rcp(rho);
   ux = mx * ir;
   uy = my * ir;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void prim_cell(const double* __restrict__ Un, size_t 
 // of its east, west, north and south neighbours.
 template <typename R>
 struct Prims {
-  R ux, uy, T;
+  R rho, ux, uy, T;
 };
 template <typename R>
 __device__ __forceinline__ void flags_from_prims(const View& V, const double* __restrict__ L1in, double* L1out,
@@ -88,8 +90,9 @@ __device__ __forceinline__ void flags_from_prims(const View& V, const double* __
   const R Dyy = R(2) * dvdy - R(2.0 / 3.0) * div;
   const R Dxy = dudy + dvdx;
   const R eps = (R)V.eps[c];
-  const R c1 = eps / (R(V.m.tau) * (R(1) - R(V.m.beta)));
-  const R kk = R(2.5) * eps * crit_rcp(R(V.m.tau) * crit_sqrt(P0.T));
+  const R tau = V.m.tau_rho ? R(V.m.tau) * P0.rho : R(V.m.tau);  // tau * rho with the density model
+  const R c1 = eps / (tau * (R(1) - R(V.m.beta)));
+  const R kk = R(2.5) * eps * crit_rcp(tau * crit_sqrt(P0.T));
   const R c2 = R(2.0 / 3.0) * kk * kk;
   const R Xxx = c1 * Dxx + c2 * dTdx * dTdx;
   const R Xxy = c1 * Dxy + c2 * dTdx * dTdy;
@@ -109,11 +112,11 @@ __device__ void flags_cell(const View& V, const double* __restrict__ Un, const d
   const Geo& g = V.g;
   const int i = c % g.nx, j = c / g.nx;
   Prims<R> P0, PE, PW, PN, PS;
-  prim_cell(Un, g.nc, j * g.nx + nb(i + 1, g.nx, g.bcx), PE.ux, PE.uy, PE.T);
-  prim_cell(Un, g.nc, j * g.nx + nb(i - 1, g.nx, g.bcx), PW.ux, PW.uy, PW.T);
-  prim_cell(Un, g.nc, nb(j + 1, g.ny, g.bcy) * g.nx + i, PN.ux, PN.uy, PN.T);
-  prim_cell(Un, g.nc, nb(j - 1, g.ny, g.bcy) * g.nx + i, PS.ux, PS.uy, PS.T);
-  prim_cell(Un, g.nc, c, P0.ux, P0.uy, P0.T);
+  prim_cell(Un, g.nc, j * g.nx + nb(i + 1, g.nx, g.bcx), PE.rho, PE.ux, PE.uy, PE.T);
+  prim_cell(Un, g.nc, j * g.nx + nb(i - 1, g.nx, g.bcx), PW.rho, PW.ux, PW.uy, PW.T);
+  prim_cell(Un, g.nc, nb(j + 1, g.ny, g.bcy) * g.nx + i, PN.rho, PN.ux, PN.uy, PN.T);
+  prim_cell(Un, g.nc, nb(j - 1, g.ny, g.bcy) * g.nx + i, PS.rho, PS.ux, PS.uy, PS.T);
+  prim_cell(Un, g.nc, c, P0.rho, P0.ux, P0.uy, P0.T);
   flags_from_prims(V, L1in, L1out, lamA, flags_out, c, plain, P0, PE, PW, PN, PS);
 }
 
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kFX* kFY) flags_tile_kernel(View V, const doub
   const int t = threadIdx.y * kFX + threadIdx.x;
   for (int h = t; h < HX * HY; h += kFX * kFY) {
     const int ci = nb(i0 + h % HX, g.nx, g.bcx), cj = nb(j0 + h / HX, g.ny, g.bcy);
-    prim_cell(Un, g.nc, cj * g.nx + ci, sp[h].ux, sp[h].uy, sp[h].T);
+    prim_cell(Un, g.nc, cj * g.nx + ci, sp[h].rho, sp[h].ux, sp[h].uy, sp[h].T);
   }
   __syncthreads();
   const int i = blockIdx.x * kFX + threadIdx.x, j = blockIdx.y * kFY + threadIdx.y;

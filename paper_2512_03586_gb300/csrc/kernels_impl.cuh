@@ -831,8 +831,10 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
     return;
   }
 
-  // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
-  const R nu = pick<R>(V.m.tau, V.m.ftau) / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
+  // collision rate nu = tau / eps (tau * rho with the density model, rho of
+  // f*) and h = dt a_ii nu in the arithmetic type
+  const R tau = pick<R>(V.m.tau, V.m.ftau) * (V.m.tau_rho ? pick<R>(g.w, g.fw) * m[0] : R(1));
+  const R nu = tau / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
   CellPar<R> P;
   bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), h, relax, P);
   if (ok) ok = project<R>(g, lane, P);
@@ -1092,8 +1094,10 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     return;
   }
 
-  // collision rate nu = tau / eps and h = dt a_ii nu in the arithmetic type
-  const R nu = pick<R>(V.m.tau, V.m.ftau) / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
+  // collision rate nu = tau / eps (tau * rho with the density model, rho of
+  // f*) and h = dt a_ii nu in the arithmetic type
+  const R tau = pick<R>(V.m.tau, V.m.ftau) * (V.m.tau_rho ? pick<R>(g.w, g.fw) * m[0] : R(1));
+  const R nu = tau / R(V.eps[c]), h = pick<R>(A.h_coef, A.f_h_coef) * nu;
   CellPar<R> P;
   bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), h, true, P);
   if (ok) ok = project<R, W, L>(g, lane, P, mask);
