@@ -297,6 +297,9 @@ size_t esbgk_batch_workspace_bytes(int32_t n, const esbgk_grid* grids, const esb
 int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes,
                        const esbgk_params* params, void* workspace, size_t workspace_bytes,
                        void* stream, esbgk_batch** out);
+/* Free the batch's host state (its graphs and events); the device workspace
+ * stays the caller's, and work already queued on the stream still uses it
+ * (synchronise first, e.g. esbgk_batch_sync).  NULL is ignored. */
 void esbgk_batch_destroy(esbgk_batch* b);
 
 /* esbgk_set_state for case i. */
@@ -396,6 +399,9 @@ typedef struct esbgk_cnn esbgk_cnn;
 size_t esbgk_cnn_workspace_bytes(int32_t max_images, int32_t H, int32_t W);
 int esbgk_cnn_create(int32_t max_images, int32_t H, int32_t W, void* workspace, size_t workspace_bytes,
                      void* stream, esbgk_cnn** out);
+/* Free the network's host state; the device workspace stays the caller's,
+ * and work already queued on the stream still uses it (synchronise first).
+ * NULL is ignored. */
 void esbgk_cnn_destroy(esbgk_cnn* c);
 /* Set (and reset the optimiser) / read the float32 parameters (host). */
 int esbgk_cnn_set_params(esbgk_cnn* c, const float* theta);
