@@ -36,7 +36,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_replicas_reduce_time_and_updates():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
     assert out[0][:2] == (11.0, 3000.0) and out[1][:2] == (11.0, 3000.0)
