@@ -97,6 +97,27 @@ def test_batch_equals_single_cases(prec, tableau, graph):
         assert cb["steps"] == 5
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_with_largest_velocity_grid(prec):
+    """A case at the largest accepted N_v = 64 (4096 nodes: the widest shared
+    f* arrays of the batched kernels) beside a small two-cells-per-warp case."""
+    import torch
+    big = W.gaussian_blob(nx=5, ny=3, nv=64, steps=2)
+    small = W.riemann_quadrants(nx=12, ny=10, nv=12, seed=4)
+    cases = [big, small]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, prec, stream=stream)
+        singles = [_single(c, prec) for c in cases]
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(3):
+            for s, c in zip(singles, cases):
+                s.step(c["dt"], "ars233")
+            b.step(dts, "ars233")
+        b.sync()
+        _compare(b, singles, prec)
+
+
 def test_batch_on_default_stream_runs_without_graph():
     cases = _mixed_cases()[:3]
     b = _batch(cases, "fp64")
