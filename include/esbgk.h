@@ -66,7 +66,11 @@ typedef struct {
   int32_t bc_x, bc_y; /* esbgk_bc */
 } esbgk_grid;
 
-/* Velocity grid of Sec. 3.2: N_v points per direction on [-v_max, v_max]. */
+/* Velocity grid of Sec. 3.2: N_v points per direction on [-v_max, v_max],
+ * 3 <= N_v <= 64.  The discrete Gaussian is corrected by a quadratic in the
+ * velocity (1, xi_x, xi_y, xi_x^2, xi_x xi_y, xi_y^2); on two points per
+ * direction xi^2 is a multiple of 1, the 6x6 moment system is singular, and
+ * N_v = 2 is rejected (E_ARG; 0 workspace bytes). */
 typedef struct {
   int32_t nv;
   double vmax;
@@ -258,7 +262,7 @@ int esbgk_last_error(esbgk_ctx* ctx, char* buf, size_t n, long long* bad_cell);
  * conserved moments and write f[n][N_v][N_v] and G_hat (same type).  This is
  * the device code the stage kernel uses.  Enqueued on `stream` (does not
  * wait); a cell whose state is not realizable (rho <= 0, T <= 0, singular
- * moment system) gets NaN in both outputs. */
+ * moment system) gets NaN in both outputs.  3 <= nv <= 64, else E_ARG. */
 int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax,
                       double beta, int32_t prec, void* f_out, void* g_out, void* stream);
 

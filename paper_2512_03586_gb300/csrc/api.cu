@@ -96,7 +96,7 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   if ((g->bc_x != ESBGK_BC_PERIODIC && g->bc_x != ESBGK_BC_OUTFLOW) ||
       (g->bc_y != ESBGK_BC_PERIODIC && g->bc_y != ESBGK_BC_OUTFLOW))
     return false;
-  if (v->nv < 2 || v->nv > 64 || !(v->vmax > 0)) return false;
+  if (v->nv < 3 || v->nv > 64 || !(v->vmax > 0)) return false;  // quadratic projection: 3 nodes at least
   if (!(p->beta >= -0.5 && p->beta < 1.0) || !(p->tau > 0) || !(p->cweno_eps > 0)) return false;
   if (!(p->eta_factor >= 0) || !(p->delta >= 0)) return false;
   if (p->sw != ESBGK_SWITCH_FROZEN && p->sw != ESBGK_SWITCH_PLAIN && p->sw != ESBGK_SWITCH_LEARNED) return false;
@@ -1080,7 +1080,7 @@ int esbgk_last_error(esbgk_ctx* X, char* buf, size_t n, long long* bad_cell) {
 int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv, double vmax, double beta,
                       int32_t prec, void* f_out, void* g_out, void* stream) {
   const Launchers* L = launchers_for(prec);
-  if (!L || !fstar || !h || !f_out || !g_out || n < 0 || nv < 2 || nv > 64 || !(vmax > 0) ||
+  if (!L || !fstar || !h || !f_out || !g_out || n < 0 || nv < 3 || nv > 64 || !(vmax > 0) ||
       !(beta >= -0.5 && beta < 1.0))
     return ESBGK_E_ARG;
   if (n == 0) return ESBGK_OK;

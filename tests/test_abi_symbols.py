@@ -59,6 +59,9 @@ def test_host_only_entry_points(libpath):
                  _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, 9)):
         assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(v), ctypes.byref(badp)) == 0
     assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(_abi.VMesh(65, 8.0)), ctypes.byref(p)) == 0
+    # two nodes per direction cannot carry the quadratic projection; three can
+    assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(_abi.VMesh(2, 8.0)), ctypes.byref(p)) == 0
+    assert _abi.esbgk_workspace_bytes(ctypes.byref(g), ctypes.byref(_abi.VMesh(3, 8.0)), ctypes.byref(p)) > 0
     # NULL arguments are rejected before any device call
     out = ctypes.c_void_p()
     assert _abi.esbgk_create(None, None, None, None, 0, None, ctypes.byref(out)) == _abi.E_ARG

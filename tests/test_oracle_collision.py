@@ -74,6 +74,26 @@ def test_projected_gaussian_exact_on_grid(nv, vmax):
     assert np.max(np.abs(Gh - G)) < 1e-3 * np.max(G)
 
 
+def test_quadratic_projection_needs_three_nodes_per_direction():
+    """Reading R4 corrects the Gaussian within span(1, v_x, v_y, v_x^2, v_x v_y,
+    v_y^2).  Brute force on the grid: the six functions are independent on the
+    N_v x N_v nodes only for N_v >= 3 (on two points v^2 is constant), the
+    bound the library enforces; on the smallest such grid the projected
+    Gaussian still reproduces its moments to round-off."""
+    for nv in (2, 3, 4, 5):
+        v, _ = O.velocity_grid(nv, 3.0)
+        VX, VY = np.meshgrid(v, v)
+        B = np.stack([np.ones_like(VX), VX, VY, VX * VX, VX * VY, VY * VY]).reshape(6, -1)
+        assert np.linalg.matrix_rank(B) == (4 if nv == 2 else 6)
+    v, w = O.velocity_grid(3, 3.0)
+    rho, u = np.array([1.1]), np.array([[0.2, -0.1]])
+    Tt = np.array([[[1.2, 0.1], [0.1, 0.9]]])
+    m = O.moments(O.projected_gaussian(rho, u, Tt, v, w), v, w)
+    S_ref = rho * np.array([Tt[0, 0, 0] + u[0, 0] ** 2, Tt[0, 0, 1] + u[0, 0] * u[0, 1], Tt[0, 1, 1] + u[0, 1] ** 2])
+    assert np.allclose(m[0, :3], [rho[0], rho[0] * u[0, 0], rho[0] * u[0, 1]], rtol=1e-13, atol=1e-14)
+    assert np.allclose(m[0, 3:6], S_ref, rtol=1e-13, atol=1e-14)
+
+
 def test_collision_conserves_h1():
     """H1: the relaxation step conserves mass, momentum and energy exactly:
     w sum (1, v, |v|^2/2) (G_hat - f) = 0 for random positive f."""
