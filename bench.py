@@ -9,7 +9,7 @@ coupling, final combination).  Metric: kinetic (cell x velocity) stage updates
 per second = sum over steps of K_kinetic * N_v^2 * (transport evaluations).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload riemann|blob|sine|batch] [--prec fp32|fp64|bf16]
+                [--workload riemann|blob|sine|batch|learned|switchnet] [--prec fp32|fp64|bf16]
 Under torchrun every rank runs an independent replica (seed = rank): weak
 scaling, no collective on the data path.  Prints one JSON line on rank 0.
 """
@@ -56,12 +56,23 @@ def make_workload(name, seed):
 
 def describe(wl, name, prec):
     g, v, p = wl["grid"], wl["vmesh"], wl["params"]
-    return {"workload": "%s %dx%d cells, %dx%d velocities on [-%g,%g]^2, %s, %s switch, %s storage" % (
+    return {"workload": "%s %dx%d cells, %dx%d velocities on [-%g,%g]^2, %s, %s switch" % (
         {"riemann": "four-quadrant Riemann ES-BGK/Euler", "blob": "Gaussian blob all-kinetic",
          "sine": "sine-periodic all-kinetic"}[name], g["nx"], g["ny"], v["nv"], v["nv"], v["vmax"], v["vmax"],
-        wl["scheme"], p["switch"], prec),
+        wl["scheme"], p["switch"]),
         "nx": g["nx"], "ny": g["ny"], "nv": v["nv"], "scheme": wl["scheme"], "prec": prec,
         "switch": p["switch"], "dt": wl["dt"]}
+
+
+def batch_workload(n):
+    return ("batched form: %d independent periodic cases, N_x = N_y in 64..256, N_v in 16..40 on [-8,8]^2, "
+            "eps log-uniform [1e-4,1e-1], plain switch, ARS(2,3,3)" % n)
+
+
+LEARNED_WORKLOAD = ("learned switch: 512x512 cells, 32x32 velocities on [-8,8]^2, four-quadrant Riemann data plus "
+                    "a density blob at (0.3, 0.7), learned switch, ARS(2,3,3)")
+SWITCHNET_METRIC = "learned-switch network: cells per second (one Adam training step)"
+SWITCHNET_WORKLOAD = "switch network: training batches of 32 x 128 x 128 cells; inference of one 512 x 512 image"
 
 
 # ---------------------------------------------------------------------------
@@ -69,11 +80,16 @@ def describe(wl, name, prec):
 
 def oracle_sample(name, steps, warmup=0):
     """Time the FP64 CPU oracle on a bounded sample of the workload: the same
-    configuration on a 32 x 32 window of cells (same velocity grid, scheme,
-    switch and data recipe).  Returns (updates/s, description, per-step s)."""
+    domain, velocity grid, scheme and data recipe on fewer cells (32 x 32 for
+    the Riemann recipes).  The learned-switch workload is sampled with the
+    paper's criterion (plain switch), the method the network assists.
+    Returns (updates/s, description, per-step s)."""
     import oracle as O
     if name == "riemann":
         wl = W.riemann_quadrants(nx=32, ny=32, seed=0)
+    elif name == "learned":
+        wl = W.learned_switch_case(nx=32, ny=32, seed=0)
+        wl["params"] = dict(wl["params"], switch="plain")
     elif name == "blob":
         wl = W.gaussian_blob(nx=16, ny=16)
     else:
@@ -93,26 +109,57 @@ def oracle_sample(name, steps, warmup=0):
     g, v = wl["grid"], wl["vmesh"]
     desc = "FP64 numpy oracle, %d steps of the same configuration on %dx%d cells (%dx%d velocities), " \
            "single-threaded" % (steps, g["nx"], g["ny"], v["nv"], v["nv"])
+    if name == "learned":
+        desc += "; plain criterion (the oracle has the paper's switch, not the network)"
     return upd / sum(per), desc, per
+
+
+def switchnet_oracle_sample(steps):
+    """FP64 oracle of the switch network on a bounded sample of its training
+    workload: Adam steps on batches of 2 images of 128 x 128 cells (the timed
+    image size, 1/16 of its batch), random features and labels.  Returns
+    (cells/s, description, per-step s)."""
+    from oracle import cnn as C
+    rng = np.random.default_rng(0)
+    theta = C.init_params(0)
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    x = rng.standard_normal((2, 128, 128, 5))
+    y = (rng.random((2, 128, 128)) < 0.25).astype(np.float64)
+    per = []
+    for t in range(1, steps + 1):
+        t0 = time.perf_counter()
+        _, g = C.grad(theta, x, y, 3.0)
+        theta, m, v = C.adam(theta, m, v, g, t, 1e-3)
+        per.append(time.perf_counter() - t0)
+    desc = ("FP64 numpy oracle of the switch network, %d Adam steps on batches of 2 x 128 x 128 cells "
+            "(random features and labels), single-threaded" % steps)
+    return x.shape[0] * 128 * 128 * steps / sum(per), desc, per
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    metric, unit = METRIC, UNIT
     if args.workload == "batch":
         val, desc, per = batch_oracle_sample(args.steps)
-        cfg = {"workload": "batched form: one case of the 64-case recipe (32x32 cells, 28x28 velocities), "
-                           "FP64 oracle", "prec": "fp64"}
+        cfg = {"workload": batch_workload(args.cases), "cases": args.cases, "prec": "fp64"}
+    elif args.workload == "learned":
+        val, desc, per = oracle_sample("learned", args.steps, warmup=args.warmup)
+        cfg = {"workload": LEARNED_WORKLOAD, "prec": "fp64"}
+    elif args.workload == "switchnet":
+        val, desc, per = switchnet_oracle_sample(args.steps)
+        metric, unit = SWITCHNET_METRIC, "cells/s"
+        cfg = {"workload": SWITCHNET_WORKLOAD, "features": 5, "hidden": 32, "prec": "fp64"}
     else:
         val, desc, per = oracle_sample(args.workload, args.steps, warmup=args.warmup)
         cfg = describe(make_workload(args.workload, 0), args.workload, "fp64")
-    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+    out = {"metric": metric, "value": val, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "impl": "reference",
-           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
-           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "cpu_baseline": {"value": val, "unit": unit, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
@@ -480,9 +527,7 @@ def batch_arm(args):
     if not args.no_cpu_baseline and world == 1:
         cv, cdesc, _ = batch_oracle_sample(max(2, args.cpu_steps // 4))
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
-    cfg = {"workload": "batched form: %d independent periodic cases, N_x = N_y in 64..256, N_v in 16..40 on "
-                       "[-8,8]^2, eps log-uniform [1e-4,1e-1], plain switch, ARS(2,3,3), %s storage" % (
-                           len(cases), args.prec),
+    cfg = {"workload": batch_workload(len(cases)),
            "cases": len(cases), "cells": ncells, "elements": elems, "prec": args.prec,
            "l2": "flushed (256 MB write) before every timed step; f arrays far exceed L2",
            "parallelism": "replicas" if world > 1 else "single GPU",
@@ -630,8 +675,7 @@ def learned_arm(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "learned switch: 512x512 cells, 32x32 velocities on [-8,8]^2, four-quadrant Riemann "
-                                  "data plus a density blob at (0.3, 0.7), learned switch, ARS(2,3,3), fp32 storage",
+           "config": {"workload": LEARNED_WORKLOAD, "prec": "fp32",
                       "training": "%d Riemann seeds x %d steps at 128x128 / 32x32 plus 3 seeds of this recipe at "
                                   "512x512 cut into 128x128 tiles (plain criterion labels, next step), 30 epochs "
                                   "Adam; collect %.1f s, train %.1f s, final loss %.4f" % (
@@ -642,6 +686,9 @@ def learned_arm(args):
            "learned_fp32_vs_plain_fp64": {"wall_per_sim_time_ratio": l32["ms_per_sim_time"] / p64["ms_per_sim_time"],
                                           "error_ratio": l32["error_vs_all_kinetic"] / p64["error_vs_all_kinetic"]},
            "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
+    if not args.no_cpu_baseline:
+        cv, cdesc, _ = oracle_sample("learned", args.cpu_steps)
+        out["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
     print(json.dumps(out), flush=True)
 
 
@@ -710,11 +757,10 @@ def switchnet_arm(args):
     except Exception:
         peak, src = 1900.0, "fallback 1.9 PFLOP/s"
     tf_inf = cells_inf * f_fwd / (ms_fwd * 1e-3) / 1e12
-    out = {"metric": "learned-switch network: cells per second (one Adam training step)", "value": cells_tr / (ms_train * 1e-3),
+    out = {"metric": SWITCHNET_METRIC, "value": cells_tr / (ms_train * 1e-3),
            "unit": "cells/s", "n_gpus": 1, "steps": k_tr, "warmup": args.warmup, "ms_per_step": ms_train,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands / f32 accumulation",
-           "data": "synthetic", "config": {"workload": "switch network: training batches of 32 x 128 x 128 cells; "
-                                                       "inference of one 512 x 512 image", "features": 5, "hidden": 32},
+           "data": "synthetic", "config": {"workload": SWITCHNET_WORKLOAD, "features": 5, "hidden": 32},
            "inference": {"ms": ms_inf, "cells_per_s": cells_inf / (ms_inf * 1e-3)},
            "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s", "frac": tf_inf / peak,
                         "traffic": None, "kernel": "forward pass (5->32 convolution on mma.sync, 32->32 convolution "
@@ -725,7 +771,10 @@ def switchnet_arm(args):
            "clocks": clk.summary(),
            # per training step: two convolutions, head, head reduction, weight gradient and its reduction
            # (twice), input-gradient convolution, Adam = 10; per inference: two convolutions and the head
-           "gpu_launches": args.steps * (10 + 3)}
+           "gpu_launches": k_tr * 10 + k_inf * 3}
+    if not args.no_cpu_baseline:
+        cv, cdesc, _ = switchnet_oracle_sample(3)
+        out["cpu_baseline"] = {"value": cv, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": cdesc}
     print(json.dumps(out), flush=True)
 
 

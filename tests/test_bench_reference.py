@@ -1,0 +1,51 @@
+"""bench.py --impl reference: the FP64 oracle timed on the host cores on a
+bounded sample of the same workload, printed as one JSON line with the bench
+line's metric and workload description.  Runs on the CPU (the arm uses no GPU)."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, env_extra=None):
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stdout.strip().splitlines()
+
+
+@pytest.mark.parametrize("workload", ["riemann", "switchnet"])
+def test_reference_line_contract(workload):
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = _run(["--workload", workload, "--steps", "3", "--warmup", "3"])
+    d = json.loads(lines[-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["unit"] == d["unit"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["dtype"] == "f64" and d["config"]["prec"] == "fp64"
+    if workload == "riemann":
+        # the same workload description as the bench line of the CUDA path
+        ours = bench.describe(bench.make_workload("riemann", 0), "riemann", "fp32")
+        assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+        assert d["config"]["workload"] == ours["workload"]
+    else:
+        assert d["metric"] == bench.SWITCHNET_METRIC and d["unit"] == "cells/s"
+        assert d["config"]["workload"] == bench.SWITCHNET_WORKLOAD
+
+
+def test_reference_runs_on_rank_zero_only():
+    assert _run(["--steps", "3", "--warmup", "3"], {"RANK": "1"}) == []
+
+
+def test_warmup_below_three_is_refused():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
+                       capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert r.returncode != 0
