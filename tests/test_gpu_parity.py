@@ -244,6 +244,20 @@ def test_largest_velocity_grids_tiny_space(nv, prec):
     assert worst.max() <= TOL[prec], worst
 
 
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, "periodic"), (1, 1, "outflow"), (2, 1, "outflow"), (1, 3, "periodic")])
+@pytest.mark.parametrize("switch", ["frozen", "plain"])
+def test_grids_of_one_to_three_cells(nx, ny, bc, switch):
+    """Degenerate grids: every stencil read wraps (periodic) or copies (outflow)
+    onto the few cells there are; one cell is a space-homogeneous problem."""
+    wl = W.riemann_quadrants(nx=nx, ny=ny, nv=8, seed=2)
+    wl["grid"] = dict(wl["grid"], bc_x=bc, bc_y=bc)
+    if switch == "frozen":
+        wl["fields"]["kin"] = np.ones((ny, nx), bool)
+    wl["params"] = dict(wl["params"], switch=switch)
+    worst, *_ = run_parity(wl, 3, "fp64")
+    assert worst.max() <= TOL["fp64"], worst
+
+
 def test_single_kinetic_cell_outflow_corner():
     wl = W.riemann_quadrants(nx=9, ny=7, nv=12, seed=6)
     kin = np.zeros((7, 9), bool)
