@@ -83,3 +83,23 @@ def test_oracle_and_library_share_no_code():
         if f.endswith(".py"):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2512_03586_gb300" not in txt, f
+
+
+@pytest.mark.parametrize("name", ["ars233", "imex_euler", "ars222", "ssp2_332"])
+def test_packed_tableau_carries_the_oracle_coefficients(libpath, name):
+    """The binding's tableaux and the oracle's are written separately; the
+    esbgk_tableau the binding packs (rows of stride 4) holds the oracle's
+    coefficients."""
+    import numpy as np
+    import oracle as O
+    import paper_2512_03586_gb300 as G
+    ref = {"ars233": O.ARS233, "imex_euler": O.IMEX_EULER, "ars222": O.ARS222, "ssp2_332": O.SSP2_332}[name]
+    t = G.make_tableau(name)
+    s = len(ref.b)
+    assert t.s == s
+    At = np.array([[t.At[i * 4 + j] for j in range(s)] for i in range(s)])
+    A = np.array([[t.A[i * 4 + j] for j in range(s)] for i in range(s)])
+    np.testing.assert_allclose(At, ref.At, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(A, ref.A, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(list(t.bt)[:s], ref.bt, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(list(t.b)[:s], ref.b, rtol=0, atol=1e-15)
