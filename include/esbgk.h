@@ -22,7 +22,10 @@
  *    workspace of esbgk_workspace_bytes() bytes (e.g. a torch uint8 tensor)
  *    and keeps it alive until esbgk_destroy.
  *  - All device work goes to the caller's CUDA stream (cudaStream_t passed as
- *    void*; NULL = legacy default stream).  A context is not thread-safe.
+ *    void*; NULL = legacy default stream).  A context is not thread-safe, and
+ *    the library keeps process-wide launch caches (occupancy per kernel and
+ *    launch shape, the shared-memory limit) without a lock: calls from several
+ *    host threads must be serialised by the caller, on one context or on many.
  *  - Velocity nodes (Sec. 3.2): v_k = -v_max + (k + 1/2) dv, dv = 2 v_max/N_v,
  *    quadrature weight dv^2 (midpoint rule).
  */
