@@ -103,3 +103,22 @@ def test_packed_tableau_carries_the_oracle_coefficients(libpath, name):
     np.testing.assert_allclose(A, ref.A, rtol=0, atol=1e-15)
     np.testing.assert_allclose(list(t.bt)[:s], ref.bt, rtol=0, atol=1e-15)
     np.testing.assert_allclose(list(t.b)[:s], ref.b, rtol=0, atol=1e-15)
+
+
+def test_relax_cells_argument_checks_and_empty_input(libpath):
+    """esbgk_relax_cells checks its arguments and returns for n = 0 before any
+    device call (the host buffers below are never dereferenced)."""
+    import numpy as np
+    from paper_2512_03586_gb300 import _abi
+    buf = np.zeros(16)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    d = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    call = _abi.esbgk_relax_cells
+    assert call(p, d, 0, 16, 6.0, -0.5, _abi.FP64, p, p, None) == 0
+    assert call(p, d, -1, 16, 6.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG
+    assert call(p, d, 0, 2, 6.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG      # N_v = 2: singular projection
+    assert call(p, d, 0, 65, 6.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG
+    assert call(p, d, 0, 16, 0.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG
+    assert call(p, d, 0, 16, 6.0, -0.6, _abi.FP64, p, p, None) == _abi.E_ARG     # beta below -1/2
+    assert call(p, d, 0, 16, 6.0, -0.5, 9, p, p, None) == _abi.E_ARG             # unknown precision
+    assert call(None, d, 0, 16, 6.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG
