@@ -122,3 +122,24 @@ def test_relax_cells_argument_checks_and_empty_input(libpath):
     assert call(p, d, 0, 16, 6.0, -0.6, _abi.FP64, p, p, None) == _abi.E_ARG     # beta below -1/2
     assert call(p, d, 0, 16, 6.0, -0.5, 9, p, p, None) == _abi.E_ARG             # unknown precision
     assert call(None, d, 0, 16, 6.0, -0.5, _abi.FP64, p, p, None) == _abi.E_ARG
+
+
+def test_batch_workspace_bytes_host_checks(libpath):
+    """The batched workspace holds every case's own workspace plus descriptor
+    tables; one precision per batch, no learned switch, every case valid."""
+    from paper_2512_03586_gb300 import _abi
+    G2 = _abi.Grid * 2
+    V2 = _abi.VMesh * 2
+    P2 = _abi.Params * 2
+    g = G2(_abi.Grid(64, 64, 0, 1, 0, 1, 0, 0), _abi.Grid(96, 80, 0, 1, 0, 1, 1, 1))
+    v = V2(_abi.VMesh(16, 8.0), _abi.VMesh(24, 8.0))
+    p = P2(_abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, _abi.FP32), _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, _abi.FP32))
+    total = _abi.esbgk_batch_workspace_bytes(2, g, v, p)
+    singles = sum(_abi.esbgk_workspace_bytes(ctypes.byref(g[i]), ctypes.byref(v[i]), ctypes.byref(p[i])) for i in range(2))
+    assert singles <= total <= singles + (1 << 22)
+    assert _abi.esbgk_batch_workspace_bytes(0, g, v, p) == 0
+    mixed = P2(p[0], _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 1, 0, _abi.FP64))
+    assert _abi.esbgk_batch_workspace_bytes(2, g, v, mixed) == 0                  # one precision per batch
+    learned = P2(p[0], _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 2, 0, _abi.FP32))
+    assert _abi.esbgk_batch_workspace_bytes(2, g, v, learned) == 0                # no learned switch in a batch
+    assert _abi.esbgk_batch_workspace_bytes(2, g, V2(v[0], _abi.VMesh(2, 8.0)), p) == 0
