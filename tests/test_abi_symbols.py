@@ -143,3 +143,37 @@ def test_batch_workspace_bytes_host_checks(libpath):
     learned = P2(p[0], _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 2, 0, _abi.FP32))
     assert _abi.esbgk_batch_workspace_bytes(2, g, v, learned) == 0                # no learned switch in a batch
     assert _abi.esbgk_batch_workspace_bytes(2, g, V2(v[0], _abi.VMesh(2, 8.0)), p) == 0
+
+
+def test_noalloc_entry_host_checks(libpath):
+    """esbgk_kinetic_steps_noalloc rejects bad arguments (E_ARG) and problems
+    larger than its static scratch (E_TOO_LARGE) before any device call."""
+    import numpy as np
+    import paper_2512_03586_gb300 as G
+    from paper_2512_03586_gb300 import _abi
+    g = _abi.Grid(8, 8, 0, 1, 0, 1, 0, 0)
+    v = _abi.VMesh(8, 6.0)
+    p = _abi.Params(-0.5, 1.0, 1.0, 1e-3, 1e-6, 0, 0, _abi.FP32)
+    tab = G.make_tableau("ars233")
+    buf = np.zeros(16)
+    d = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    vp = buf.ctypes.data_as(ctypes.c_void_p)
+    call = _abi.esbgk_kinetic_steps_noalloc
+    R = ctypes.byref
+    assert call(R(g), R(v), R(p), 0.0, R(tab), 1, d, vp, d, None) == _abi.E_ARG          # dt <= 0
+    assert call(R(g), R(v), R(p), float("inf"), R(tab), 1, d, vp, d, None) == _abi.E_ARG
+    assert call(R(g), R(v), R(p), 1e-3, R(tab), -1, d, vp, d, None) == _abi.E_ARG        # nsteps < 0
+    assert call(R(g), R(v), R(p), 1e-3, None, 1, d, vp, d, None) == _abi.E_ARG
+    assert call(R(g), R(v), R(p), 1e-3, R(tab), 1, None, vp, d, None) == _abi.E_ARG
+    assert call(R(g), R(_abi.VMesh(2, 6.0)), R(p), 1e-3, R(tab), 1, d, vp, d, None) == _abi.E_ARG
+    bad = G.make_tableau("ars233")
+    bad.s = 5                                                                             # more stages than fit
+    assert call(R(g), R(v), R(p), 1e-3, R(bad), 1, d, vp, d, None) == _abi.E_ARG
+    upper = G.make_tableau("ars233")
+    upper.At[0 * 4 + 1] = 0.3                                                             # explicit part not strictly lower
+    assert call(R(g), R(v), R(p), 1e-3, R(upper), 1, d, vp, d, None) == _abi.E_ARG
+    neg = G.make_tableau("ars233")
+    neg.A[1 * 4 + 1] = -0.1                                                               # negative implicit diagonal
+    assert call(R(g), R(v), R(p), 1e-3, R(neg), 1, d, vp, d, None) == _abi.E_ARG
+    huge = _abi.Grid(2048, 2048, 0, 1, 0, 1, 0, 0)
+    assert call(R(huge), R(_abi.VMesh(32, 8.0)), R(p), 1e-3, R(tab), 1, d, vp, d, None) == _abi.E_TOO_LARGE
