@@ -180,6 +180,31 @@ def test_riemann_full_size_first_steps():
     assert st.kin.sum() > 0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_blob_full_size_sampled_cells(prec):
+    """Precision-form configuration at its full size (256^2 periodic cells,
+    48^2 velocities on [-8,8]^2, all kinetic, ARS(2,3,3)) in the per-cell form
+    the bench times: one step on the GPU, and at sampled cells (centre, flank,
+    far field, cells whose stencils wrap) the oracle's step on the periodic
+    window of radius 7 around the cell -- one step depends on the cells within
+    6 (pinned in the oracle tests)."""
+    from windows import window
+    wl = W.gaussian_blob()
+    g = gpu_solver(wl, prec)
+    g.advance(wl["dt"], wl["scheme"])
+    U = g.cons()
+    tab = tableau_of(wl["scheme"])
+    R = 7
+    for (j0, i0) in [(128, 128), (128, 155), (100, 140), (0, 0), (255, 3), (40, 220)]:
+        w = window(wl, j0, i0, R)
+        P, st = oracle_pair(w)
+        Uo = O.advance(P, st, wl["dt"], tab).U[:, R, R]
+        Ug = U[:, j0, i0]
+        rel = max(abs(Ug[0] - Uo[0]) / Uo[0], abs(Ug[1] - Uo[1]) / Uo[0], abs(Ug[2] - Uo[2]) / Uo[0],
+                  abs(Ug[3] - Uo[3]) / Uo[3])
+        assert rel <= TOL[prec], (j0, i0, rel)
+
+
 # (precision, N_v, expected form: nodes per group, cells per warp)
 STRADDLE = [("fp64", 10, (2, 2)), ("fp64", 26, (2, 1)), ("fp32", 12, (4, 2)), ("fp32", 20, (4, 2)),
             ("fp32", 28, (4, 1)), ("fp32", 18, (2, 2)), ("fp32", 26, (2, 1)), ("fp32", 11, (1, 1))]

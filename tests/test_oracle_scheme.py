@@ -363,3 +363,27 @@ def test_stiff_limit_kinetic_approaches_euler():
             res.append(st.U.copy())
         diffs.append(np.mean(np.abs(res[0] - res[1])))
     assert diffs[1] < diffs[0] and diffs[1] < 1e-3, diffs
+
+
+def test_one_step_domain_of_dependence_is_six_cells():
+    """Each ARS(2,3,3) stage reads the two-cell cross stencil of the previous
+    stage values (CWENO3 faces, Sec. 3.2), so one step of a frozen all-kinetic
+    problem at a cell depends on the cells within 6 of it and on no others: the
+    run on the periodic window of radius 6 around a cell reproduces the full
+    run there exactly, and radius 5 does not.  (This is what lets the GPU
+    tests check sampled cells of full-size problems against the oracle.)"""
+    from windows import window
+    wl = W.gaussian_blob(nx=40, ny=36, nv=12, u0=(0.4, -0.3))
+    P = O.Problem(**wl["grid"], **wl["vmesh"], **wl["params"])
+    full = O.advance(P, O.init_state(P, **wl["fields"]), wl["dt"], O.ARS233).U
+    for (j0, i0) in [(18, 20), (5, 33), (0, 0), (35, 39)]:
+        for R in (6, 5):
+            w = window(wl, j0, i0, R)
+            Pw = O.Problem(**w["grid"], **w["vmesh"], **w["params"])
+            Uw = O.advance(Pw, O.init_state(Pw, **w["fields"]), w["dt"], O.ARS233).U[:, R, R]
+            d = np.abs(Uw - full[:, j0, i0]).max()
+            if R == 6:
+                assert d <= 1e-15 * np.abs(full[:, j0, i0]).max(), (j0, i0, d)
+            elif (j0, i0) == (18, 20):
+                assert d > 1e-10, d          # the blob's flank: cells at distance 6 matter
+
