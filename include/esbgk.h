@@ -95,8 +95,8 @@ typedef struct {
  *             BF16 storage with FP32 arithmetic.  Per-cell tensor solves,
  *             U and the totals are always FP64.
  *  interface_flux  esbgk_interface: OWN -- at a face between a kinetic and a
- *             fluid cell each cell uses its own model's flux (Sec. 3.5 gives
- *             no interface flux; the totals then drift at the interfaces);
+ *             fluid cell each cell uses its own model's flux (Sec. 3.6 states
+ *             conservation but gives no interface flux; the totals then drift at the interfaces);
  *             CONSERVATIVE -- the fluid cell's Euler update takes, at that
  *             face, the moments (1, v, |v|^2/2) of the kinetic numerical flux
  *             the kinetic cell uses, so that mass, momentum and energy are

@@ -38,7 +38,7 @@ class Problem:
         'conservative' -- at a face between a kinetic and a fluid cell the
         fluid cell's Euler update takes the moments (1, v, |v|^2/2) of the
         kinetic cell's numerical flux through that face, so that what leaves
-        one side enters the other and the totals are conserved (Sec. 3.5
+        one side enters the other and the totals are conserved (Sec. 3.6
         states conservation without giving an interface flux; Reading R22).
     """
     nx: int
