@@ -102,7 +102,7 @@ typedef struct {
  *             the kinetic cell uses, so that mass, momentum and energy are
  *             conserved to rounding.  Zero-initialised structs get OWN.
  *  tau_model  esbgk_tau_model: CONSTANT -- nu = tau / eps(x); DENSITY -- the
- *             relaxation time scales with the density (Sec. 2.1 lets tau
+ *             relaxation time scales with the density (Sec. 2 lets tau
  *             depend on the macroscopic moments): nu = tau rho / eps(x), rho
  *             of the cell's f* at each stage, and the criterion's viscosity
  *             and conductivity use tau rho.  Zero-initialised: CONSTANT. */

@@ -30,7 +30,7 @@ class Problem:
     coupling: 'stage' couples at every stage (Algorithm 1), 'step' only at the
         end of the step (the LOC-hybrid of Sec. 3.5).
     tau_model: 'constant' -- tau fixed (Reading R2); 'density' -- tau = tau *
-        rho (Sec. 2.1 lets tau depend on the macroscopic moments; Reading
+        rho (Sec. 2 lets tau depend on the macroscopic moments; Reading
         R23): the collision rate of a kinetic cell is nu = tau rho / eps with
         the density of its f* at each stage (which the relaxation conserves),
         and the criterion's mu and kappa use tau rho.
