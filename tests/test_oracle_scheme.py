@@ -288,6 +288,30 @@ def test_regime_update_rules():
     assert new[2, 2] and not new[1, 1] and new.sum() == 1
 
 
+def test_l1_deviation_closed_form():
+    """Reading R9: ||f - M_hat[f]||_1 with the quadrature weight dv^2 and the
+    discrete Maxwellian of f's own moments.  f = M_hat + s g with g orthogonal
+    (node sums) to 1, v_x, v_y, |v|^2 has the moments of M_hat, hence the same
+    M_hat, so the deviation is exactly dv^2 sum |s g|."""
+    prob = O.Problem(nx=3, ny=3, nv=14, vmax=6.0, switch="plain")
+    one = np.ones((3, 3))
+    kin = np.zeros((3, 3), bool)
+    kin[1, 1] = True
+    st = O.init_state(prob, 1.3 * one, 0.2 * one, -0.1 * one, 0.9 * one, 1e-3 * one, kin)
+    v, w = O.velocity_grid(prob.nv, prob.vmax)
+    VX, VY = np.meshgrid(v, v)
+    B = np.stack([np.ones(VX.size), VX.ravel(), VY.ravel(), (VX ** 2 + VY ** 2).ravel()], 1)
+    h = np.random.default_rng(4).standard_normal(VX.size)
+    g = (h - B @ np.linalg.solve(B.T @ B, B.T @ h)).reshape(VX.shape)
+    assert np.abs(B.T @ g.ravel()).max() < 1e-10
+    s_amp = 1e-3
+    st.f[1, 1] = st.f[1, 1] + s_amp * g
+    _, L1 = O.regime_indicators(prob, st)
+    expect = w * np.abs(s_amp * g).sum()
+    assert L1[1, 1] == pytest.approx(expect, rel=1e-9)
+    assert (np.abs(v[1] - v[0]) ** 2) == pytest.approx(w)
+
+
 def test_buffer_mask_cross_stencil():
     """Remark rem_coupling: the buffer is the fluid part of the two-cell cross
     stencil of the kinetic cells."""
