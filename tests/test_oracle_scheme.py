@@ -312,6 +312,39 @@ def test_l1_deviation_closed_form():
     assert (np.abs(v[1] - v[0]) ** 2) == pytest.approx(w)
 
 
+def test_regime_conversions_keep_the_cell_state():
+    """Eqs. Coupling_FluKin / Coupling_KinFlu with Reading R4: a cell turned
+    kinetic gets the discrete Maxwellian whose node moments are exactly its
+    (rho, rho u, E) -- on a coarse grid, where a sampled continuous Maxwellian
+    would miss them by ~1e-3 -- and a cell turned fluid takes the moments of
+    its f."""
+    prob = O.Problem(nx=4, ny=3, nv=10, vmax=5.0, switch="plain")
+    X, Y = prob.centres()
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * X)
+    ux, uy = 0.4 * np.cos(2 * np.pi * Y), -0.3 + 0 * X
+    T = 0.8 + 0.5 * X
+    kin0 = np.zeros(X.shape, bool)
+    kin0[0, :2] = True
+    st = O.init_state(prob, rho, ux, uy, T, 1e-3 + 0 * X, kin0)
+    v, w = O.velocity_grid(prob.nv, prob.vmax)
+    VX, VY = np.meshgrid(v, v)
+    st.f[0, 0] *= 1.0 + 0.1 * np.tanh(VX - VY)          # a non-equilibrium kinetic cell
+    new = ~kin0                                          # every cell switches
+    out = O.convert(prob, st, new)
+
+    def node_moments(g):
+        return np.stack([w * (g * q).sum(axis=(-2, -1)) for q in
+                         (np.ones_like(VX), VX, VY, 0.5 * (VX ** 2 + VY ** 2))])
+
+    up = new & ~kin0
+    np.testing.assert_allclose(node_moments(out.f[up]), st.U[:, up], rtol=1e-12, atol=1e-13)
+    down = kin0 & ~new
+    np.testing.assert_allclose(out.U[:, down], node_moments(st.f[down]), rtol=1e-12, atol=1e-13)
+    # the sampled continuous Maxwellian would not do: its moments miss U here
+    G = O.gaussian(rho[up], np.stack([ux[up], uy[up]], -1), T[up][:, None, None] * np.eye(2), v)
+    assert np.abs(node_moments(G) - st.U[:, up]).max() > 1e-6
+
+
 def test_buffer_mask_cross_stencil():
     """Remark rem_coupling: the buffer is the fluid part of the two-cell cross
     stencil of the kinetic cells."""
