@@ -24,8 +24,11 @@ Euler flux, regime criterion, tableaux, stepper (order, conservation, limits),
 and the learned switch in ``oracle.cnn`` (network forward and gradients,
 features, Adam, the learned map rule).
 Parity unpinned beyond invariants: the CWENO epsilon value, the choice of the
-quadratic moment projection, and the criterion constants (paper's printed
-d_v = 3 values), which are readings, not results the paper fixes.
+quadratic moment projection, the criterion constants (paper's printed
+d_v = 3 values), and the dissipation speed of the Euler flux (local
+Lax-Friedrichs, max |u_n| + sqrt(gamma P / rho): the pins fix consistency
+and convergence to the exact Riemann solution, which a smaller speed also
+passes), which are readings, not results the paper fixes.
 """
 
 from .kinetic import (velocity_grid, moments, macro_from_moments, gaussian,
