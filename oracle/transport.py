@@ -2,8 +2,9 @@
 
 Test infrastructure only (see the package docstring).
 
-The paper uses "a CWENO3 scheme with a Lax-Friedrichs flux" for both the
-kinetic advection and the Euler flux (Sec. 3.2) and prints no formula.
+Sec. 3.2 names third-order CWENO reconstruction with a Lax-Friedrichs
+numerical flux for both the kinetic advection and the Euler flux, and prints
+no formula for either.
 Reading R5: the third-order CWENO reconstruction of Levy, Puppo and Russo
 (1999), applied dimension by dimension on cell averages, evaluated at the two
 faces of each cell; the Lax-Friedrichs (Rusanov) numerical flux with the local
