@@ -243,6 +243,20 @@ def test_criterion_shear_flow_closed_form():
     assert np.all(L1 == 0)
 
 
+def test_criterion_compression_closed_form():
+    """u = (a x, 0), a one-dimensional compression or expansion: grad u =
+    diag(a, 0), div u = a, D = diag(2a - 2/3 a, -2/3 a) = diag(4a/3, -2a/3)
+    (Reading R8: the trace part -2/3 div u I), so lambda_A =
+    (4/3) eps |a| / (tau (1 - beta)) in the interior cells."""
+    prob = O.Problem(nx=8, ny=5, nv=8, vmax=5.0, bc_x="outflow", bc_y="periodic", beta=-0.5, tau=1.1)
+    X, Y = prob.centres()
+    eps = np.full_like(X, 0.04)
+    for a in (0.6, -0.9):
+        st = O.init_state(prob, np.ones_like(X), a * X, 0 * X, np.ones_like(X), eps, np.zeros_like(X, bool))
+        lamA, _ = O.regime_indicators(prob, st)
+        assert np.allclose(lamA[:, 1:-1], (4.0 / 3.0) * 0.04 * abs(a) / (1.1 * 1.5), rtol=1e-12)
+
+
 def test_criterion_temperature_gradient_closed_form():
     """T = T0 + g x, u = 0: X = 2/3 (5/2 eps/(tau sqrt T))^2 grad T grad T^T has
     the single nonzero eigenvalue 2/3 (5/2 eps/(tau sqrt T))^2 g^2
