@@ -458,3 +458,46 @@ def test_one_step_domain_of_dependence_is_six_cells():
             elif (j0, i0) == (18, 20):
                 assert d > 1e-10, d          # the blob's flank: cells at distance 6 matter
 
+
+def _explicit_rk(y0, op, dt, At, bt):
+    """Textbook explicit Runge-Kutta step (Butcher tableau At, bt) of y' = -op(y)."""
+    ks = []
+    for i in range(len(bt)):
+        y = y0.copy()
+        for j in range(i):
+            y -= dt * At[i, j] * ks[j]
+        ks.append(op(y))
+    out = y0.copy()
+    for i in range(len(bt)):
+        out -= dt * bt[i] * ks[i]
+    return out
+
+
+@pytest.mark.parametrize("tab_name", ["ARS222", "IMEX_EULER", "ARS233"])
+def test_collisionless_and_fluid_steps_are_the_explicit_rk(tab_name):
+    """Sec. 3.4: the explicit part of the IMEX pair is (At, bt).  With the
+    collisions switched off (eps -> infinity, nu ~ 1e-30) an all-kinetic step
+    is the explicit RK step of the transport, and an all-fluid step is the
+    explicit RK step of the Euler divergence -- in particular the final
+    combination weights the fluxes by bt, not b (ARS(2,2,2) and IMEX-Euler
+    have bt != b)."""
+    tab = getattr(O, tab_name)
+    wl = W.gaussian_blob(nx=10, ny=8, nv=10, vmax=6.0, u0=(0.4, -0.2))
+    g = wl["grid"]
+    dt = 0.02
+    # all kinetic, no collisions
+    P = O.Problem(**g, **wl["vmesh"], **dict(wl["params"], switch="frozen"))
+    f = dict(wl["fields"], eps=np.full((8, 10), 1e30))
+    st = O.init_state(P, **f)
+    v, _ = O.velocity_grid(P.nv, P.vmax)
+    args = (P.dx, P.dy, P.bc_x, P.bc_y, P.cweno_eps)
+    ref = _explicit_rk(st.f, lambda y: O.kinetic_transport(y, v, *args), dt, tab.At, tab.bt)
+    out = O.advance(P, st, dt, tab)
+    assert np.abs(out.f - ref).max() <= 1e-13 * np.abs(ref).max()
+    # all fluid
+    f = dict(wl["fields"], kin=np.zeros((8, 10), bool))
+    st = O.init_state(P, **f)
+    ref = _explicit_rk(st.U, lambda y: O.euler_phi(y, *args), dt, tab.At, tab.bt)
+    out = O.advance(P, st, dt, tab)
+    assert np.abs(out.U - ref).max() <= 1e-13 * np.abs(ref).max()
+
