@@ -49,3 +49,13 @@ def test_warmup_below_three_is_refused():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
                        capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode != 0
+
+
+def test_committed_traffic_matches_the_committed_kernel_sources():
+    """The DRAM traffic per element under profiles/ was captured on the
+    kernel sources as committed (same source hash), so the bench's roofline
+    line reports it; a kernel change needs a new capture."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tr = bench.stored_traffic("fp32", "riemann")
+    assert tr is not None and 8.0 < tr < 24.0
