@@ -186,3 +186,18 @@ def test_euler_sod_converges_to_exact_riemann_solution():
         ex = exact_riemann_density(1.0, 0.0, 1.0, 0.125, 0.0, 1.0 / 32, 2.0, (y - 0.5) / t_end)
         errs.append(np.mean(np.abs(r - ex)))
     assert errs[1] < errs[0] and errs[1] < 0.01, errs
+
+
+def test_exact_riemann_helper_reproduces_the_published_sod_star_state():
+    """The exact Riemann solution used as the Sod reference is pinned to the
+    published exact values of the classic Sod problem at gamma = 1.4 (Toro,
+    Riemann Solvers and Numerical Methods for Fluid Dynamics, Ch. 4, Test 1:
+    rho*_L = 0.42632, rho*_R = 0.26557), the rarefaction fan's closed form,
+    and the undisturbed states."""
+    g = 1.4
+    xi = np.array([-2.0, -0.5, 0.5, 1.2, 2.0])
+    rho = exact_riemann_density(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g, xi)
+    cL, gm = np.sqrt(g), (g - 1) / (g + 1)
+    fan = (2 / (g + 1) + gm / cL * 0.5) ** (2 / (g - 1))     # s = -0.5 inside the fan
+    np.testing.assert_allclose(rho, [1.0, fan, 0.42632, 0.26557, 0.125], rtol=2e-5)
+
