@@ -1,0 +1,79 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake
+in a copy of the oracle (in a temporary directory, on the CPU), runs the pin
+that should catch it against the copy, and requires that pin to fail; the
+unmutated copy must pass the same pins.  The repository's oracle is never
+modified."""
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (file under oracle/, text, replacement, pin file, -k expression, the mistake)
+MUTATIONS = [
+    ("kinetic.py", "+ beta * Theta", "- beta * Theta", "test_oracle_collision.py", "stability_function",
+     "ES tensor with the wrong sign of beta"),
+    ("kinetic.py", "f = (fstar + h[..., None, None] * Gh) / (1.0 + h)[..., None, None]",
+     "f = (fstar + h[..., None, None] * Gh) / (1.0 + 0.9 * h)[..., None, None]", "test_oracle_collision.py",
+     "implicit_stage_residual", "implicit relaxation not solving its equation"),
+    ("transport.py", "un * (E + P)]), np.abs", "un * E]), np.abs", "test_oracle_transport.py", "sod",
+     "energy flux without the pressure work"),
+    ("transport.py", "np.clip(idx, 0, m - 1)", "(idx % m)", "test_oracle_transport.py", "sod",
+     "outflow ghost cells wrapped periodically"),
+    ("scheme.py", "g -= dt * tab.bt[i] * Ls[i][kin]", "g -= dt * tab.b[i] * Ls[i][kin]", "test_oracle_scheme.py",
+     "explicit_rk", "final transport weighted by the implicit weights"),
+    ("scheme.py", "(2.0 / 3.0) * div[..., None, None]", "(1.0) * div[..., None, None]", "test_oracle_scheme.py",
+     "compression", "criterion without the 2/3 trace part of D(u)"),
+    ("scheme.py", "L1[st.kin] = w * np.sum", "L1[st.kin] = np.sum", "test_oracle_scheme.py", "l1_deviation",
+     "L1 deviation without the quadrature weight"),
+    ("scheme.py", "f_i[buf] = _mhat_of_U(prob, U_i[:, buf])", "f_i[buf] = _mhat_of_U(prob, U_n[:, buf])",
+     "test_oracle_scheme.py", "second_order_pairs_converge", "buffer cells not coupled at every stage"),
+    ("cnn.py", "mh = m / (1 - b1 ** t)", "mh = m", "test_oracle_cnn.py", "adam", "Adam without bias correction"),
+]
+
+
+@pytest.fixture(scope="module")
+def sandbox(tmp_path_factory):
+    """A copy of the oracle, the generators and the pin tests."""
+    base = tmp_path_factory.mktemp("mut")
+    for d in ("oracle", "workloads"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(base, d),
+                        ignore=shutil.ignore_patterns("__pycache__"))
+    tests = os.path.join(base, "tests")
+    os.makedirs(tests)
+    for f in os.listdir(os.path.join(ROOT, "tests")):
+        if f.endswith(".py") and (f.startswith("test_oracle_") and f != "test_oracle_mutations.py"
+                                  or not f.startswith("test_")):
+            shutil.copy(os.path.join(ROOT, "tests", f), tests)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(tests, "golden"))
+    return str(base)
+
+
+def _run_pin(base, pin, kexpr):
+    env = dict(os.environ, PYTHONPATH=base, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", pin), "-q", "-x", "-k", kexpr,
+                        "-p", "no:cacheprovider"], cwd=base, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-1500:]
+
+
+def test_unmutated_copy_passes_the_pins(sandbox):
+    for pin, kexpr in sorted({(m[3], m[4]) for m in MUTATIONS}):
+        rc, out = _run_pin(sandbox, pin, kexpr)
+        assert rc == 0, (pin, kexpr, out)
+
+
+@pytest.mark.parametrize("fname,old,new,pin,kexpr,what", MUTATIONS, ids=[m[5] for m in MUTATIONS])
+def test_planted_mistake_fails_its_pin(sandbox, fname, old, new, pin, kexpr, what):
+    path = os.path.join(sandbox, "oracle", fname)
+    src = open(path).read()
+    assert src.count(old) == 1, "mutation site not unique: " + old
+    try:
+        open(path, "w").write(src.replace(old, new))
+        rc, out = _run_pin(sandbox, pin, kexpr)
+    finally:
+        open(path, "w").write(src)
+    assert rc == 1, "%s: pin %s -k %s did not fail\n%s" % (what, pin, kexpr, out)
