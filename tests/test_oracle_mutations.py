@@ -33,6 +33,11 @@ MUTATIONS = [
     ("scheme.py", "f_i[buf] = _mhat_of_U(prob, U_i[:, buf])", "f_i[buf] = _mhat_of_U(prob, U_n[:, buf])",
      "test_oracle_scheme.py", "second_order_pairs_converge", "buffer cells not coupled at every stage"),
     ("cnn.py", "mh = m / (1 - b1 ** t)", "mh = m", "test_oracle_cnn.py", "adam", "Adam without bias correction"),
+    ("scheme.py", "f[up] = _mhat_of_U(prob, U[:, up])", "f[up] = 1.001 * _mhat_of_U(prob, U[:, up])",
+     "test_oracle_scheme.py", "conversions", "fluid-to-kinetic conversion off in normalisation"),
+    ("transport.py", "psi = np.stack([np.ones_like(VX), VX, VY, 0.5 * (VX * VX + VY * VY)])",
+     "psi = np.stack([np.ones_like(VX), VX, VY, 0.5 * (VX * VX)])", "test_oracle_scheme.py",
+     "conservative_interface", "interface energy flux missing the v_y^2 part"),
 ]
 
 
