@@ -23,14 +23,14 @@ pinned -- moments, Gaussian, projected Gaussian, relaxation, CWENO3, transport,
 Euler flux, regime criterion, tableaux, stepper (order, conservation, limits),
 and the learned switch in ``oracle.cnn`` (network forward and gradients,
 features, Adam, the learned map rule).
+The dissipation speed of the Euler flux (local Lax-Friedrichs,
+max |u_n| + sqrt(gamma P / rho)) is pinned by the closed-form linearisation
+of the scheme about a uniform moving state (tests/test_oracle_transport.py).
 Parity unpinned beyond invariants: the CWENO epsilon value and linear weights
 (d_0 = 1/2, d_L = d_R = 1/4: any weights give the optimal parabola on smooth
 data by construction of P_0), the choice of the
-quadratic moment projection, the criterion constants (paper's printed
-d_v = 3 values), and the dissipation speed of the Euler flux (local
-Lax-Friedrichs, max |u_n| + sqrt(gamma P / rho): the pins fix consistency
-and convergence to the exact Riemann solution, which a smaller speed also
-passes), which are readings, not results the paper fixes.
+quadratic moment projection and the criterion constants (paper's printed
+d_v = 3 values), which are readings, not results the paper fixes.
 """
 
 from .kinetic import (velocity_grid, moments, macro_from_moments, gaussian,

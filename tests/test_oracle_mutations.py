@@ -38,6 +38,10 @@ MUTATIONS = [
     ("transport.py", "psi = np.stack([np.ones_like(VX), VX, VY, 0.5 * (VX * VX + VY * VY)])",
      "psi = np.stack([np.ones_like(VX), VX, VY, 0.5 * (VX * VX)])", "test_oracle_scheme.py",
      "conservative_interface", "interface energy flux missing the v_y^2 part"),
+    ("transport.py", "a = np.maximum(am, ap)", "a = 0.5 * np.maximum(am, ap)", "test_oracle_transport.py",
+     "dissipation", "Euler flux with half the Lax-Friedrichs speed"),
+    ("transport.py", "np.abs(un) + np.sqrt(GAMMA * P / rho)", "np.sqrt(GAMMA * P / rho)", "test_oracle_transport.py",
+     "dissipation", "Euler flux speed without the flow speed |u_n|"),
 ]
 
 

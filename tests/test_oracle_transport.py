@@ -201,3 +201,75 @@ def test_exact_riemann_helper_reproduces_the_published_sod_star_state():
     fan = (2 / (g + 1) + gm / cL * 0.5) ** (2 / (g - 1))     # s = -0.5 inside the fan
     np.testing.assert_allclose(rho, [1.0, fan, 0.42632, 0.26557, 0.125], rtol=2e-5)
 
+
+
+# ---------------------------------------------------------------------------
+# The Euler flux's dissipation speed, pinned by the linearisation about a
+# uniform state (von Neumann analysis of the semi-discrete scheme).
+
+GAMMA_TEST = 2.0  # gamma = (d_v + 2)/d_v with d_v = 2
+
+
+def _textbook_flux(U, d):
+    """Physical flux of the 2-D Euler equations (textbook form)."""
+    rho, mx, my, E = U
+    P = (GAMMA_TEST - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
+    mn = mx if d == 0 else my
+    return np.array([mn, mx * mn / rho + (P if d == 0 else 0.0), my * mn / rho + (P if d == 1 else 0.0),
+                     (E + P) * mn / rho])
+
+
+def _linear_symbol(U0, d, theta, h):
+    """M(theta) with Phi(U0 + delta r e^{i theta j}) = delta M r e^{i theta j} + O(delta^2):
+    on small perturbations the CWENO3 weights take their linear values, so the
+    face states are the optimal parabola's, q^- = (-q_{j-1} + 5 q_j + 2 q_{j+1})/6
+    and q^+ = (2 q_j + 5 q_{j+1} - q_{j+2})/6 at face j+1/2; the local
+    Lax-Friedrichs flux 1/2 A (q^- + q^+) - 1/2 a (q^+ - q^-) then has the flux
+    Jacobian A of U0 and the speed a = |u_d| + sqrt(gamma P/rho) of U0 (its
+    perturbation multiplies q^+ - q^-, a second-order term)."""
+    e = np.exp(1j * theta)
+    qm = (-1.0 / e + 5.0 + 2.0 * e) / 6.0
+    qp = (2.0 + 5.0 * e - e * e) / 6.0
+    A = np.empty((4, 4))
+    for k in range(4):  # complex-step derivative: exact to rounding
+        dU = np.zeros(4, complex)
+        dU[k] = 1e-30j
+        A[:, k] = _textbook_flux(U0.astype(complex) + dU, d).imag / 1e-30
+    rho, mx, my, E = U0
+    un = (mx if d == 0 else my) / rho
+    P = (GAMMA_TEST - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
+    a = abs(un) + np.sqrt(GAMMA_TEST * P / rho)
+    return (1.0 - 1.0 / e) / h * (0.5 * (qm + qp) * A - 0.5 * (qp - qm) * a * np.eye(4)), a
+
+
+@pytest.mark.parametrize("d", [0, 1])
+@pytest.mark.parametrize("mode", [1, 3])
+def test_euler_flux_dissipation_matches_linearisation(d, mode):
+    """Phi of a small sine perturbation of a uniform moving state equals the
+    closed-form linear symbol of CWENO3 + local Lax-Friedrichs with
+    a = |u_n| + sqrt(gamma P/rho): a wrong dissipation speed (half of it, or
+    the speed without |u_n|) changes the damping part of the symbol by far
+    more than the tolerance."""
+    n, h = 12, 0.1
+    rho0, ux0, uy0, p0 = 1.3, 0.4, -0.25, 0.9
+    U0 = np.array([rho0, rho0 * ux0, rho0 * uy0, p0 / (GAMMA_TEST - 1.0) + 0.5 * rho0 * (ux0 ** 2 + uy0 ** 2)])
+    r = np.array([1.0, -0.7, 0.45, 1.9])  # a generic direction: every characteristic field is excited
+    delta = 1e-7
+    theta = 2.0 * np.pi * mode / n
+    jj = np.arange(n)
+    shape = (1, n) if d == 0 else (n, 1)
+    pert = np.cos(theta * jj + 0.3).reshape(shape)
+    U = U0[:, None, None] + delta * r[:, None, None] * pert[None]
+    U = np.broadcast_to(U, (4, 3, n) if d == 0 else (4, n, 3)).copy()
+    phi = O.euler_phi(U, h, h, "periodic", "periodic", 1e-6)
+    phi = phi[:, 1, :] if d == 0 else phi[:, :, 1]
+    M, a = _linear_symbol(U0, d, theta, h)
+    want = delta * np.real((M @ r)[:, None] * np.exp(1j * (theta * jj + 0.3))[None])
+    scale = np.abs(want).max()
+    assert np.abs(phi - want).max() <= 1e-5 * scale
+    # the damping part is resolved: the same symbol with half the speed is far off
+    M_half = M + (1.0 - 1.0 / np.exp(1j * theta)) / h * 0.25 * a * \
+        ((2.0 + 5.0 * np.exp(1j * theta) - np.exp(2j * theta)) / 6.0
+         - (-np.exp(-1j * theta) + 5.0 + 2.0 * np.exp(1j * theta)) / 6.0) * np.eye(4)
+    other = delta * np.real((M_half @ r)[:, None] * np.exp(1j * (theta * jj + 0.3))[None])
+    assert np.abs(other - want).max() > 1e-3 * scale
