@@ -152,3 +152,61 @@ def test_learned_map_keeps_every_plain_kinetic_cell():
     pred = rng.random((8, 8)) < 0.3
     m = C.learned_map(plain, pred)
     assert np.all(m[plain]) and np.all(m[pred]) and not np.any(m[~plain & ~pred])
+
+
+# ---------------------------------------------------------------------------
+# The GPU gradient bars (tests/switch_bars.py) catch plausible kernel mistakes.
+
+GRAD_MISTAKES = [
+    ('dz2 = rnd(da2 * (f["z2"] > 0))', 'dz2 = rnd(da2)', "second ReLU mask dropped"),
+    ('g["b1"] = dz1.sum(axis=(0, 1, 2))', 'g["b1"] = dz1[:, 1:-1, 1:-1].sum(axis=(0, 1, 2))',
+     "first bias gradient without the image edges"),
+    ('g["W1"][:, ky, kx, :] = np.einsum("nyxo,nyxc->oc", dz1, _shift(f["x"], ky - 1, kx - 1))',
+     'g["W1"][:, ky, kx, :] = np.einsum("nyxo,nyxc->oc", dz1, _shift(f["x"], 1 - ky, 1 - kx))',
+     "first weight gradient with the taps mirrored"),
+    ('"w3": np.einsum("nyx,nyxc->c", dz3, f["a2"])}', '"w3": np.einsum("nyx,nyxc->c", (sig - y) / M, f["a2"])}',
+     "head gradient without the class weight"),
+    ('da1 += np.einsum("nyxo,oc->nyxc", _shift(dz2, 1 - ky, 1 - kx), p["W2"][:, ky, kx, :])',
+     'da1 += np.einsum("nyxo,oc->nyxc", _shift(dz2, ky - 1, kx - 1), p["W2"][:, ky, kx, :])',
+     "input gradient of the second convolution with the taps mirrored"),
+]
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("old,new,what", GRAD_MISTAKES, ids=[m[2] for m in GRAD_MISTAKES])
+def test_gpu_gradient_bars_reject_planted_mistakes(tmp_path, old, new, what):
+    """Each mistake is planted in a temporary copy of this oracle and its
+    gradient computed the way the GPU stores values (bf16 a1, a2, dz2, dz1):
+    the bars the GPU gradient must meet reject it on some block, while the
+    unmutated bf16 emulation meets them."""
+    import importlib.util
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import switch_bars
+    src = open(C.__file__).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "cnn_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("cnn_mutant", str(path))
+    mut = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mut)
+    rng = np.random.default_rng(7)
+    p = C.unpack(C.init_params(7))
+    p["b1"][:] = rng.normal(0, 0.1, 32)
+    p["b2"][:] = rng.normal(0, 0.1, 32)
+    p["b3"][:] = -0.3
+    p["W1"][:] = _bf16(p["W1"])
+    p["W2"][:] = _bf16(p["W2"])
+    theta = C.pack(p)
+    x = _bf16(rng.normal(size=(2, 12, 20, 5)))
+    y = (rng.random((2, 12, 20)) < 0.3).astype(np.float64)
+    _, g_exact = C.grad(theta, x, y, 2.5)
+    _, g_emu = C.grad(theta, x, y, 2.5, rnd=_bf16)
+    assert not switch_bars.check(g_emu, g_exact, g_emu, C.unpack)
+    _, g_bad = mut.grad(theta, x, y, 2.5, rnd=_bf16)
+    assert switch_bars.check(g_bad, g_exact, g_emu, C.unpack), what
