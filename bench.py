@@ -1,9 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the ES-BGK kinetic stage update (coupled IMEX domain decomposition).
 
-Workload (default): the coupled ES-BGK/Euler configuration -- 128 x 128 cells on
-[0,1]^2 (outflow), 32 x 32 velocities on [-8,8]^2, seeded four-quadrant Riemann
-data, eps(x) between 1e-4 and 1e-1, plain switch, ARS(2,3,3), f stored in FP32.
+Workload (default): the precision-form configuration -- 256 x 256 periodic cells
+on [0,1]^2, 48 x 48 velocities on [-8,8]^2, a Gaussian density blob on a uniform
+flow, every cell kinetic, ARS(2,3,3), f stored in FP32 (six f-sized arrays of
+604 MB: the stage kernel streams from HBM).  Beside it, the coupled
+ES-BGK/Euler configuration (128 x 128 outflow cells, 32 x 32 velocities,
+four-quadrant Riemann data, plain switch) under the key riemann_128x32.
 A step is one full step of Algorithm 1 (regime update, three stages with
 coupling, final combination).  Metric: kinetic (cell x velocity) stage updates
 per second = sum over steps of K_kinetic * N_v^2 * (transport evaluations).
@@ -44,11 +47,13 @@ ELEM = {"fp64": 8, "fp32": 4, "bf16": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "bf16": "bf16-storage/f32"}
 
 
-def make_workload(name, seed):
+def make_workload(name, seed, nx=None):
+    """The workload recipe; nx (blob only) shrinks the grid to nx x nx cells
+    for profiling captures."""
     if name == "riemann":
         return W.riemann_quadrants(seed=seed)
     if name == "blob":
-        return W.gaussian_blob()
+        return W.gaussian_blob() if nx is None else W.gaussian_blob(nx=nx, ny=nx)
     if name == "sine":
         return W.sine_periodic()
     raise SystemExit("unknown workload " + name)
@@ -136,29 +141,72 @@ def switchnet_oracle_sample(steps):
     return x.shape[0] * 128 * 128 * steps / sum(per), desc, per
 
 
+def _sample(kind, steps, warmup=0):
+    """One bounded oracle sample of a workload kind (single process)."""
+    if kind == "batch":
+        return batch_oracle_sample(steps)
+    if kind == "switchnet":
+        return switchnet_oracle_sample(steps)
+    return oracle_sample(kind, steps, warmup=warmup)
+
+
+def _sample_worker(job):
+    kind, steps, warmup = job
+    t0 = time.perf_counter()
+    val, desc, per = _sample(kind, steps, warmup)
+    return val, desc, per, time.perf_counter() - t0
+
+
+def oracle_all_cores(kind, steps, warmup=0, procs=None):
+    """The oracle on every host core: one single-threaded process per core,
+    each running the same bounded sample (independent copies of the sampled
+    window, like the GPU's replicas).  Throughput = the work of all processes
+    over the slowest process's timed steps.  The pool is started with 'spawn'
+    (fresh interpreters that never touch the GPU).  Returns (value, desc,
+    per-step seconds of process 0, cores)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_sample_worker, [(kind, steps, warmup)] * procs)
+    per_proc = [sum(r[2]) for r in res]
+    work = sum(r[0] * sum(r[2]) for r in res)  # each process's units = its rate x its timed seconds
+    value = work / max(per_proc)
+    desc = res[0][1].replace("single-threaded", "%d single-threaded processes (one per host core)" % procs)
+    return value, desc, res[0][2], procs
+
+
+def cpu_baseline(kind, steps):
+    """cpu_baseline of a bench line: the oracle on all host cores, and on one."""
+    unit = "cells/s" if kind == "switchnet" else UNIT
+    v1, d1, _ = _sample(kind, steps)
+    va, da, _, cores = oracle_all_cores(kind, steps)
+    return {"value": va, "unit": unit, "cores": cores, "kind": "oracle", "sample": da,
+            "single_core": {"value": v1, "cores": 1, "sample": d1}}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     metric, unit = METRIC, UNIT
     if args.workload == "batch":
-        val, desc, per = batch_oracle_sample(args.steps)
         cfg = {"workload": batch_workload(args.cases), "cases": args.cases, "prec": "fp64"}
     elif args.workload == "learned":
-        val, desc, per = oracle_sample("learned", args.steps, warmup=args.warmup)
         cfg = {"workload": LEARNED_WORKLOAD, "prec": "fp64"}
     elif args.workload == "switchnet":
-        val, desc, per = switchnet_oracle_sample(args.steps)
         metric, unit = SWITCHNET_METRIC, "cells/s"
         cfg = {"workload": SWITCHNET_WORKLOAD, "features": 5, "hidden": 32, "prec": "fp64"}
     else:
-        val, desc, per = oracle_sample(args.workload, args.steps, warmup=args.warmup)
         cfg = describe(make_workload(args.workload, 0), args.workload, "fp64")
+    val, desc, per, cores = oracle_all_cores(args.workload, args.steps,
+                                             warmup=0 if args.workload in ("batch", "switchnet") else args.warmup)
+    # the oracle runs the same recipe on a bounded window, named here
+    cfg["sampled"] = desc
     out = {"metric": metric, "value": val, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "impl": "reference",
-           "cpu_baseline": {"value": val, "unit": unit, "cores": 1, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": val, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc},
            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -264,6 +312,129 @@ def combine_ranks(ms, updates, device, world):
     return float(mx[0]), float(t[1])
 
 
+def _measure(G, args, name, prec, steps, warmup, dev, world, local, rank, barrier, cpu_steps=0):
+    """Time `steps` steps of workload `name` on this rank's replica (seed =
+    rank): the device-timed line, the stage kernel's roofline, the end-to-end
+    figure through the C ABI and the clock record."""
+    import torch
+    wl = make_workload(name, rank, nx=args.nx if name == args.workload else None)
+    f = wl["fields"]
+    # a non-default stream: repeated steps replay as CUDA graphs
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
+    s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=prec, device=dev)
+    s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+    tab = G.make_tableau(wl["scheme"])
+    dt = wl["dt"]
+    nvv = wl["vmesh"]["nv"] ** 2
+    acc, nL = ACCESSES[wl["scheme"]]
+    ebytes = ELEM[prec]
+    for _ in range(warmup):
+        s.step(dt, tab)
+    s.sync()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    # --- timed region: K steps, L2 flushed before each (outside the events)
+    c0 = s.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.step(dt, tab)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    s.sync()
+    c1 = s.counters()
+    updates = (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv
+    fills_timed = c1["buffer_fills"] - c0["buffer_fills"]
+    ms_max, updates_all = combine_ranks(ms, float(updates), dev, world)
+    value = updates_all / (ms_max * 1e-3)
+    # algorithmic bytes of the timed steps (all stage launches) over the whole step time
+    step_bytes = updates * (acc / nL) * ebytes + fills_timed * nvv * ebytes
+
+    # --- per-kernel device times: the same steps as plain launches (no graph),
+    # an event pair around every launch on the launching stream
+    k2 = max(3, min(steps, 20))
+    s.timing(True)
+    s.timing_read()
+    cb = s.counters()
+    for k in range(k2):
+        flush.fill_(float(k))
+        s.step(dt, tab)
+    tk = s.timing_read()
+    s.timing(False)
+    ca = s.counters()
+    evals = ca["kinetic_cell_updates"] - cb["kinetic_cell_updates"]
+    fills = ca["buffer_fills"] - cb["buffer_fills"]
+    st_ms = tk["stage"][0] + tk["final"][0]
+    st_n = tk["stage"][1] + tk["final"][1]
+    algo_bytes = evals * nvv * (acc / nL) * ebytes + fills * nvv * ebytes
+    achieved = algo_bytes / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
+    peak, peak_src = measured_peak()
+    tr = stored_traffic(prec, name)
+    launches_per_step = (tk["l1"][1] + tk["flags"][1] + 2 * tk["compact"][1] + tk["prep"][1] + tk["stage"][1]
+                         + tk["final"][1]) / k2
+    step_ms_kernels = sum(v[0] for v in tk.values()) / k2
+
+    # --- end to end through the C ABI with pinned host buffers
+    nc = s.nc
+    pin = {k: torch.empty(nc, dtype=torch.float64).pin_memory().numpy() for k in ("rho", "ux", "uy", "T", "eps")}
+    mom = s.moments()
+    for q, k in enumerate(("rho", "ux", "uy", "T")):
+        pin[k][:] = mom[q].reshape(-1)
+    pin["eps"][:] = f["eps"].reshape(-1)
+    kin = torch.empty(nc, dtype=torch.uint8).pin_memory().numpy()
+    kin[:] = s.flags().reshape(-1)
+    outp = torch.empty((4, nc), dtype=torch.float64).pin_memory().numpy()
+    k3 = max(3, min(steps, 10))
+    e0 = s.counters()["kinetic_cell_updates"]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k3):
+        s.set_state(pin["rho"], pin["ux"], pin["uy"], pin["T"], pin["eps"], kin)
+        s.step(dt, tab)
+        s.moments(out=outp)
+    t_e2e = time.perf_counter() - t0
+    e_upd = (s.counters()["kinetic_cell_updates"] - e0) * nvv
+    kin_frac = c1["kinetic_cells"] / nc
+    s.close()
+    del flush
+
+    cfg = describe(wl, name, prec)
+    cfg.update({"l2": "flushed (256 MB write) before every timed step, outside the step's events",
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "kinetic_fraction_end": kin_frac, "kernel_launches_per_step": launches_per_step})
+    return {"value": value, "ms_per_step": ms_max / steps, "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": (tr * evals * nvv / st_n) if (tr is not None and st_n) else None,
+                         "kernel": "stage_kernel (fused IMEX stage + final combination)",
+                         "algorithmic_bytes_per_launch": algo_bytes / st_n if st_n else None,
+                         "avg_launch_ms": st_ms / st_n if st_n else None,
+                         "stage_ms_per_step": st_ms / k2, "peak_source": peak_src,
+                         "bytes_model": "%d f-array accesses per element per step / %d transport evaluations x %d B,"
+                                        " plus one write per buffer-cell element reconstructed" % (acc, nL, ebytes),
+                         "timing": "avg_launch_ms from CUDA events around each stage launch on its stream, in "
+                                   "plain launches of the same steps right after the timed region",
+                         "whole_step": {"achieved": step_bytes / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                                        "frac": step_bytes / (ms * 1e-3) / 1e9 / peak if ms > 0 else None,
+                                        "note": "algorithmic bytes of the timed steps' stage launches divided by "
+                                                "the whole timed step (every other launch of the step included)"}},
+            "kernel_ms_per_step": {k: v[0] / k2 for k, v in tk.items()},
+            "kernel_sum_ms_per_step": step_ms_kernels,
+            "e2e": {"value": e_upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * nc * 8 + nc,
+                    "d2h_bytes_per_step": 4 * nc * 8,
+                    "note": "each step: esbgk_set_state from pinned host arrays, which restarts the run from "
+                            "the macroscopic state and regime map (f rebuilt as the projected Maxwellian of U in "
+                            "kinetic cells), then esbgk_step, then esbgk_get_moments to pinned host arrays"},
+            "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * steps))}
+
+
 def ours_arm(args):
     import torch
     import torch.distributed as dist
@@ -281,122 +452,29 @@ def ours_arm(args):
         if world > 1:
             dist.barrier()
 
-    wl = make_workload(args.workload, rank)
-    f = wl["fields"]
-    # a non-default stream: repeated steps replay as CUDA graphs
-    torch.cuda.set_stream(torch.cuda.Stream(dev))
-    s = G.Solver(wl["grid"], wl["vmesh"], wl["params"], prec=args.prec, device=dev)
-    s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
-    tab = G.make_tableau(wl["scheme"])
-    dt = wl["dt"]
-    nvv = wl["vmesh"]["nv"] ** 2
-    acc, nL = ACCESSES[wl["scheme"]]
-    ebytes = ELEM[args.prec]
-    for _ in range(args.warmup):
-        s.step(dt, tab)
-    s.sync()
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-
-    # --- timed region: K steps, L2 flushed before each (outside the events)
-    c0 = s.counters()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            s.step(dt, tab)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    s.sync()
-    c1 = s.counters()
-    updates = (c1["kinetic_cell_updates"] - c0["kinetic_cell_updates"]) * nvv
-    ms_max, updates_all = combine_ranks(ms, float(updates), dev, world)
-    value = updates_all / (ms_max * 1e-3)
-
-    # --- per-kernel device times (separate pass; events around each launch)
-    k2 = max(3, min(args.steps, 20))
-    s.timing(True)
-    s.timing_read()
-    cb = s.counters()
-    for k in range(k2):
-        flush.fill_(float(k))
-        s.step(dt, tab)
-    tk = s.timing_read()
-    s.timing(False)
-    ca = s.counters()
-    evals = ca["kinetic_cell_updates"] - cb["kinetic_cell_updates"]
-    fills = ca["buffer_fills"] - cb["buffer_fills"]
-    st_ms = tk["stage"][0] + tk["final"][0]
-    st_n = tk["stage"][1] + tk["final"][1]
-    algo_bytes = evals * nvv * (acc / nL) * ebytes + fills * nvv * ebytes
-    achieved = algo_bytes / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
-    peak, peak_src = measured_peak()
-    tr = stored_traffic(args.prec, args.workload)
-    launches_per_step = (tk["l1"][1] + tk["flags"][1] + 2 * tk["compact"][1] + tk["prep"][1] + tk["stage"][1]
-                         + tk["final"][1]) / k2
-    step_ms_kernels = sum(v[0] for v in tk.values()) / k2
-
-    # --- end to end through the C ABI with pinned host buffers
-    nc = s.nc
-    pin = {k: torch.empty(nc, dtype=torch.float64).pin_memory().numpy() for k in ("rho", "ux", "uy", "T", "eps")}
-    mom = s.moments()
-    for q, k in enumerate(("rho", "ux", "uy", "T")):
-        pin[k][:] = mom[q].reshape(-1)
-    pin["eps"][:] = f["eps"].reshape(-1)
-    kin = torch.empty(nc, dtype=torch.uint8).pin_memory().numpy()
-    kin[:] = s.flags().reshape(-1)
-    outp = torch.empty((4, nc), dtype=torch.float64).pin_memory().numpy()
-    k3 = max(3, min(args.steps, 10))
-    e0 = s.counters()["kinetic_cell_updates"]
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(k3):
-        s.set_state(pin["rho"], pin["ux"], pin["uy"], pin["T"], pin["eps"], kin)
-        s.step(dt, tab)
-        s.moments(out=outp)
-    t_e2e = time.perf_counter() - t0
-    e_upd = (s.counters()["kinetic_cell_updates"] - e0) * nvv
-
-    kin_frac = c1["kinetic_cells"] / nc
+    m = _measure(G, args, args.workload, args.prec, args.steps, args.warmup, dev, world, local, rank, barrier)
+    extra = None
+    if args.workload == "blob" and not args.no_extra:
+        # the coupled Riemann configuration (128^2 cells, 32^2 velocities, plain switch) beside the headline
+        r = _measure(G, args, "riemann", args.prec, 50, args.warmup, dev, world, local, rank, barrier)
+        extra = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "steps": 50,
+                 "config": r["config"], "roofline": r["roofline"], "e2e": r["e2e"], "clocks": r["clocks"],
+                 "kernel_ms_per_step": r["kernel_ms_per_step"]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    cpu = None
+    out = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+           "config": m["config"], "roofline": m["roofline"], "kernel_ms_per_step": m["kernel_ms_per_step"],
+           "kernel_sum_ms_per_step": m["kernel_sum_ms_per_step"], "e2e": m["e2e"], "clocks": m["clocks"],
+           "gpu_launches": m["gpu_launches"]}
+    if extra:
+        out["riemann_128x32"] = extra
     if not args.no_cpu_baseline and world == 1:
-        cv, cdesc, _ = oracle_sample(args.workload, args.cpu_steps)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
-
-    cfg = describe(wl, args.workload, args.prec)
-    cfg.update({"l2": "flushed (256 MB write) before every timed step, outside the step's events",
-                "parallelism": "replicas" if world > 1 else "single GPU",
-                "kinetic_fraction_end": kin_frac, "kernel_launches_per_step": launches_per_step})
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic", "config": cfg,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": (achieved / peak) if achieved else None,
-                        "traffic": (tr * evals * nvv / st_n) if (tr is not None and st_n) else None,
-                        "kernel": "stage_kernel (fused IMEX stage + final combination)",
-                        "algorithmic_bytes_per_launch": algo_bytes / st_n if st_n else None,
-                        "avg_launch_ms": st_ms / st_n if st_n else None, "peak_source": peak_src,
-                        "bytes_model": "%d f-array accesses per element per step / %d transport evaluations x %d B,"
-                                       " plus one write per buffer-cell element reconstructed" % (acc, nL, ebytes)},
-           "kernel_ms_per_step": {k: v[0] / k2 for k, v in tk.items()},
-           "kernel_sum_ms_per_step": step_ms_kernels,
-           "e2e": {"value": e_upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * nc * 8 + nc,
-                   "d2h_bytes_per_step": 4 * nc * 8,
-                   "note": "each step: esbgk_set_state from pinned host arrays (restart from the macroscopic "
-                           "state and regime map), esbgk_step, esbgk_get_moments to pinned host arrays"},
-           "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
-    if cpu:
-        out["cpu_baseline"] = cpu
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_steps)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -525,8 +603,7 @@ def batch_arm(args):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cv, cdesc, _ = batch_oracle_sample(max(2, args.cpu_steps // 4))
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
+        cpu = cpu_baseline("batch", max(2, args.cpu_steps // 4))
     cfg = {"workload": batch_workload(len(cases)),
            "cases": len(cases), "cells": ncells, "elements": elems, "prec": args.prec,
            "l2": "flushed (256 MB write) before every timed step; f arrays far exceed L2",
@@ -687,8 +764,7 @@ def learned_arm(args):
                                           "error_ratio": l32["error_vs_all_kinetic"] / p64["error_vs_all_kinetic"]},
            "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
     if not args.no_cpu_baseline:
-        cv, cdesc, _ = oracle_sample("learned", args.cpu_steps)
-        out["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
+        out["cpu_baseline"] = cpu_baseline("learned", args.cpu_steps)
     print(json.dumps(out), flush=True)
 
 
@@ -773,18 +849,17 @@ def switchnet_arm(args):
            # (twice), input-gradient convolution, Adam = 10; per inference: two convolutions and the head
            "gpu_launches": k_tr * 10 + k_inf * 3}
     if not args.no_cpu_baseline:
-        cv, cdesc, _ = switchnet_oracle_sample(3)
-        out["cpu_baseline"] = {"value": cv, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": cdesc}
+        out["cpu_baseline"] = cpu_baseline("switchnet", 3)
     print(json.dumps(out), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "blob", "sine", "batch", "learned", "switchnet"])
+    ap.add_argument("--workload", default="blob", choices=["riemann", "blob", "sine", "batch", "learned", "switchnet"])
     ap.add_argument("--train-seeds", type=int, default=48)
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--sim-steps", type=int, default=100, help="steps of the learned-switch comparison runs")
@@ -792,6 +867,8 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=None, help="blob workload on nx x nx cells (profiling captures)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the coupled Riemann line beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
