@@ -8,12 +8,20 @@ eps (ny, nx) the Knudsen number field.  f is only meaningful in kinetic cells.
 """
 
 from dataclasses import dataclass, replace
+from functools import lru_cache
 
 import numpy as np
 
 from .kinetic import (velocity_grid, moments, cons_from_moments, cons_from_prim,
                       prim_from_cons, maxwellian_hat, es_gaussian_of, relax)
 from .transport import pad_cells, kinetic_transport, kinetic_face_fluxes, flux_moments, euler_phi
+from . import walls as Wl
+
+
+@lru_cache(maxsize=16)
+def _wall_maps(solid_bytes, ny, nx, bc_x, bc_y):
+    solid = Wl.check_solid(np.frombuffer(solid_bytes, bool).reshape(ny, nx), bc_x, bc_y)
+    return solid, Wl.stencil_maps(solid, bc_x, bc_y)
 
 
 @dataclass(frozen=True)
@@ -29,6 +37,9 @@ class Problem:
         criteria of Sec. 3.1.2 before every step (Algorithm 1).
     coupling: 'stage' couples at every stage (Algorithm 1), 'step' only at the
         end of the step (the LOC-hybrid of Sec. 3.5).
+    solid: None, or a bool mask (ny, nx) of solid obstacle cells (Sec. 4.2.3-
+        4.2.4): no integrator runs in them and their walls reflect
+        specularly (Reading R24, oracle.walls).
     tau_model: 'constant' -- tau fixed (Reading R2); 'density' -- tau = tau *
         rho (Sec. 2 lets tau depend on the macroscopic moments; Reading
         R23): the collision rate of a kinetic cell is nu = tau rho / eps with
@@ -60,6 +71,14 @@ class Problem:
     coupling: str = "stage"
     interface: str = "own"
     tau_model: str = "constant"
+    solid: object = None
+
+    @property
+    def walls(self):
+        """(solid mask, stencil maps) of the obstacles (reading R24), or None."""
+        if self.solid is None:
+            return None
+        return _wall_maps(np.asarray(self.solid, bool).tobytes(), self.ny, self.nx, self.bc_x, self.bc_y)
 
     @property
     def dx(self):
@@ -149,6 +168,8 @@ def init_state(prob, rho, ux, uy, T, eps, kin=None):
     (every test of Sec. 4 starts from a Maxwellian)."""
     U = np.moveaxis(cons_from_prim(rho, ux, uy, T), -1, 0).copy()
     kin = np.ones((prob.ny, prob.nx), bool) if kin is None else np.asarray(kin, bool).copy()
+    if prob.solid is not None:
+        kin &= ~np.asarray(prob.solid, bool)  # no integrator runs in a solid cell
     f = np.zeros((prob.ny, prob.nx, prob.nv, prob.nv))
     if kin.any():
         f[kin] = _mhat_of_U(prob, U[:, kin])
@@ -161,7 +182,10 @@ def macro(st):
 
 
 def totals(prob, st):
-    """Global mass, momentum and energy: sum over cells of U dx dy."""
+    """Global mass, momentum and energy: sum over cells of U dx dy (solid
+    cells hold no state and are left out)."""
+    if prob.solid is not None:
+        return st.U[:, ~np.asarray(prob.solid, bool)].sum(axis=1) * prob.dx * prob.dy
     return st.U.reshape(4, -1).sum(axis=1) * prob.dx * prob.dy
 
 
@@ -171,6 +195,14 @@ def buffer_mask(prob, kin):
     buffer region of Remark rem_coupling where f must be reconstructed."""
     ny, nx = kin.shape
     hit = np.zeros_like(kin)
+    if prob.walls is not None:
+        # the cells the kinetic stencils read, mirror images included
+        solid, maps = prob.walls
+        flat = hit.reshape(-1)
+        for src, _ in maps:
+            for k in (0, 1, 3, 4):
+                flat[src[k][kin]] = True
+        return hit & ~kin & ~solid
     J, I = np.nonzero(kin)
     for d in (-2, -1, 1, 2):
         ii = I + d
@@ -209,11 +241,24 @@ def regime_indicators(prob, st):
         return (ap[2:, :] - ap[:-2, :]) / (2.0 * dy)
 
     gu = np.empty(rho.shape + (2, 2))  # gu[..., a, b] = d u_a / d x_b
-    gu[..., 0, 0], gu[..., 0, 1] = ddx(ux), ddy(ux)
-    gu[..., 1, 0], gu[..., 1, 1] = ddx(uy), ddy(uy)
+    if prob.walls is None:
+        gu[..., 0, 0], gu[..., 0, 1] = ddx(ux), ddy(ux)
+        gu[..., 1, 0], gu[..., 1, 1] = ddx(uy), ddy(uy)
+        gT = np.stack([ddx(T), ddy(T)], axis=-1)
+    else:
+        # neighbour states across a wall are mirror states (reading R24)
+        solid, maps = prob.walls
+        Uc = np.moveaxis(st.U, 0, -1)
+        gT = np.empty(rho.shape + (2,))
+        for b, h in ((0, dx), (1, dy)):
+            lo, hi = Wl.neighbour_values(Uc, maps, b, Wl.reflect_U)
+            _, uxl, uyl, Tl = prim_from_cons(lo)
+            _, uxh, uyh, Th = prim_from_cons(hi)
+            gu[..., 0, b] = (uxh - uxl) / (2.0 * h)
+            gu[..., 1, b] = (uyh - uyl) / (2.0 * h)
+            gT[..., b] = (Th - Tl) / (2.0 * h)
     div = gu[..., 0, 0] + gu[..., 1, 1]
     D = gu + np.swapaxes(gu, -1, -2) - (2.0 / 3.0) * div[..., None, None] * np.eye(2)
-    gT = np.stack([ddx(T), ddy(T)], axis=-1)
     eps = st.eps
     tau = prob.tau * rho if prob.tau_model == "density" else prob.tau
     c1 = eps / (tau * (1.0 - prob.beta))
@@ -236,7 +281,10 @@ def regime_update(prob, st):
     go back to Euler)."""
     lamA, L1 = regime_indicators(prob, st)
     eta = prob.eta_factor * st.eps
-    return (lamA > eta) | (st.kin & (L1 > prob.delta))
+    new = (lamA > eta) | (st.kin & (L1 > prob.delta))
+    if prob.solid is not None:
+        new &= ~np.asarray(prob.solid, bool)  # no integrator runs in a solid cell
+    return new
 
 
 def convert(prob, st, new_kin):
@@ -261,7 +309,7 @@ def _interface_fluxes(prob, f, kin, v, w):
     one side and a fluid cell on the other (the faces i-1/2 of the ghost-padded
     map, as in the transport).  f must hold f in the kinetic and buffer cells,
     which cover the stencils of those faces."""
-    Fx, Fy = kinetic_face_fluxes(f, v, prob.bc_x, prob.bc_y, prob.cweno_eps)
+    Fx, Fy = kinetic_face_fluxes(f, v, prob.bc_x, prob.bc_y, prob.cweno_eps, prob.walls)
     out = []
     for F, axis, bc in ((Fx, 1, prob.bc_x), (Fy, 0, prob.bc_y)):
         k = pad_cells(kin, axis, bc, n=1)
@@ -294,6 +342,8 @@ def advance(prob, st, dt, tab):
     nu = prob.tau / st.eps
     s = tab.s
     args = (prob.dx, prob.dy, prob.bc_x, prob.bc_y, prob.cweno_eps)
+    walls = prob.walls
+    fluid_only = 1.0 if walls is None else (~walls[0]).astype(np.float64)  # solid cells keep U
 
     U_n = st.U.copy()
     f_n = np.zeros_like(st.f)
@@ -334,11 +384,12 @@ def advance(prob, st, dt, tab):
         else:
             U_i[:, kin] = U_n[:, kin]
             f_i[buf] = f_n[buf]
-        Ls.append(kinetic_transport(f_i, v, *args))
+        Ls.append(kinetic_transport(f_i, v, *args, walls=walls))
         if prob.interface == "conservative" and kin.any() and not kin.all():
-            Phis.append(euler_phi(U_i, *args, override=_interface_fluxes(prob, f_i, kin, v, w)))
+            Phis.append(fluid_only * euler_phi(U_i, *args, override=_interface_fluxes(prob, f_i, kin, v, w),
+                                               walls=walls))
         else:
-            Phis.append(euler_phi(U_i, *args))
+            Phis.append(fluid_only * euler_phi(U_i, *args, walls=walls))
         Qs.append(Q_i)
 
     f_new = st.f.copy()

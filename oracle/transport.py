@@ -105,27 +105,41 @@ def _divergence(F, axis, h):
             - np.take(F, np.arange(0, n), axis=axis)) / h
 
 
-def kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w):
+def _recon(eps_w):
+    def r(qm, q0, qp):
+        return cweno3_faces(qm, q0, qp, eps_w)
+    return r
+
+
+def kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w, walls=None):
     """The numerical fluxes of the kinetic transport at every face: Fx at the
     faces i-1/2 (i = 0..nx) along x, Fy at j-1/2 along y, per velocity node
-    (the F of kinetic_transport, whose divergence is L(f))."""
+    (the F of kinetic_transport, whose divergence is L(f)).  walls: None, or
+    (solid mask, stencil maps) of oracle.walls (specular walls, reading R24)."""
+    from . import walls as Wl
     vx = v[None, None, None, :]
     vy = v[None, None, :, None]
-    qm, qp = _face_states(f, 1, bc_x, eps_w)
+    if walls is None:
+        qm, qp = _face_states(f, 1, bc_x, eps_w)
+    else:
+        qm, qp = Wl.face_states(f, walls[0], walls[1], 0, bc_x, eps_w, Wl.reflect_f, _recon(eps_w))
     Fx = 0.5 * vx * (qm + qp) - 0.5 * np.abs(vx) * (qp - qm)
-    qm, qp = _face_states(f, 0, bc_y, eps_w)
+    if walls is None:
+        qm, qp = _face_states(f, 0, bc_y, eps_w)
+    else:
+        qm, qp = Wl.face_states(f, walls[0], walls[1], 1, bc_y, eps_w, Wl.reflect_f, _recon(eps_w))
     Fy = 0.5 * vy * (qm + qp) - 0.5 * np.abs(vy) * (qp - qm)
     return Fx, Fy
 
 
-def kinetic_transport(f, v, dx, dy, bc_x, bc_y, eps_w):
+def kinetic_transport(f, v, dx, dy, bc_x, bc_y, eps_w, walls=None):
     """L(f), the discretisation of v . grad_x f (Eq. semidiscrete ES-BGK).
 
     f: (ny, nx, nv, nv) indexed [j, i, vy, vx].  Per velocity node and axis the
     Lax-Friedrichs flux with the exact local speed,
     F = 1/2 v (q^- + q^+) - 1/2 |v| (q^+ - q^-), then L = dF/dx + dG/dy.
     """
-    Fx, Fy = kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w)
+    Fx, Fy = kinetic_face_fluxes(f, v, bc_x, bc_y, eps_w, walls)
     return _divergence(Fx, 1, dx) + _divergence(Fy, 0, dy)
 
 
@@ -151,7 +165,7 @@ def euler_flux(U, d):
                      un * (E + P)]), np.abs(un) + np.sqrt(GAMMA * P / rho)
 
 
-def euler_phi(U, dx, dy, bc_x, bc_y, eps_w, override=None):
+def euler_phi(U, dx, dy, bc_x, bc_y, eps_w, override=None, walls=None):
     """Phi(U), the discretisation of div_x F(U) (Eq. semidiscrete Euler).
 
     U: (4, ny, nx).  Component-wise CWENO3 face states and the local
@@ -159,11 +173,18 @@ def euler_phi(U, dx, dy, bc_x, bc_y, eps_w, override=None):
     a = max over the two states of |u_n| + sqrt(gamma P / rho).
     override: None, or ((Gx, mask_x), (Gy, mask_y)) -- face fluxes (4, ny,
     nx+1) / (4, ny+1, nx) that replace the Euler flux where the boolean face
-    mask is set.
+    mask is set.  walls: None, or (solid mask, stencil maps) of oracle.walls
+    (the mirror state across a wall, reading R24).
     """
+    from . import walls as Wl
     out = np.zeros_like(U)
     for k, (d, axis, h, bc) in enumerate(((0, 2, dx, bc_x), (1, 1, dy, bc_y))):
-        Um, Up = _face_states(U, axis, bc, eps_w)
+        if walls is None:
+            Um, Up = _face_states(U, axis, bc, eps_w)
+        else:
+            Uc = np.moveaxis(U, 0, -1)
+            Um, Up = Wl.face_states(Uc, walls[0], walls[1], d, bc, eps_w, Wl.reflect_U, _recon(eps_w))
+            Um, Up = np.moveaxis(Um, -1, 0), np.moveaxis(Up, -1, 0)
         Fm, am = euler_flux(Um, d)
         Fp, ap = euler_flux(Up, d)
         a = np.maximum(am, ap)

@@ -42,6 +42,12 @@ MUTATIONS = [
      "dissipation", "Euler flux with half the Lax-Friedrichs speed"),
     ("transport.py", "np.abs(un) + np.sqrt(GAMMA * P / rho)", "np.sqrt(GAMMA * P / rho)", "test_oracle_transport.py",
      "dissipation", "Euler flux speed without the flow speed |u_n|"),
+    ("walls.py", "return g[..., ::-1] if axis == 0 else g[..., ::-1, :]", "return g", "test_oracle_walls.py",
+     "symmetry", "wall mirror images of f without the specular reflection"),
+    ("walls.py", "pm = 2 * a + sg - p", "pm = 2 * a - p", "test_oracle_walls.py", "symmetry",
+     "wall mirror image one cell off"),
+    ("walls.py", "out[..., 1 + axis] *= -1.0", "out[..., 1 + axis] *= 1.0", "test_oracle_walls.py", "symmetry",
+     "Euler mirror state keeping the normal momentum"),
 ]
 
 
