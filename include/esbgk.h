@@ -60,6 +60,7 @@ typedef enum { ESBGK_SWITCH_FROZEN = 0, ESBGK_SWITCH_PLAIN = 1, ESBGK_SWITCH_LEA
 typedef enum { ESBGK_COUPLE_STAGE = 0, ESBGK_COUPLE_STEP = 1 } esbgk_coupling;
 typedef enum { ESBGK_INTERFACE_OWN = 0, ESBGK_INTERFACE_CONSERVATIVE = 1 } esbgk_interface;
 typedef enum { ESBGK_TAU_CONSTANT = 0, ESBGK_TAU_DENSITY = 1 } esbgk_tau_model;
+typedef enum { ESBGK_SUMS_PLAIN = 0, ESBGK_SUMS_COMPENSATED = 1 } esbgk_moment_sums;
 
 /* Cartesian grid of Sec. 3.2: N_x x N_y cells on [x0,x1] x [y0,y1]; two ghost
  * cells per side, periodic or outflow (copy of the edge cell). */
@@ -105,10 +106,20 @@ typedef struct {
  *             relaxation time scales with the density (Sec. 2 lets tau
  *             depend on the macroscopic moments): nu = tau rho / eps(x), rho
  *             of the cell's f* at each stage, and the criterion's viscosity
- *             and conductivity use tau rho.  Zero-initialised: CONSTANT. */
+ *             and conductivity use tau rho.  Zero-initialised: CONSTANT.
+ *  moment_sums  esbgk_moment_sums: how FP32 and BF16 storage sum the moments
+ *             of f* over the velocity nodes in the stages (Sec. 2: the
+ *             moments set the targets of the projected Gaussian, so their
+ *             rounding enters the relaxation's mass balance).  PLAIN --
+ *             paired per-lane partial sums and a butterfly over the lanes;
+ *             COMPENSATED -- the per-lane runs go every 16 nodes into a
+ *             Neumaier-compensated accumulator and the lanes are added with
+ *             error-free two-sums (several times smaller mass drift for a
+ *             few per cent of the step time).  No effect in FP64 storage.
+ *             Zero-initialised: PLAIN. */
 typedef struct {
   double beta, tau, eta_factor, delta, cweno_eps;
-  int32_t sw, coupling, prec, interface_flux, tau_model;
+  int32_t sw, coupling, prec, interface_flux, tau_model, moment_sums;
 } esbgk_params;
 
 /* IMEX tableaux (Sec. 3.4), 2 <= s <= 4 stages: explicit (At, bt) for the
@@ -167,6 +178,25 @@ int esbgk_regime_update(esbgk_ctx* ctx);
  * of the previous step. */
 int esbgk_set_flags(esbgk_ctx* ctx, const uint8_t* kinetic);
 
+/* Solid obstacles with specularly reflecting walls (Sec. 4.2.3-4.2.4, Tests 5
+ * and 6: a cylinder or a rectangle "such that the integrators are never
+ * executed in it" with specular reflection on its surface).  solid[N_c] (host,
+ * 1 = solid, cell order j*N_x + i), copied within the call; NULL or all zero
+ * removes the obstacles.  Call after esbgk_set_state (which keeps the mask).
+ * Solid cells hold no state, are never kinetic, buffer or fluid, and are left
+ * out of esbgk_totals.  Every stencil value a fluid or kinetic cell needs from
+ * beyond a wall is the mirror image, across the wall face, of a cell on its
+ * own side: f with the velocity component normal to the wall reversed
+ * (v_n -> -v_n: the node index along that axis reversed on the midpoint
+ * grid), and (rho, -m_n, m_t, E) for the Euler flux and the criterion's
+ * gradients; the mass and energy fluxes through a wall then vanish exactly.
+ * The paper gives no wall discretisation: this is the library's reading.
+ * Obstacles must stay three cells away from an outflow edge (a periodic axis
+ * wraps), and are not combined with the conservative interface, the learned
+ * switch or the batched form (ESBGK_E_ARG).  Problems with obstacles run the
+ * generic per-cell stage kernel.  Synchronises the stream. */
+int esbgk_set_solid(esbgk_ctx* ctx, const uint8_t* solid);
+
 /* Copy the current regime map to host kinetic[N_c]. */
 int esbgk_get_flags(esbgk_ctx* ctx, uint8_t* kinetic);
 
@@ -211,6 +241,20 @@ int esbgk_wait_probe(int32_t arrive, int32_t polls, void* stream);
  * the vector form for velocity grids of at most 512 nodes, one cell per
  * half-warp; else 1).  Host only, no launch; any pointer may be NULL. */
 int esbgk_kinetic_form(const esbgk_ctx* ctx, int32_t* nodes_per_group, int32_t* cells_per_warp);
+
+/* Tiled stage kernel (Sec. 3.2 transport, Eq. RKEI1-RKEI2): when every cell
+ * is kinetic (the last esbgk_set_state or esbgk_set_flags map) and the regime
+ * is frozen (ESBGK_SWITCH_FROZEN), the specialised stage launches run on
+ * tiles of 4 x 4 cells whose threads compute each CWENO3 face once and share
+ * it between the two cells it separates (the per-cell kernel computes every
+ * face twice).  Needs an even N_v and f* of 16 cells in shared memory
+ * (on GB300: N_v <= 54 in FP32/BF16 storage, N_v <= 34 in FP64); other
+ * problems keep the per-cell kernel.  Results agree with the per-cell kernel
+ * to rounding (a different but equivalent order of the face arithmetic).
+ * esbgk_tiles enables it (default) or disables it; host only, no launch.
+ * esbgk_tiled reports whether the next step's stages take it. */
+int esbgk_tiles(esbgk_ctx* ctx, int32_t enable);
+int esbgk_tiled(const esbgk_ctx* ctx, int32_t* tiled);
 
 /* Macroscopic fields of every cell (moments of f in kinetic cells, the Euler
  * solution elsewhere), each [N_c] float64; any pointer may be NULL. */
@@ -428,16 +472,20 @@ int esbgk_cnn_sync(esbgk_cnn* c);
 /* Allocation-free stepping of an all-kinetic problem.  (The paper has no
  * counterpart: this is a service for callers.)
  *
- * Who needs it: code that must not call cudaMalloc or any allocating library
- * routine -- work launched while a CUDA stream is being captured into a graph,
- * a host that owns every device allocation through its own pool or budget, or
- * a real-time loop that may not touch the allocator.  Every other entry point
- * needs a caller-provided workspace (esbgk_create); this one needs none.
+ * Who needs it: callers that cannot allocate device memory at all -- a plugin
+ * or embedded solver inside a host application that owns every device
+ * allocation through its own pool or fixed budget (an allocation of ours would
+ * bypass its accounting or fail), or a latency-bound loop that must never
+ * enter the allocator.  Every other entry point needs a caller-provided
+ * workspace (esbgk_create), which such a caller may not be able to obtain;
+ * this one needs none.
  *
  * It advances f by `nsteps` IMEX steps (dt, tab) with every cell kinetic and
  * the regime frozen (params->sw and params->coupling are validated but make no
  * difference when no cell is fluid), exactly as esbgk_create + esbgk_set_f +
- * esbgk_step would.  The caller passes, in device memory:
+ * esbgk_step would (with BF16 storage the stochastic-rounding keys restart at
+ * every call, as in a fresh context, so a sequence of calls agrees with one
+ * long run to the BF16 rounding bound rather than bit for bit).  The caller passes, in device memory:
  *   f    in/out [N_c][N_v][N_v], storage type of params->prec (f^n in,
  *        f^{n+nsteps} out);
  *   eps  in [N_c] float64, the Knudsen number;
@@ -446,7 +494,8 @@ int esbgk_cnn_sync(esbgk_cnn* c);
  * 32 MiB that the library keeps on every GPU it is loaded on until the process
  * exits.  The problem fits when
  *   5 * N_c * N_v^2 * (8, 4 or 2 bytes for FP64, FP32, BF16)
- *     + 68 * N_c + 3 KiB  <=  32 MiB  (each array rounded up to 256 bytes);
+ *     + 68 * N_c + 3 KiB  <=  32 MiB  (each array rounded up to 256 bytes;
+ *   the 3 KiB hold the counters, the error word and the rounding key);
  * larger problems are rejected with ESBGK_E_TOO_LARGE before any device work.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture begins.

@@ -38,6 +38,7 @@ CNN_PARAMS, CNN_CHANNELS = 10753, 16
 COUPLING = {"stage": 0, "step": 1}
 INTERFACE = {"own": 0, "conservative": 1}
 TAU_MODEL = {"constant": 0, "density": 1}
+MOMENT_SUMS = {"plain": 0, "compensated": 1}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 
 __all__ = ["Solver", "BatchSolver", "SwitchNet", "make_tableau", "ARS233", "IMEX_EULER", "relax_cells", "Error"]
@@ -104,7 +105,8 @@ def _structs(_abi, grid, vmesh, params, prec):
     q = _abi.Params(float(p.get("beta", -0.5)), float(p.get("tau", 1.0)), float(p.get("eta_factor", 1.0)),
                     float(p.get("delta", 1e-3)), float(p.get("cweno_eps", 1e-6)),
                     SWITCH[p.get("switch", "frozen")], COUPLING[p.get("coupling", "stage")], PREC[prec],
-                    INTERFACE[p.get("interface", "own")], TAU_MODEL[p.get("tau_model", "constant")])
+                    INTERFACE[p.get("interface", "own")], TAU_MODEL[p.get("tau_model", "constant")],
+                    MOMENT_SUMS[p.get("moment_sums", "plain")])
     return g, v, q
 
 
@@ -115,7 +117,8 @@ class Solver:
     vmesh: nv, vmax
     params: beta, tau, eta_factor, delta, cweno_eps, switch ('frozen' | 'plain'),
             coupling ('stage' | 'step'), interface ('own' | 'conservative'),
-            tau_model ('constant' | 'density');
+            tau_model ('constant' | 'density'),
+            moment_sums ('plain' | 'compensated': FP32/BF16 moment sums);
             prec: 'fp64' | 'fp32' | 'bf16'.
     """
 
@@ -185,6 +188,15 @@ class Solver:
         k = np.ascontiguousarray(np.asarray(kin).reshape(-1), dtype=np.uint8)
         self._check(self._abi.esbgk_set_flags(self._ctx, _u8ptr(k)), "set_flags")
 
+    def set_solid(self, solid):
+        """Solid obstacles with specular walls: a bool mask (ny, nx), or None
+        to remove them (call after set_state)."""
+        if solid is None:
+            self._check(self._abi.esbgk_set_solid(self._ctx, None), "set_solid")
+            return
+        m = np.ascontiguousarray(np.asarray(solid).reshape(-1), dtype=np.uint8)
+        self._check(self._abi.esbgk_set_solid(self._ctx, _u8ptr(m)), "set_solid")
+
     def flags(self):
         out = np.empty((self.ny, self.nx), np.uint8)
         self._check(self._abi.esbgk_get_flags(self._ctx, _u8ptr(out)), "get_flags")
@@ -240,6 +252,17 @@ class Solver:
         w, p = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._abi.esbgk_kinetic_form(self._ctx, ctypes.byref(w), ctypes.byref(p)), "kinetic form")
         return w.value, p.value
+
+    def tiles(self, enable=True):
+        """Enable or disable the tiled stage kernel (every cell kinetic,
+        regime frozen)."""
+        self._check(self._abi.esbgk_tiles(self._ctx, int(bool(enable))), "tiles")
+
+    def tiled(self):
+        """Whether the next step's stage launches take the tiled kernel."""
+        t = ctypes.c_int32()
+        self._check(self._abi.esbgk_tiled(self._ctx, ctypes.byref(t)), "tiled")
+        return bool(t.value)
 
     def timing(self, enable=True):
         """Bracket every library kernel with CUDA events on the stream."""

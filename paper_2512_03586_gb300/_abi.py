@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("eta_factor", ctypes.c_double),
                 ("delta", ctypes.c_double), ("cweno_eps", ctypes.c_double), ("sw", ctypes.c_int32),
                 ("coupling", ctypes.c_int32), ("prec", ctypes.c_int32), ("interface_flux", ctypes.c_int32),
-                ("tau_model", ctypes.c_int32)]
+                ("tau_model", ctypes.c_int32), ("moment_sums", ctypes.c_int32)]
 
 
 class Tableau(ctypes.Structure):
@@ -92,6 +92,9 @@ _SIGS = {
     "esbgk_counters": (I, [P, LL, LL, LL, LL]),
     "esbgk_graphs": (I, [P, ctypes.c_int32]),
     "esbgk_kinetic_form": (I, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_tiles": (I, [P, ctypes.c_int32]),
+    "esbgk_set_solid": (I, [P, ctypes.c_void_p]),
+    "esbgk_tiled": (I, [P, ctypes.POINTER(ctypes.c_int32)]),
     "esbgk_wait_probe": (I, [ctypes.c_int32, ctypes.c_int32, P]),
     "esbgk_timing": (I, [P, I]),
     "esbgk_timing_read": (I, [P, D, LL, ctypes.c_int32]),

@@ -35,6 +35,7 @@ const Launchers* launchers_for(int prec) {
 struct Layout {
   size_t F[3], ACC[3], Un, Us[2], Phi, eps, lamA, L1, stage5, red, tot;
   size_t flags, flags_prev, cat, klist, blist, flist, clist, counts, err, ctr, wq, blockc, seed;
+  size_t wsrc, wrefl, solid;  // obstacles: stencil maps and the solid mask
   // learned switch only: features, activations, logits, prediction, weights, statistics
   size_t cx, ca1, ca2, logits, pred, cnnw, sctr;
   size_t total;
@@ -76,6 +77,9 @@ Layout make_layout(int nc, int nvv, size_t elem, bool learned) {
   L.wq = take((kMaxStages + 1) * sizeof(int));
   L.blockc = take(4 * (size_t)categorize_blocks(nc) * sizeof(int));
   L.seed = take(sizeof(unsigned));
+  L.wsrc = take(8 * (size_t)nc * sizeof(int));
+  L.wrefl = take(8 * (size_t)nc);
+  L.solid = take(nc);
   if (learned) {
     L.cx = take((size_t)nc * cnn::kCinPad * 2);
     L.ca1 = take((size_t)nc * cnn::kHid * 2);
@@ -103,6 +107,7 @@ bool valid_inputs(const esbgk_grid* g, const esbgk_vmesh* v, const esbgk_params*
   if (p->coupling != ESBGK_COUPLE_STAGE && p->coupling != ESBGK_COUPLE_STEP) return false;
   if (p->interface_flux != ESBGK_INTERFACE_OWN && p->interface_flux != ESBGK_INTERFACE_CONSERVATIVE) return false;
   if (p->tau_model != ESBGK_TAU_CONSTANT && p->tau_model != ESBGK_TAU_DENSITY) return false;
+  if (p->moment_sums != ESBGK_SUMS_PLAIN && p->moment_sums != ESBGK_SUMS_COMPENSATED) return false;
   return launchers_for(p->prec) != nullptr;
 }
 
@@ -160,6 +165,10 @@ struct esbgk_ctx {
   int* wq = nullptr;  // work counters of the stage launches of a step
   int* blockc = nullptr;  // per-block category counts of the compaction
   unsigned* seed = nullptr;  // step counter of the stochastic rounding of bf16 stores
+  // solid obstacles (esbgk_set_solid): stencil maps and mask; walls = false: none
+  int* wsrc = nullptr;
+  uint8_t *wrefl = nullptr, *solid = nullptr;
+  bool walls = false;
   int cur;
   bool have_state, conv_pending;
   bool l1_fresh;  // L1 holds ||f^n - M_hat||_1 of the kinetic cells (from the last final combination)
@@ -180,6 +189,11 @@ struct esbgk_ctx {
   GraphEntry graphs[3];
   std::vector<unsigned char> last_key;  // key of the previous un-captured step
   bool graphs_on = true;
+  // every cell kinetic as far as the host knows (the last set_state or
+  // set_flags map); with the regime frozen the stages may use the tiled kernel
+  bool all_kin = false;
+  bool tiles_on = true;
+  bool tiled() const { return tiles_on && all_kin && sw == ESBGK_SWITCH_FROZEN; }
   void drop_graphs() {
     for (auto& e : graphs) {
       if (e.exec) cudaGraphExecDestroy(e.exec);
@@ -225,6 +239,9 @@ struct esbgk_ctx {
     V.clist = clist;
     V.counts = counts;
     V.err = err;
+    V.wsrc = walls ? wsrc : nullptr;
+    V.wrefl = walls ? wrefl : nullptr;
+    V.solid = walls ? solid : nullptr;
     return V;
   }
 };
@@ -532,10 +549,14 @@ int advance_launches(esbgk_ctx* X, const StepPlan& PL) {
   }
   int r = after_launch(X, "prep kernel");
   if (r) return r;
+  const bool tiles = X->tiled();
   for (int q = 0; q < PL.n; ++q) {
     {
       Timed t(X, PL.fin[q] ? ESBGK_K_FINAL : ESBGK_K_STAGE);
-      X->L->stage(PL.st[q], V, X->grid_stage, X->stream);
+      if (tiles && X->L->tile_ok(PL.st[q], X->g))
+        X->L->stage_tile(PL.st[q], V, X->grid_stage, X->stream);
+      else
+        X->L->stage(PL.st[q], V, X->grid_stage, X->stream);
     }
     if ((r = after_launch(X, PL.fin[q] ? "final kernel" : "stage kernel"))) return r;
   }
@@ -580,11 +601,12 @@ int step_all(esbgk_ctx* X, double dt, const esbgk_tableau* T) {
     X->have_pred = saved_pred;
     return r;
   }
-  std::vector<unsigned char> key(3 + sizeof PL);
+  std::vector<unsigned char> key(4 + sizeof PL);
   key[0] = crit;
   key[1] = l1_needed;
   key[2] = judge_prev;
-  memcpy(key.data() + 3, &PL, sizeof PL);
+  key[3] = X->tiled();
+  memcpy(key.data() + 4, &PL, sizeof PL);
   esbgk_ctx::GraphEntry* hit = nullptr;
   for (auto& e : X->graphs)
     if (e.exec && e.key == key) hit = &e;
@@ -692,6 +714,7 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->m.beta = params->beta;
   X->m.tau = params->tau;
   X->m.tau_rho = params->tau_model == ESBGK_TAU_DENSITY ? 1 : 0;
+  X->m.comp_moments = params->moment_sums == ESBGK_SUMS_COMPENSATED ? 1 : 0;
   X->m.eps_w = params->cweno_eps;
   X->m.eta_factor = params->eta_factor;
   X->m.delta = params->delta;
@@ -731,6 +754,9 @@ int esbgk_create(const esbgk_grid* grid, const esbgk_vmesh* vmesh, const esbgk_p
   X->wq = (int*)(w + lay.wq);
   X->blockc = (int*)(w + lay.blockc);
   X->seed = (unsigned*)(w + lay.seed);
+  X->wsrc = (int*)(w + lay.wsrc);
+  X->wrefl = w + lay.wrefl;
+  X->solid = w + lay.solid;
   if (X->sw == ESBGK_SWITCH_LEARNED) {
     X->cx = (__nv_bfloat16*)(w + lay.cx);
     X->ca1 = (__nv_bfloat16*)(w + lay.ca1);
@@ -792,8 +818,14 @@ int esbgk_set_state(esbgk_ctx* X, const double* rho, const double* ux, const dou
     r = cuda_check(X, cudaMemcpyAsync(X->cat, kinetic, nc, cudaMemcpyHostToDevice, X->stream), "flags copy");
   if (!r) r = cuda_check(X, cudaMemsetAsync(X->err, 0, sizeof(DevErr), X->stream), "clear error word");
   if (r) return r;
+  X->all_kin = !X->walls;
+  for (int c = 0; kinetic && c < nc && X->all_kin; ++c) X->all_kin = kinetic[c] != 0;
   launch_init_state(X->stage5, kinetic ? X->cat : nullptr, X->Un, X->eps, X->flags, X->flags_prev, nc, X->stream);
   if ((r = after_launch(X, "init kernel"))) return r;
+  if (X->walls) {  // no integrator runs in a solid cell
+    launch_clear_solid(X->flags, X->flags_prev, X->solid, nc, X->stream);
+    if ((r = after_launch(X, "solid mask"))) return r;
+  }
   if ((r = compact(X))) return r;
   // f = M_hat[U] in kinetic cells
   PrepArgs P{};
@@ -902,12 +934,111 @@ int esbgk_set_flags(esbgk_ctx* X, const uint8_t* kinetic) {
   NEED_STATE(X);
   if (!kinetic) return ESBGK_E_ARG;
   std::vector<uint8_t> k(X->g.nc);
-  for (int c = 0; c < X->g.nc; ++c) k[c] = kinetic[c] ? 1 : 0;
+  bool all = true;
+  for (int c = 0; c < X->g.nc; ++c) {
+    k[c] = kinetic[c] ? 1 : 0;
+    all = all && k[c];
+  }
+  X->all_kin = all;
   int r = cuda_check(X, cudaMemcpyAsync(X->flags, k.data(), k.size(), cudaMemcpyHostToDevice, X->stream),
                      "set_flags copy");
   if (!r) r = compact(X);
   if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_flags sync");
   if (!r) X->conv_pending = true;
+  X->l1_fresh = false;
+  return r;
+}
+
+// Stencil of every cell with specular walls (reading R24 of the design
+// notes): per axis and offset d in (-2, -1, +1, +2) the source cell and
+// whether it is a mirror image.  Walking from the cell toward c + d, the first
+// solid cell w found (if any) makes the value the mirror, across the face
+// between a = w - sign(d) and w, of position c + d: 2a + sign(d) - (c + d),
+// or a itself when that position is solid too.  Boundary conditions map every
+// position first (obstacles stay off outflow edges, so they never meet).
+static void wall_maps(const Geo& g, const uint8_t* solid, std::vector<int>& src, std::vector<uint8_t>& refl) {
+  const int nc = g.nc;
+  src.assign(8 * (size_t)nc, 0);
+  refl.assign(8 * (size_t)nc, 0);
+  const int off[4] = {-2, -1, 1, 2};
+  for (int axis = 0; axis < 2; ++axis) {
+    const int n = axis == 0 ? g.nx : g.ny, bc = axis == 0 ? g.bcx : g.bcy;
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const int c = axis == 0 ? i : j, me = j * g.nx + i;
+        auto cell = [&](int pos) {
+          const int q = bc == 0 ? ((pos % n) + n) % n : (pos < 0 ? 0 : (pos >= n ? n - 1 : pos));
+          return axis == 0 ? j * g.nx + q : q * g.nx + i;
+        };
+        for (int e = 0; e < 4; ++e) {
+          const int d = off[e], p = c + d, sg = d > 0 ? 1 : -1;
+          const size_t at = (size_t)(axis * 4 + e) * nc + me;
+          int w = 0;
+          bool hit = false;
+          if (!solid[me])
+            for (int t = c + sg; t != p + sg && !hit; t += sg)
+              if (solid[cell(t)]) {
+                w = t;
+                hit = true;
+              }
+          if (!hit) {
+            src[at] = cell(p);
+            continue;
+          }
+          const int a = w - sg;
+          int pm = 2 * a + sg - p;
+          if (solid[cell(pm)]) pm = a;
+          src[at] = cell(pm);
+          refl[at] = 1;
+        }
+      }
+  }
+}
+
+int esbgk_set_solid(esbgk_ctx* X, const uint8_t* solid) {
+  GUARD(X);
+  NEED_STATE(X);
+  const Geo& g = X->g;
+  int r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_solid sync");
+  if (r) return r;
+  X->drop_graphs();
+  if (!solid) {
+    X->walls = false;
+    return ESBGK_OK;
+  }
+  if (X->iface == ESBGK_INTERFACE_CONSERVATIVE || X->sw == ESBGK_SWITCH_LEARNED)
+    return fail(X, ESBGK_E_ARG, "set_solid: obstacles are not combined with the conservative interface or the "
+                                "learned switch");
+  std::vector<uint8_t> m(g.nc);
+  bool any = false;
+  for (int c = 0; c < g.nc; ++c) {
+    m[c] = solid[c] ? 1 : 0;
+    any = any || m[c];
+    const int i = c % g.nx, j = c / g.nx;
+    if (m[c] && ((g.bcx == 1 && (i < 3 || i > g.nx - 4)) || (g.bcy == 1 && (j < 3 || j > g.ny - 4))))
+      return fail(X, ESBGK_E_ARG, "set_solid: obstacles must stay three cells away from an outflow edge");
+  }
+  if (!any) {
+    X->walls = false;
+    return ESBGK_OK;
+  }
+  std::vector<int> src;
+  std::vector<uint8_t> refl;
+  wall_maps(g, m.data(), src, refl);
+  r = cuda_check(X, cudaMemcpyAsync(X->solid, m.data(), g.nc, cudaMemcpyHostToDevice, X->stream), "solid copy");
+  if (!r)
+    r = cuda_check(X, cudaMemcpyAsync(X->wsrc, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, X->stream),
+                   "wall map copy");
+  if (!r)
+    r = cuda_check(X, cudaMemcpyAsync(X->wrefl, refl.data(), refl.size(), cudaMemcpyHostToDevice, X->stream),
+                   "wall map copy");
+  if (r) return r;
+  X->walls = true;
+  X->all_kin = false;
+  launch_clear_solid(X->flags, X->flags_prev, X->solid, g.nc, X->stream);
+  if ((r = after_launch(X, "solid mask"))) return r;
+  r = compact(X);
+  if (!r) r = cuda_check(X, cudaStreamSynchronize(X->stream), "set_solid sync");  // the host vectors go out of scope
   X->l1_fresh = false;
   return r;
 }
@@ -975,7 +1106,8 @@ int esbgk_totals(esbgk_ctx* X, double out[4]) {
   GUARD(X);
   NEED_STATE(X);
   if (!out) return ESBGK_E_ARG;
-  launch_totals(X->Un, X->g.nc, X->red, X->tot, X->g.dx * X->g.dy, X->grid_red, X->stream);
+  launch_totals(X->Un, X->walls ? X->solid : nullptr, X->g.nc, X->red, X->tot, X->g.dx * X->g.dy, X->grid_red,
+                X->stream);
   int r = after_launch(X, "totals kernels");
   if (!r) r = cuda_check(X, cudaMemcpyAsync(out, X->tot, 4 * sizeof(double), cudaMemcpyDeviceToHost, X->stream),
                          "totals copy");
@@ -1004,6 +1136,25 @@ int esbgk_graphs(esbgk_ctx* X, int32_t enable) {
   if (r) return r;
   X->graphs_on = enable != 0;
   X->drop_graphs();
+  return ESBGK_OK;
+}
+
+int esbgk_tiles(esbgk_ctx* X, int32_t enable) {
+  GUARD(X);
+  X->tiles_on = enable != 0;
+  return ESBGK_OK;
+}
+
+int esbgk_tiled(const esbgk_ctx* X, int32_t* tiled) {
+  GUARD(X);
+  if (!tiled) return ESBGK_E_ARG;
+  StageArgs A;  // a relaxed first stage over the context's own f arrays
+  memset(&A, 0, sizeof A);
+  A.f_src = X->F[0];
+  A.star_base = X->F[0];
+  A.f_out = X->F[1];
+  A.h_coef = 1.0;
+  *tiled = X->tiled() && X->L->tile_ok(A, X->g) ? 1 : 0;
   return ESBGK_OK;
 }
 
@@ -1663,8 +1814,10 @@ cudaError_t noalloc_scratch(unsigned char** out) {
 }
 
 // Every cell kinetic: klist = 0..nc-1, no buffer/fluid/converted cells; clear
-// the error word and the counters.
-__global__ void noalloc_init_kernel(int* klist, int* counts, DevErr* err, long long* ctr, int nc) {
+// the error word, the counters and the step counter of the bf16 rounding keys
+// (so that a call's results do not depend on earlier calls).
+__global__ void noalloc_init_kernel(int* klist, int* counts, DevErr* err, long long* ctr, unsigned* seed,
+                                    int nc) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nc) klist[c] = c;
   if (c == 0) {
@@ -1673,6 +1826,7 @@ __global__ void noalloc_init_kernel(int* klist, int* counts, DevErr* err, long l
     err->code = 0;
     err->cell = -1;
     ctr[0] = ctr[1] = 0;
+    *seed = 0u;
   }
 }
 
@@ -1693,7 +1847,8 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   const size_t off_cnt = off_kl + up((size_t)g.nc * sizeof(int));
   const size_t off_err = off_cnt + up(4 * sizeof(int));
   const size_t off_ctr = off_err + up(sizeof(DevErr));
-  const size_t need = off_ctr + up(2 * sizeof(long long));
+  const size_t off_seed = off_ctr + up(2 * sizeof(long long));
+  const size_t need = off_seed + up(sizeof(unsigned));
   if (need > kNoallocScratchBytes) return ESBGK_E_TOO_LARGE;
   unsigned char* base = nullptr;
   if (noalloc_scratch(&base) != cudaSuccess) return ESBGK_E_CUDA;
@@ -1709,6 +1864,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.m.beta = params->beta;
   X.m.tau = params->tau;
   X.m.tau_rho = params->tau_model == ESBGK_TAU_DENSITY ? 1 : 0;
+  X.m.comp_moments = params->moment_sums == ESBGK_SUMS_COMPENSATED ? 1 : 0;
   X.m.eps_w = params->cweno_eps;
   X.m.eta_factor = params->eta_factor;
   X.m.delta = params->delta;
@@ -1737,7 +1893,11 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.counts = (int*)(base + off_cnt);
   X.err = (DevErr*)(base + off_err);
   X.ctr = (long long*)(base + off_ctr);
+  // bf16 stores round stochastically with a key that advances every step, as
+  // in a workspace context
+  X.seed = (unsigned*)(base + off_seed);
   X.cur = 0;
+  X.all_kin = true;
   X.have_state = true;
   X.conv_pending = false;
   X.l1_fresh = false;
@@ -1745,7 +1905,7 @@ extern "C" int esbgk_kinetic_steps_noalloc(const esbgk_grid* grid, const esbgk_v
   X.status = ESBGK_OK;
   X.bad_cell = -1;
 
-  noalloc_init_kernel<<<(g.nc + 255) / 256, 256, 0, X.stream>>>(X.klist, X.counts, X.err, X.ctr, g.nc);
+  noalloc_init_kernel<<<(g.nc + 255) / 256, 256, 0, X.stream>>>(X.klist, X.counts, X.err, X.ctr, X.seed, g.nc);
   if (cudaGetLastError() != cudaSuccess) return ESBGK_E_CUDA;
   // U^n from f: the steps read it (reference velocity of the moment sums,
   // the stage-start copy), and the caller's U is an output only

@@ -37,6 +37,7 @@ struct Model {
   double beta, tau, eps_w, eta_factor, delta;
   float fbeta, ftau, feps_w;
   int tau_rho;  // relaxation time tau * rho (else tau)
+  int comp_moments;  // compensated FP32 moment sums
 };
 
 // The double or the float copy of a constant, for arithmetic type R.

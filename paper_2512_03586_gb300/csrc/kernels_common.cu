@@ -20,6 +20,15 @@ __global__ void init_state_kernel(const double* __restrict__ prim, const uint8_t
   flags_prev[c] = k;
 }
 
+__global__ void clear_solid_kernel(uint8_t* flags, uint8_t* flags_prev, const uint8_t* __restrict__ solid, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc && solid[c]) flags[c] = flags_prev[c] = 0;
+}
+
+void launch_clear_solid(uint8_t* flags, uint8_t* flags_prev, const uint8_t* solid, int nc, cudaStream_t s) {
+  clear_solid_kernel<<<(nc + 255) / 256, 256, 0, s>>>(flags, flags_prev, solid, nc);
+}
+
 void launch_init_state(const double* prim, const uint8_t* kin_in, double* Un, double* eps, uint8_t* flags,
                        uint8_t* flags_prev, int nc, cudaStream_t s) {
   init_state_kernel<<<(nc + 255) / 256, 256, 0, s>>>(prim, kin_in, Un, eps, flags, flags_prev, nc);
@@ -144,9 +153,50 @@ __global__ void __launch_bounds__(kFX* kFY) flags_tile_kernel(View V, const doub
                    sp[h0 - HX]);
 }
 
+// The criterion with solid obstacles: a neighbour across a wall is the
+// mirror state of the cell's own side (the stencil maps of View, normal
+// velocity reversed); solid cells are never kinetic.
+template <typename R>
+__global__ void flags_walls_kernel(View V, const double* __restrict__ Un, const double* __restrict__ L1in,
+                                   double* L1out, double* lamA, uint8_t* flags_out) {
+  const Geo& g = V.g;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nc) return;
+  if (V.solid[c]) {
+    lamA[c] = 0.0;
+    L1out[c] = 0.0;
+    flags_out[c] = 0;
+    return;
+  }
+  Prims<R> P0, Pn[4];  // east, west, north, south: offsets +1, -1 along x, then y
+  prim_cell(Un, g.nc, c, P0.rho, P0.ux, P0.uy, P0.T);
+  const int slot[4] = {2, 1, 2, 1};  // offset index of +1 and -1 in (-2, -1, +1, +2)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int axis = q / 2, at = (axis * 4 + slot[q]) * g.nc + c;
+    Prims<R>& P = Pn[q];
+    prim_cell(Un, g.nc, V.wsrc[at], P.rho, P.ux, P.uy, P.T);
+    if (V.wrefl[at]) {
+      if (axis == 0)
+        P.ux = -P.ux;
+      else
+        P.uy = -P.uy;
+    }
+  }
+  flags_from_prims(V, L1in, L1out, lamA, flags_out, c, true, P0, Pn[0], Pn[1], Pn[2], Pn[3]);
+}
+
 void launch_flags(const View& V, const double* Un, const double* L1in, double* L1out, double* lamA,
                   uint8_t* flags_out, bool fp32, cudaStream_t s) {
   const dim3 grid((V.g.nx + kFX - 1) / kFX, (V.g.ny + kFY - 1) / kFY);
+  if (V.wsrc) {
+    const int nb = (V.g.nc + 255) / 256;
+    if (fp32)
+      flags_walls_kernel<float><<<nb, 256, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+    else
+      flags_walls_kernel<double><<<nb, 256, 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
+    return;
+  }
   if (fp32)
     flags_tile_kernel<float><<<grid, dim3(kFX, kFY), 0, s>>>(V, Un, L1in, L1out, lamA, flags_out);
   else
@@ -156,7 +206,9 @@ void launch_flags(const View& V, const double* Un, const double* L1in, double* L
 // Category of each cell: 0 kinetic, 1 buffer (fluid cell inside the two-cell
 // cross stencil of a kinetic cell, Remark rem_coupling), 2 other fluid; bit 2
 // (value 4) marks a kinetic cell that was fluid in the previous step.
-__device__ int category_of(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev, int c) {
+__device__ int category_of(const Geo& g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev, int c,
+                           const uint8_t* __restrict__ solid = nullptr) {
+  if (solid && solid[c]) return 3;  // solid: in no list
   if (flags[c]) return prev[c] ? 0 : 4;
   const int i = c % g.nx, j = c / g.nx;
   bool hit = false;
@@ -175,14 +227,14 @@ __device__ void categorize_cell(const Geo& g, const uint8_t* __restrict__ flags,
 }
 
 __global__ void categorize_kernel(Geo g, const uint8_t* __restrict__ flags, const uint8_t* __restrict__ prev,
-                                  uint8_t* cat) {
+                                  uint8_t* cat, const uint8_t* __restrict__ solid) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < g.nc) categorize_cell(g, flags, prev, cat, c);
+  if (c < g.nc) cat[c] = (uint8_t)category_of(g, flags, prev, c, solid);
 }
 
 void launch_categorize(const View& V, const uint8_t* flags, const uint8_t* flags_prev, uint8_t* cat,
                        cudaStream_t s) {
-  categorize_kernel<<<(V.g.nc + 255) / 256, 256, 0, s>>>(V.g, flags, flags_prev, cat);
+  categorize_kernel<<<(V.g.nc + 255) / 256, 256, 0, s>>>(V.g, flags, flags_prev, cat, V.solid);
 }
 
 // Deterministic stream compaction of the categories into the lists of
@@ -287,12 +339,13 @@ constexpr int kCatBlock = 1024;
 
 __global__ void __launch_bounds__(kCatBlock) categorize_count_kernel(Geo g, const uint8_t* __restrict__ flags,
                                                                      const uint8_t* __restrict__ prev, uint8_t* cat,
-                                                                     int* block_counts) {
+                                                                     int* block_counts,
+                                                                     const uint8_t* __restrict__ solid) {
   __shared__ int sc[4];
   if (threadIdx.x < 4) sc[threadIdx.x] = 0;
   __syncthreads();
   const int c = blockIdx.x * kCatBlock + threadIdx.x;
-  const int t = c < g.nc ? category_of(g, flags, prev, c) : -1;
+  const int t = c < g.nc ? category_of(g, flags, prev, c, solid) : -1;
   if (c < g.nc) cat[c] = (uint8_t)t;
   const unsigned full = 0xffffffffu;
   const unsigned m[4] = {__ballot_sync(full, t == 0 || t == 4), __ballot_sync(full, t == 1),
@@ -339,7 +392,7 @@ void launch_categorize_compact(const View& V, const uint8_t* flags, const uint8_
                                int* block_counts, int* klist, int* blist, int* flist, int* clist, int* counts,
                                cudaStream_t s) {
   const int nb = (V.g.nc + kCatBlock - 1) / kCatBlock;
-  categorize_count_kernel<<<nb, kCatBlock, 0, s>>>(V.g, flags, flags_prev, cat, block_counts);
+  categorize_count_kernel<<<nb, kCatBlock, 0, s>>>(V.g, flags, flags_prev, cat, block_counts, V.solid);
   emit_lists_kernel<<<nb, kCatBlock, 0, s>>>(V.g.nc, cat, block_counts, nb, klist, blist, flist, clist, counts);
 }
 
@@ -365,12 +418,15 @@ void launch_prim(const double* Un, double* out, int nc, cudaStream_t s) {
 }
 
 // Global totals: fixed-order two-level sum of U over cells, times dx dy.
-__global__ void totals_partial_kernel(const double* __restrict__ Un, int nc, double* partial) {
+__global__ void totals_partial_kernel(const double* __restrict__ Un, const uint8_t* __restrict__ solid, int nc,
+                                      double* partial) {
   __shared__ double red[4][256];
   double s[4] = {0, 0, 0, 0};
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    if (solid && solid[c]) continue;  // solid cells hold no state
 #pragma unroll
     for (int q = 0; q < 4; ++q) s[q] += Un[(size_t)q * nc + c];
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = s[q];
   __syncthreads();
@@ -391,8 +447,9 @@ __global__ void totals_final_kernel(const double* __restrict__ partial, int nb, 
   }
 }
 
-void launch_totals(const double* Un, int nc, double* partial, double* out, double dxdy, int grid, cudaStream_t s) {
-  totals_partial_kernel<<<grid, 256, 0, s>>>(Un, nc, partial);
+void launch_totals(const double* Un, const uint8_t* solid, int nc, double* partial, double* out, double dxdy,
+                   int grid, cudaStream_t s) {
+  totals_partial_kernel<<<grid, 256, 0, s>>>(Un, solid, nc, partial);
   totals_final_kernel<<<1, 32, 0, s>>>(partial, grid, out, dxdy);
 }
 

@@ -19,9 +19,6 @@
 #include "common.cuh"
 #include "launch.h"
 
-#ifndef ESBGK_COMPENSATED_MOMENTS
-#define ESBGK_COMPENSATED_MOMENTS 0  // compensated FP32 moment sums (see kinetic_cell_vec)
-#endif
 
 namespace esbgk {
 
@@ -281,6 +278,9 @@ ESBGK_DEV R gauss_at(const CellPar<R>& P, R cx, R cy) {
 // H_mn = w sum G psi_m psi_n, r_m = w sum G psi_m, psi = (1, x, y, x^2, xy, y^2).
 // After this G_hat = G (1 + a . psi) has w sum psi G_hat = t.
 // L lanes per cell (32, or 16 for a half-warp; mask: the group's lanes).
+template <typename R, int L>
+ESBGK_DEV bool project_solve(const R (&s)[15], int lane, CellPar<R>& P, unsigned mask);
+
 template <typename R, int W = 1, int L = 32>
 ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0xffffffffu) {
   const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
@@ -355,6 +355,13 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0x
   }
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = group_sum<L>(s[n], mask) * pick<R>(g.w, g.fw);
+  return project_solve<R, L>(s, lane, P, mask);
+}
+
+// The projection's 6 x 6 system from the 15 weighted sums s (mono order),
+// identical in every lane: H a = t - r.
+template <typename R, int L>
+ESBGK_DEV bool project_solve(const R (&s)[15], int lane, CellPar<R>& P, unsigned mask) {
   // H a = t - r by Gaussian elimination spread over lanes 0..5 (lane m holds
   // row m and its right-hand side; H is symmetric positive definite, so no
   // pivoting), pivot rows broadcast by shuffles.
@@ -460,23 +467,35 @@ ESBGK_DEV void euler_phys(const R (&U)[4], int d, R (&F)[4], R& a) {
 // the four faces of the cell, divergence (Eq. semidiscrete Euler).
 // ovr/omask: faces whose flux is given (bit 2d: the face -1/2 along axis d,
 // bit 2d+1: the face +1/2; ovr[bit][component]).
-template <typename R>
+// WALLS (solid obstacles, View::wsrc): the line's values come from the
+// stencil maps; a mirror image across a wall has its normal momentum reversed.
+template <typename R, bool WALLS = false>
 ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c, R epsw, R (&phi)[4],
-                              const R (*ovr)[4] = nullptr, int omask = 0) {
+                              const R (*ovr)[4] = nullptr, int omask = 0, const View* Vw = nullptr) {
   const int i = c % g.nx, j = c / g.nx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) phi[q] = R(0);
 #pragma unroll 1
   for (int d = 0; d < 2; ++d) {
     int cell[5];
+    bool refl[5] = {false, false, false, false, false};
 #pragma unroll
-    for (int t = 0; t < 5; ++t)
-      cell[t] = d == 0 ? j * g.nx + nb(i + t - 2, g.nx, g.bcx) : nb(j + t - 2, g.ny, g.bcy) * g.nx + i;
+    for (int t = 0; t < 5; ++t) {
+      if (WALLS && t != 2) {
+        const size_t at = (size_t)(d * 4 + (t < 2 ? t : t - 1)) * g.nc + c;
+        cell[t] = Vw->wsrc[at];
+        refl[t] = Vw->wrefl[at] != 0;
+      } else {
+        cell[t] = d == 0 ? j * g.nx + nb(i + t - 2, g.nx, g.bcx) : nb(j + t - 2, g.ny, g.bcy) * g.nx + i;
+      }
+    }
     R q[5][4];
 #pragma unroll
-    for (int t = 0; t < 5; ++t)
+    for (int t = 0; t < 5; ++t) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) q[t][m] = (R)U[(size_t)m * g.nc + cell[t]];
+      if (WALLS && refl[t]) q[t][1 + d] = -q[t][1 + d];
+    }
     R Lm[4], Rm[4], Lp[4], Rp[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -505,13 +524,13 @@ ESBGK_DEV void euler_phi_cell(const Geo& g, const double* __restrict__ U, int c,
 
 // U^(i)(c) = U^n(c) - sum_j coef_j Phi_j(c) for a fluid cell, after storing
 // Phi_{i-1}(c) when requested (Eqs. RKEuler, RKEuler_2).
-template <typename R>
+template <typename R, bool WALLS = false>
 ESBGK_DEV void euler_cell(const StageArgs& A, const View& V, int c, double (&Uc)[4], const R (*ovr)[4] = nullptr,
                           int omask = 0) {
   const size_t nc = V.g.nc;
   if (A.phi_store >= 0) {
     R phi[4];
-    euler_phi_cell<R>(V.g, A.U_prev, c, pick<R>(V.m.eps_w, V.m.feps_w), phi, ovr, omask);
+    euler_phi_cell<R, WALLS>(V.g, A.U_prev, c, pick<R>(V.m.eps_w, V.m.feps_w), phi, ovr, omask, &V);
 #pragma unroll
     for (int m = 0; m < 4; ++m) A.Phi[((size_t)A.phi_store * 4 + m) * nc + c] = (double)phi[m];
   }
@@ -642,6 +661,37 @@ ESBGK_DEV void stencil_load(const S* __restrict__ f, unsigned o0, const unsigned
   q[6] = ld(f + (py ? o[4] : o[7]) + k);
 }
 
+// The same with solid obstacles: o[8] and the reflection bits rb come from the
+// stencil maps (stencil_walls); a reflected value is read at the mirrored node
+// (v_x -> -v_x: kxm, v_y -> -v_y: kym).
+template <typename S, typename R>
+ESBGK_DEV void stencil_load_walls(const S* __restrict__ f, unsigned o0, const unsigned (&o)[8], unsigned rb,
+                                  unsigned k, unsigned kxm, unsigned kym, bool px, bool py, R (&q)[7]) {
+  auto val = [&](int e) {
+    const unsigned kk = (rb >> e) & 1u ? (e < 4 ? kxm : kym) : k;
+    return ld(f + o[e] + kk);
+  };
+  q[0] = ld(f + o0 + k);
+  q[1] = val(px ? 1 : 2);
+  q[2] = val(px ? 2 : 1);
+  q[3] = val(px ? 0 : 3);
+  q[4] = val(py ? 5 : 6);
+  q[5] = val(py ? 6 : 5);
+  q[6] = val(py ? 4 : 7);
+}
+
+// Element offsets and reflection bits of the stencil of cell c with solid
+// obstacles (View::wsrc, wrefl; the order of stencil_offsets).
+ESBGK_DEV void stencil_walls(const View& V, int c, unsigned (&o)[8], unsigned& rb) {
+  rb = 0u;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const size_t at = (size_t)e * V.g.nc + c;
+    o[e] = (unsigned)V.wsrc[at] * (unsigned)V.g.nvv;
+    rb |= (unsigned)(V.wrefl[at] != 0) << e;
+  }
+}
+
 // L(f) at a node from its stencil values: upwind (Lax-Friedrichs with |v|)
 // flux of CWENO3 face values; L_x = |v_x| (F(face away from the upwind
 // neighbour) - F(face toward it)) / dx, the same along y.
@@ -717,14 +767,17 @@ struct ModeT<kFirstRelax0> {
 // acc_in + acc_cL L to the accumulator outputs; pass 3 adds acc_cQ Q to them
 // (a re-read that stays in L2) and writes f.  Without a collision term
 // (the final combination) everything is written in pass 1.
-template <typename S, int M>
+template <typename S, int M, bool WALLS = false>
 ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs) {
   using R = typename Real<S>::T;
   constexpr bool GEN = M == kGeneric;
   const Geo& g = V.g;
   const unsigned o0 = (unsigned)c * (unsigned)g.nvv;
-  unsigned o[8];
-  stencil_offsets(g, c, o);
+  unsigned o[8], rb = 0u;
+  if (WALLS)
+    stencil_walls(V, c, o, rb);
+  else
+    stencil_offsets(g, c, o);
   const S* fsrc = (const S*)A.f_src;
   const S* sbase = (const S*)A.star_base;
   const bool has_src = GEN ? fsrc != nullptr : true;
@@ -775,7 +828,13 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
       if (!val[u]) continue;
       const int k = kk[u];
       if (has_src) {
-        stencil_load<S, R>(fsrc, o0, o, k, vx[u] > R(0), vy[u] > R(0), q[u]);
+        if (WALLS) {
+          const unsigned ky = (unsigned)k / (unsigned)g.nv, kx = (unsigned)k - ky * (unsigned)g.nv;
+          const unsigned kxm = k + g.nv - 1u - 2u * kx, kym = k + (g.nv - 1u - 2u * ky) * (unsigned)g.nv;
+          stencil_load_walls<S, R>(fsrc, o0, o, rb, k, kxm, kym, vx[u] > R(0), vy[u] > R(0), q[u]);
+        } else {
+          stencil_load<S, R>(fsrc, o0, o, k, vx[u] > R(0), vy[u] > R(0), q[u]);
+        }
       } else {
 #pragma unroll
         for (int e = 0; e < 7; ++e) q[u][e] = R(0);
@@ -930,12 +989,11 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   // pass 1: transport of the previous stage, f*, moments of f*
   // (FP32 arithmetic with an even group: pairs of nodes on paired instructions)
   // FP32 moments: paired partial sums per lane (short runs), a butterfly over
-  // the lanes.  With ESBGK_COMPENSATED_MOMENTS the paired sums go every
-  // kFlush groups into a Neumaier-compensated accumulator per lane (m, mc)
-  // and the lanes are added with error-free two-sums (C3 run: mass drift
-  // 2.1e-7 -> 4.1e-8 for 7-8 % of the step time; both meet the FP32 bars).
+  // the lanes.  With compensated sums (Model::comp_moments) the paired sums
+  // go every kFlush groups into a Neumaier-compensated accumulator per lane
+  // (m, mc) and the lanes are added with error-free two-sums.
   constexpr bool kPacked = std::is_same<R, float>::value && W % 2 == 0;
-  constexpr bool kComp = kPacked && ESBGK_COMPENSATED_MOMENTS;
+  const bool kComp = kPacked && V.m.comp_moments;
   constexpr int kFlush = 4;
   R m[6];
   float2 m2[6];
@@ -1051,8 +1109,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     }
 #pragma unroll
     for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
-    if constexpr (kComp) {
-      if (++blk == kFlush) {
+    if constexpr (kPacked) {
+      if (kComp && ++blk == kFlush) {
         blk = 0;
 #pragma unroll
         for (int n = 0; n < 6; ++n) {
@@ -1062,15 +1120,17 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
       }
     }
   }
-  if constexpr (kComp) {
+  if constexpr (kPacked) {
+    if (kComp) {
 #pragma unroll
-    for (int n = 0; n < 6; ++n) {
-      comp_add(m[n], mc[n], m2[n].x + m2[n].y);
-      m[n] = group_sum_comp<L>(m[n], mc[n], mask);
+      for (int n = 0; n < 6; ++n) {
+        comp_add(m[n], mc[n], m2[n].x + m2[n].y);
+        m[n] = group_sum_comp<L>(m[n], mc[n], mask);
+      }
+    } else {
+#pragma unroll
+      for (int n = 0; n < 6; ++n) m[n] = group_sum<L>(m2[n].x + m2[n].y, mask);
     }
-  } else if constexpr (kPacked) {
-#pragma unroll
-    for (int n = 0; n < 6; ++n) m[n] = group_sum<L>(m2[n].x + m2[n].y, mask);
   } else {
 #pragma unroll
     for (int n = 0; n < 6; ++n) m[n] = group_sum<L>(m[n], mask);
@@ -1233,7 +1293,8 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 // PAIR (vector form, small velocity grids): a kinetic unit is two cells, one
 // per half-warp, so that twice as many cells are in flight when a cell has
 // only a few node groups per lane.
-template <typename S, int M, int W, bool PAIR = false, bool SX = false>
+// WALLS: solid obstacles (View::wsrc); only the generic scalar form is compiled with them.
+template <typename S, int M, int W, bool PAIR = false, bool SX = false, bool WALLS = false>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1264,7 +1325,7 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
         kinetic_cell_vec<S, M, W, 32, SX>(A, V, V.klist[u], lane, sfs);
         ++mine;
       } else {
-        kinetic_cell<S, M>(A, V, V.klist[u], lane, sfs);
+        kinetic_cell<S, M, WALLS>(A, V, V.klist[u], lane, sfs);
         ++mine;
       }
       __syncwarp();
@@ -1278,7 +1339,7 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       R ovr[4][4];
       const int omask =
           (buf && A.iface && A.f_src && A.phi_store >= 0) ? interface_fluxes<S>(A, V, V.blist[u - nKu], lane, ovr) : 0;
-      if (ec >= 0) euler_cell<R>(A, V, ec, Uc, ovr, omask);
+      if (ec >= 0) euler_cell<R, WALLS>(A, V, ec, Uc, ovr, omask);
       if (buf) {
         buffer_fill<S, W>(A, V, V.blist[u - nKu], lane, Uc);
         fills += A.fill ? 1 : 0;
@@ -1580,6 +1641,12 @@ __global__ void __launch_bounds__(kCellThreads) batch_l1_kernel(const CaseRegime
   }
 }
 
+}  // namespace esbgk
+
+#include "tile_impl.cuh"
+
+namespace esbgk {
+
 // ---------------------------------------------------------------------------
 // Host-side launchers for storage type S.
 template <typename S>
@@ -1691,16 +1758,64 @@ struct Launch {
       default: return batch_stage_kernel<S, kGeneric, 1, false, false>;
     }
   }
+  // Tiled stage kernel (every cell kinetic, regime frozen): the specialised
+  // modes, an even N_v, the per-pair arrays aligned, no fused L1 deviation,
+  // and f* of a whole tile in shared memory.
+  using TileFn = void (*)(StageArgs, View);
+  template <int M>
+  static TileFn tile_variant(bool sx, bool comp) {
+    if (comp) return sx ? tile_stage_kernel<S, M, true, true> : tile_stage_kernel<S, M, false, true>;
+    return sx ? tile_stage_kernel<S, M, true, false> : tile_stage_kernel<S, M, false, false>;
+  }
+  // compensated sums only change the float arithmetic
+  static TileFn tile_fn(int m, bool sx, bool comp) {
+    comp = comp && std::is_same<R, float>::value;
+    switch (m) {
+      case kFirstRelax2: return tile_variant<kFirstRelax2>(sx, comp);
+      case kLoadedRelax1: return tile_variant<kLoadedRelax1>(sx, comp);
+      case kFinal: return tile_variant<kFinal>(sx, comp);
+      case kFirstRelax0: return tile_variant<kFirstRelax0>(sx, comp);
+      default: return nullptr;
+    }
+  }
+  static bool aligned_pair(const void* p) { return ((uintptr_t)p % (2 * sizeof(S))) == 0; }
+  static int tile_ok(const StageArgs& A, const Geo& g) {
+    const int mode = stage_mode(A);
+    if (mode == kGeneric || g.nv % 2 != 0 || A.l1_out || A.iface) return 0;
+    if (TileSmem<R>::bytes(g) > (size_t)max_smem()) return 0;
+    if (!aligned_pair(A.f_src) || !aligned_pair(A.star_base) || !aligned_pair(A.f_out)) return 0;
+    for (int t = 0; t < A.nacc; ++t)
+      if (!aligned_pair(A.acc_in[t]) || !aligned_pair(A.acc_out[t])) return 0;
+    return 1;
+  }
+  static void stage_tile(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
+    const Geo& g = V.g;
+    const TileFn fn = tile_fn(stage_mode(A), (g.nv / 2) % 2 != 0, V.m.comp_moments != 0);
+    const size_t smem = TileSmem<R>::bytes(g);
+    const int ntiles = ((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY);
+    int gr = rescale(g, grid, (const void*)fn, kTileThreads, smem);
+    if (gr > ntiles) gr = ntiles;
+    fn<<<gr, kTileThreads, smem, s>>>(A, V);
+  }
   static cudaError_t setup(const Geo& g) {
     if ((size_t)g.nvv * sizeof(R) > (size_t)max_smem()) return cudaErrorInvalidValue;
     cudaError_t e;
     const int mx = max_smem();
+    for (int m = 0; m < kNumModes; ++m)
+      for (int v = 0; v < 4; ++v)
+        if (tile_fn(m, v & 1, v & 2) &&
+            (e = cudaFuncSetAttribute(tile_fn(m, v & 1, v & 2), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+                cudaSuccess)
+          return e;
     for (int m = 0; m < kNumModes; ++m)
       for (int v = 0; v < kNumVariants; ++v)
         if ((e = cudaFuncSetAttribute(stage_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
             cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(stage_kernel<S, kGeneric, 1, false, false, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
     // batched kernels: set here so that their launches can be graph-captured
     const int mb = mx - kBatchStaticSmem;
@@ -1726,10 +1841,11 @@ struct Launch {
   static void stage(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
     const bool proj = A.h_coef > 0.0 || A.need_q || A.l1_out;
     const int mode = stage_mode(A), var = variant(A, V.g, mode);
-    const int arrays = variant_pairs(var) ? 2 : 1;  // f* arrays per warp
+    const int arrays = V.wsrc || !variant_pairs(var) ? 1 : 2;  // f* arrays per warp
     const int threads = 32 * warps_for(V.g, arrays);
     const size_t smem = proj ? smem_for(V.g, arrays) : 0;
-    const StageFn fn = stage_fn(mode, var);
+    // solid obstacles: the generic scalar form with the wall stencils
+    const StageFn fn = V.wsrc ? stage_kernel<S, kGeneric, 1, false, false, true> : stage_fn(mode, var);
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {
@@ -1772,6 +1888,7 @@ struct Launch {
                           &Launch<S>::stage,                  &Launch<S>::prep,         &Launch<S>::l1,            \
                           &Launch<S>::relax_cells,            &Launch<S>::moments,      &Launch<S>::batch_stage,   \
                           &Launch<S>::batch_prep,             &Launch<S>::batch_l1,                               \
-                          &Launch<S>::batch_stage_occupancy, &Launch<S>::variant_public, VecW<S>::value};
+                          &Launch<S>::batch_stage_occupancy, &Launch<S>::variant_public, VecW<S>::value,       \
+                          &Launch<S>::tile_ok,                &Launch<S>::stage_tile};
 
 }  // namespace esbgk

@@ -21,6 +21,12 @@ struct View {
   const int* clist;        // cells that turned kinetic since the last step
   const int* counts;       // [4] nK, nB, nF, nC
   DevErr* err;
+  // solid obstacles (null: none): per axis (x, y) and stencil offset (-2, -1,
+  // +1, +2) the source cell of every cell's stencil value, [2][4][nc], and
+  // whether it is a mirror image across a wall (specular reflection), [2][4][nc]
+  const int* wsrc;
+  const uint8_t* wrefl;
+  const uint8_t* solid;  // [nc] 1 = solid cell (no state, never kinetic or fluid)
 };
 
 // One stage (or the final combination) of the IMEX step; see the stage
@@ -210,6 +216,9 @@ struct Launchers {
   int (*batch_stage_occupancy)(int mode, int var, int max_nvv, int threads);
   int (*variant)(const StageArgs& A, const Geo& g);
   int wide_nodes;  // nodes per group of the kVarWide variants
+  // tiled stage kernel for problems whose every cell is kinetic (regime frozen)
+  int (*tile_ok)(const StageArgs& A, const Geo& g);
+  void (*stage_tile)(const StageArgs&, const View&, int grid, cudaStream_t);
 };
 
 extern const Launchers kLaunchF64;
@@ -236,9 +245,13 @@ int categorize_blocks(int nc);
 // withholds the arrival.  *err_out: 0, or kErrTimeout when the wait ran out.
 cudaError_t launch_wait_probe(int arrive, unsigned limit, int* err_out, cudaStream_t s);
 void launch_prim(const double* Un, double* out /*[4][nc]*/, int nc, cudaStream_t s);
+// flags and flags_prev := 0 in solid cells
+void launch_clear_solid(uint8_t* flags, uint8_t* flags_prev, const uint8_t* solid, int nc, cudaStream_t s);
 // advance the step counter of the stochastic rounding (one thread)
 void launch_seed_advance(unsigned* seed, cudaStream_t s);
-void launch_totals(const double* Un, int nc, double* partial /*[grid][4]*/, double* out, double dxdy, int grid,
+// solid (may be null): cells left out of the totals
+void launch_totals(const double* Un, const uint8_t* solid, int nc, double* partial /*[grid][4]*/, double* out,
+                   double dxdy, int grid,
                    cudaStream_t s);
 // batched regime update: offsets of the L1 units, flags, categories,
 // compaction (one CTA per case), offsets of the stage and start-of-step units

@@ -1,0 +1,527 @@
+// tile_impl.cuh -- the tiled stage kernel for regions where every cell is kinetic.
+//
+// Included by kernels_impl.cuh.  A CTA owns a tile of kTileX x kTileY cells,
+// one warp per cell (as in stage_kernel), and walks the velocity nodes in
+// chunks of kTilePairs node pairs.  Per chunk:
+//
+//   walk phase   -- the transport of Sec. 3.2 computed per face, not per cell:
+//                   a thread takes one node pair and one tile row (x walk) or
+//                   column (y walk), loads the 7 upwind-relevant values of the
+//                   line (two ghost cells each side), forms the 5 CWENO3 face
+//                   values between its 4 cells once each, and writes
+//                   v (F_{i+1/2} - F_{i-1/2}) / dx of its 4 cells to shared
+//                   memory.  A cell's 4 faces are shared with its neighbours,
+//                   so the tile computes 2.5 faces per cell and node instead
+//                   of 4; neighbouring faces also share one difference and its
+//                   smoothness term.
+//   cell phase   -- the warp of each cell adds its x and y parts, forms
+//                   f* = base + c_L L and the partial accumulators, keeps f*
+//                   in shared memory and sums the moments of f* (Eq. RKEI1).
+//
+// After the last chunk each warp finishes its own cell exactly as
+// kinetic_cell_vec does: moments -> ES parameters -> projection -> implicit
+// relaxation, Q and accumulators (Sec. 2, 3.3, Eq. RKEI1-RKEI2).
+//
+// The face value uses the same CWENO3 weights as cweno_face, rearranged so
+// that the upwind direction is a per-thread coefficient instead of a branch:
+// with dl = b - a, dr = c - b, x = (eps+dl^2)^2, y = (eps+dr^2)^2,
+// z = (eps + 13/3 (dr-dl)^2 + 1/4 (dl+dr)^2)^2,
+//   face = b + 1/2 [x y (5 dr + dl)/3 + z (y dl + x dr)] / [2 x y + z (x + y)]
+//        = b + 1/2 [x y (5 dr + dl)/6 + (z/2) (y dl + x dr)] / [x y + (z/2) (x + y)],
+// and the face of the mirrored stencil (c, b, a) -- the other upwind
+// direction -- is the same expression with 5 dr + dl replaced by 5 dl + dr and
+// the sign of the correction flipped.  With t = d^2 + eps of the two
+// differences, 13/3 (dr-dl)^2 + 1/4 (dl+dr)^2 + eps
+//   = 55/12 (t_l + t_r) - 49/6 dl dr + eps (1 - 55/6),
+// so the squares already formed for x and y give z.  Paired FP32 instructions
+// take register pairs only, so every constant factor sits in a scalar
+// multiply-add or in a per-thread coefficient pair.
+#pragma once
+
+namespace esbgk {
+
+constexpr int kTileX = 4, kTileY = 4;
+constexpr int kTileCells = kTileX * kTileY;
+constexpr int kTileThreads = 32 * kTileCells;  // one warp per cell
+constexpr int kTilePairs = 64;                 // node pairs per chunk: (kTileX + kTileY) * kTilePairs walks
+static_assert((kTileX + kTileY) * kTilePairs == kTileThreads, "one walk per thread and chunk");
+static_assert(kTilePairs == 64, "the cell phase gives each lane two pairs");
+
+// Two lanes of arithmetic: paired FP32 instructions for float, component-wise
+// for double.
+template <typename R> struct PairT;
+template <> struct PairT<float> { using T = float2; };
+template <> struct PairT<double> { using T = double2; };
+
+ESBGK_DEV float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+ESBGK_DEV float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+ESBGK_DEV float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+ESBGK_DEV float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+ESBGK_DEV float2 pdiv(float2 a, float2 b) { return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y)); }
+ESBGK_DEV float2 psplat(float a) { return make_float2(a, a); }
+ESBGK_DEV double2 pfma(double2 a, double2 b, double2 c) { return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)); }
+ESBGK_DEV double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+ESBGK_DEV double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+ESBGK_DEV double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+ESBGK_DEV double2 pdiv(double2 a, double2 b) { return make_double2(a.x / b.x, a.y / b.y); }
+ESBGK_DEV double2 psplat(double a) { return make_double2(a, a); }
+ESBGK_DEV float2 mk2(float a, float b) { return make_float2(a, b); }
+ESBGK_DEV double2 mk2(double a, double b) { return make_double2(a, b); }
+
+// G_hat at the two nodes of a pair of one velocity row (cx: v_x - u_x of
+// both, cy: v_y - u_y): the per-row terms once, then both nodes.
+ESBGK_DEV GhatRow ghat_row2(const CellPar<float>& P, float cy) { return ghat_row(P, cy); }
+ESBGK_DEV float2 ghat2(const CellPar<float>& P, const GhatRow& r, float2 cx) { return ghat_pair(P, r, cx); }
+struct GhatRowD {
+  double cy;
+};
+ESBGK_DEV GhatRowD ghat_row2(const CellPar<double>&, double cy) { return GhatRowD{cy}; }
+ESBGK_DEV double2 ghat2(const CellPar<double>& P, const GhatRowD& r, double2 cx) {
+  return make_double2(ghat(P, cx.x, r.cy), ghat(P, cx.y, r.cy));
+}
+
+// A node pair (two consecutive nodes of one velocity row) of storage type S,
+// in the arithmetic type.
+template <typename S> struct PairIO;
+template <>
+struct PairIO<float> {
+  static ESBGK_DEV float2 ld(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+  static ESBGK_DEV float2 ldc(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static ESBGK_DEV void st(float* p, float2 v, uint32_t) { *reinterpret_cast<float2*>(p) = v; }
+};
+template <>
+struct PairIO<double> {
+  static ESBGK_DEV double2 ld(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+  static ESBGK_DEV double2 ldc(const double* p) { return *reinterpret_cast<const double2*>(p); }
+  static ESBGK_DEV void st(double* p, double2 v, uint32_t) { *reinterpret_cast<double2*>(p) = v; }
+};
+template <>
+struct PairIO<__nv_bfloat16> {
+  static ESBGK_DEV float2 unpack(unsigned t) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t));
+  }
+  static ESBGK_DEV float2 ld(const __nv_bfloat16* p) { return unpack(__ldg(reinterpret_cast<const unsigned*>(p))); }
+  static ESBGK_DEV float2 ldc(const __nv_bfloat16* p) { return unpack(*reinterpret_cast<const unsigned*>(p)); }
+  // stochastic rounding (key: random bits for the pair)
+  static ESBGK_DEV void st(__nv_bfloat16* p, float2 v, uint32_t key) {
+    const uint32_t r = mix32(key);
+    *reinterpret_cast<unsigned*>(p) = (uint32_t)bf16_sr_bits(v.x, r) | ((uint32_t)bf16_sr_bits(v.y, r >> 16) << 16);
+  }
+};
+
+// Reciprocal: the hardware approximation for float (rcp.approx, at most
+// 1 ulp), an IEEE division for double.
+ESBGK_DEV float rcp_(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+ESBGK_DEV double rcp_(double x) { return 1.0 / x; }
+
+// Upwind CWENO3 faces along one line of the tile and the transport of its 4
+// cells.  u[0..6]: the pair's values in 7 consecutive cells, shifted so that
+// u[q+1] is the upwind cell of face q, the face between tile cells q-1 and q
+// (q = 0..4): cells -2..4 of the line for velocities toward increasing cell
+// index, -1..5 otherwise.  Per node of the pair: (cA, cB) = (1/6, 5/6) toward
+// increasing index, (5/6, 1/6) the other way, sgnh = +1/2 / -1/2;
+// eps2 = (eps_w, eps_w), c3 = eps_w (1 - 55/6)/sqrt(2), vs = v / h.  Writes
+// v (face_{q+1} - face_q) / h of tile cell q to out[q * stride].  The faces
+// are formed in order, each from the difference behind and the difference
+// ahead of its upwind cell, so only two differences are live at a time.
+template <typename P, typename R>
+ESBGK_DEV void walk_line(const P (&u)[7], P eps2, R c3, P cA, P cB, P sgnh, P vs, P* out, int stride) {
+  constexpr R C1 = R(55.0 / 12.0 / 1.4142135623730951), C2 = R(-49.0 / 6.0 / 1.4142135623730951);
+  P dl = mk2(u[1].x - u[0].x, u[1].y - u[0].y);
+  P tl = pfma(dl, dl, eps2);
+  P sl = pmul(tl, tl);
+  P prev = psplat(R(0));
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const P dr = mk2(u[q + 2].x - u[q + 1].x, u[q + 2].y - u[q + 1].y);
+    const P tr = pfma(dr, dr, eps2);
+    const P sr = pmul(tr, tr);
+    const P T = padd(tl, tr), Pd = pmul(dl, dr);
+    // sqrt(z/2), then z/2
+    const P z0 = mk2(fma(T.x, C1, fma(Pd.x, C2, c3)), fma(T.y, C1, fma(Pd.y, C2, c3)));
+    const P zh = pmul(z0, z0);
+    const P xy = pmul(sl, sr);
+    const P p = pfma(cA, dl, pmul(cB, dr));         // (5 d_r + d_l)/6, upwind orientation
+    const P tt = pfma(sr, dl, pmul(sl, dr));         // y d_l + x d_r, either orientation
+    const P num = pfma(xy, p, pmul(zh, tt));
+    const P den = pfma(zh, padd(sl, sr), xy);
+    const P face = pfma(sgnh, pmul(num, mk2(rcp_(den.x), rcp_(den.y))), u[q + 1]);
+    if (q > 0) out[(q - 1) * stride] = pmul(vs, mk2(face.x - prev.x, face.y - prev.y));
+    prev = face;
+    dl = dr;
+    tl = tr;
+    sl = sr;
+  }
+}
+
+// Projection sums of the discrete Gaussian (the 15 sums of project), factored
+// by velocity rows: along a row segment v_y is fixed, so the lane sums
+// G x^p (p = 0..4) over the segment's node pairs and then adds them times
+// y^q into the 15 sums once per segment.  Segments are half rows (N_v a
+// multiple of 4: the tiled kernel's per-cell groups of 4 nodes).  The
+// relaxation pass must see the same G at every node, or the projected
+// Gaussian's moments miss their targets by rounding each stage: each node's
+// v_x - u_x and exponent are formed exactly as the relaxation pass forms
+// them (group start from the velocity table's expression, then + j dv).
+// The sums are then solved as in project.
+ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P) {
+  const float v0 = g.fv0, dv = g.fdv;
+  const int seg = g.nv / 2, nseg = g.nvv / seg;
+  const float2 qxx2 = splat2(P.qxx), isT2 = splat2(P.isT), pref2 = splat2(P.pref);
+  float s[15];
+#pragma unroll
+  for (int n = 0; n < 15; ++n) s[n] = 0.0f;
+#pragma unroll 1
+  for (int sg = lane; sg < nseg; sg += 32) {
+    const int ky = sg >> 1, kx0 = (sg & 1) * seg;
+    const float cy = (v0 + float(ky) * dv) - P.uy, y = cy * P.isT;
+    const float2 qy2 = splat2(P.qyy * cy * cy), qc2 = splat2(P.qxy * cy);
+    float2 R0 = splat2(0.0f), R1 = R0, R2 = R0, R3 = R0, R4 = R0;
+#pragma unroll 2
+    for (int j = 0; j < seg; j += 2) {
+      const int kg = kx0 + (j & ~3);  // first node of the relaxation pass's group
+      const float cxa = ((v0 + float(kg) * dv) - P.ux) + float(j & 3) * dv;
+      const float2 cx = make_float2(cxa, cxa + dv);
+      const float2 e = __ffma2_rn(qxx2, __fmul2_rn(cx, cx), __ffma2_rn(qc2, cx, qy2));
+      const float2 G = __fmul2_rn(pref2, make_float2(exp2r(e.x), exp2r(e.y)));
+      const float2 x = __fmul2_rn(cx, isT2);
+      const float2 t1 = __fmul2_rn(G, x), t2 = __fmul2_rn(t1, x), t3 = __fmul2_rn(t2, x);
+      R0 = __fadd2_rn(R0, G);
+      R1 = __fadd2_rn(R1, t1);
+      R2 = __fadd2_rn(R2, t2);
+      R3 = __fadd2_rn(R3, t3);
+      R4 = __ffma2_rn(t3, x, R4);
+    }
+    const float r[5] = {R0.x + R0.y, R1.x + R1.y, R2.x + R2.y, R3.x + R3.y, R4.x + R4.y};
+    float yq[5];
+    yq[0] = 1.0f;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) yq[q] = yq[q - 1] * y;
+#pragma unroll
+    for (int pp = 0; pp < 5; ++pp)
+#pragma unroll
+      for (int q = 0; q + pp < 5; ++q) s[mono(pp, q)] = fmaf(r[pp], yq[q], s[mono(pp, q)]);
+  }
+#pragma unroll
+  for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * g.fw;
+  return project_solve<float, 32>(s, lane, P, 0xffffffffu);
+}
+
+// Shared-memory layout of the tiled kernel (dynamic): f* of each cell, the
+// x and y transport parts of two chunks, and the per-pair velocities.
+template <typename R>
+struct TileSmem {
+  static size_t bytes(const Geo& g) {
+    using P = typename PairT<R>::T;
+    return (size_t)kTileCells * g.nvv * sizeof(R) + 2 * 2 * kTileCells * kTilePairs * sizeof(P) +
+           (size_t)(g.nvv / 2) * sizeof(P);
+  }
+};
+
+// Tile t of the grid: its first cell (i0, j0).
+ESBGK_DEV void tile_origin(const Geo& g, int t, int& i0, int& j0) {
+  const int tx = (g.nx + kTileX - 1) / kTileX;
+  i0 = (t % tx) * kTileX;
+  j0 = (t / tx) * kTileY;
+}
+
+// SX: some node pair straddles v_x = 0 (N_v/2 odd): its two nodes take
+// opposite upwind directions in the x walk.  Otherwise N_v is a multiple of 4
+// and the per-cell passes take groups of 4 nodes (two pairs of one row).
+// COMP: compensated moment sums (Model::comp_moments, float arithmetic).
+//
+// Latency: the walk's line values are loaded one chunk ahead into the other
+// of two register sets, so they are in flight while the previous chunk
+// computes; the cell phase's base and accumulator values are loaded at the
+// start of their chunk, before its walk.
+template <typename S, int M, bool SX, bool COMP>
+__global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A, View V) {
+  using R = typename Real<S>::T;
+  using P = typename PairT<R>::T;
+  using IO = PairIO<S>;
+  using MT = ModeT<M>;
+  constexpr bool relax = MT::relax;
+  constexpr int nacc = MT::nacc;
+  constexpr int NW = SX ? 8 : 7;                    // line values a walk loads
+  constexpr int NB = 1 + (MT::acc_src ? 0 : nacc);  // base and accumulator inputs of a cell pair
+  constexpr bool F32 = std::is_same<R, float>::value;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const Geo& g = V.g;
+  const int nvv = g.nvv, npairs = nvv / 2;
+  R* fs_all = reinterpret_cast<R*>(dsm);
+  P* Lb = reinterpret_cast<P*>(dsm + (size_t)kTileCells * nvv * sizeof(R));  // [2][2][cells][pairs]
+  P* vt = Lb + 2 * 2 * kTileCells * kTilePairs;                              // [npairs] (v_x of the first node, v_y)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
+  for (int p = tid; p < npairs; p += kTileThreads) {
+    const int k = 2 * p, ky = k / g.nv;
+    P v;
+    v.x = v0 + R(k - ky * g.nv) * dv;
+    v.y = v0 + R(ky) * dv;
+    vt[p] = v;
+  }
+  __syncthreads();
+
+  const S* fsrc = (const S*)A.f_src;
+  const S* bsrc = MT::base_src ? fsrc : (const S*)A.star_base;
+  S* fout = (S*)A.f_out;
+  const R idx = pick<R>(1.0 / g.dx, g.fidx), idy = pick<R>(1.0 / g.dy, g.fidy);
+  const P cL2 = psplat(pick<R>(A.star_cL, A.f_star_cL));
+  const R epsw = pick<R>(V.m.eps_w, V.m.feps_w);
+  const P eps2 = psplat(epsw);
+  const R c3 = epsw * R((1.0 - 55.0 / 6.0) / 1.4142135623730951);
+  const S* ain[nacc > 0 ? nacc : 1];
+  S* aout[nacc > 0 ? nacc : 1];
+  P aL2[nacc > 0 ? nacc : 1];
+  R aQ[nacc > 0 ? nacc : 1];
+#pragma unroll
+  for (int t = 0; t < nacc; ++t) {
+    ain[t] = (const S*)A.acc_in[t];
+    aout[t] = (S*)A.acc_out[t];
+    aL2[t] = psplat(pick<R>(A.acc_cL[t], A.f_acc_cL[t]));
+    aQ[t] = pick<R>(A.acc_cQ[t], A.f_acc_cQ[t]);
+  }
+  const uint32_t s0 = A.seed ? mix32(*A.seed * 0x632be5abu + A.sid) : 0u;
+
+  // walk of this thread: x walks (one per tile row) then y walks (one per column)
+  const bool xwalk = tid < kTileY * kTilePairs;
+  const int wline = xwalk ? tid / kTilePairs : (tid - kTileY * kTilePairs) / kTilePairs;
+  const int wpair = tid % kTilePairs;
+  const R wscale = xwalk ? idx : idy;
+  const int wstride = xwalk ? kTilePairs : kTileX * kTilePairs;
+  const int wout = xwalk ? (wline * kTileX) * kTilePairs + wpair : wline * kTilePairs + wpair;
+  // cell of this warp in the cell phase
+  const int ci = warp % kTileX, cj = warp / kTileX;
+  R* fs = fs_all + (size_t)warp * nvv;
+
+  constexpr int W3 = SX ? 2 : 4;  // nodes per group of the per-cell passes
+  const int ntiles = ((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY);
+  const int nchunks = (npairs + kTilePairs - 1) / kTilePairs;
+  long long mine = 0;
+  // chunks walked so far: the parity picks the transport buffer, so a buffer
+  // is rewritten only after the barrier of the chunk that follows its readers
+  int gch = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int i0, j0;
+    tile_origin(g, tile, i0, j0);
+    // the walk's line: cells -2..5 of it (boundary conditions applied)
+    const bool wvalid = xwalk ? (j0 + wline < g.ny) : (i0 + wline < g.nx);
+    unsigned wb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = xwalk ? (j0 + wline) * g.nx + nb(i0 - 2 + q, g.nx, g.bcx)
+                          : nb(j0 - 2 + q, g.ny, g.bcy) * g.nx + (i0 + wline);
+      wb[q] = wvalid ? (unsigned)c * (unsigned)nvv : 0u;
+    }
+    // this warp's cell
+    const int ccell = (j0 + cj) * g.nx + (i0 + ci);
+    const bool cvalid = (i0 + ci < g.nx) && (j0 + cj < g.ny);
+    const unsigned o0 = cvalid ? (unsigned)ccell * (unsigned)nvv : 0u;
+    R u0x = R(0), u0y = R(0);
+    if (cvalid) ref_velocity(A.U_prev, g.nc, ccell, u0x, u0y);
+    P m2[6];
+    R mc_s[COMP ? 6 : 1], mc_c[COMP ? 6 : 1];  // compensated sums: running sum and compensation
+#pragma unroll
+    for (int n = 0; n < 6; ++n) m2[n] = psplat(R(0));
+#pragma unroll
+    for (int n = 0; n < (COMP ? 6 : 1); ++n) mc_s[n] = mc_c[n] = R(0);
+
+    // two register sets of the walk's loads; chunk c uses set c & 1
+    P wA[NW], wB[NW], cb[2][NB];
+    P vwA = psplat(R(0)), vwB = psplat(R(0));
+    bool okA = false, okB = false;
+    auto load_walk = [&](int ch, P (&w)[NW], P& vw, bool& ok) {
+      const int pr = ch * kTilePairs + wpair;
+      ok = wvalid && pr < npairs;
+      if (ok) {
+        const P v = vt[pr];
+        vw = xwalk ? mk2(v.x, v.x + dv) : mk2(v.y, v.y);
+        const unsigned k = 2u * pr;
+        if (SX) {
+#pragma unroll
+          for (int q = 0; q < NW; ++q) w[q] = IO::ld(fsrc + wb[q] + k);
+        } else {
+          // the window starts one cell further for velocities toward lower indices
+          const bool pos = vw.x > R(0);
+#pragma unroll
+          for (int q = 0; q < NW; ++q) w[q] = IO::ld(fsrc + (pos ? wb[q] : wb[q + 1]) + k);
+        }
+      }
+    };
+    auto load_cell = [&](int ch) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int prc = ch * kTilePairs + lane + 32 * h;
+        if (cvalid && prc < npairs) {
+          const unsigned k = 2u * prc;
+          cb[h][0] = IO::ld(bsrc + o0 + k);
+#pragma unroll
+          for (int t = 1; t < NB; ++t) cb[h][t] = IO::ld(ain[t - 1] + o0 + k);
+        }
+      }
+    };
+    auto chunk = [&](int ch, const P (&w)[NW], P vw, bool ok) {
+      load_cell(ch);
+      P* Lx = Lb + (size_t)(gch & 1) * 2 * kTileCells * kTilePairs;
+      P* Ly = Lx + kTileCells * kTilePairs;
+      // --- walk phase
+      if (ok) {
+        P u[7];
+        if (SX) {
+          // per node: the window of its own direction
+#pragma unroll
+          for (int q = 0; q < 7; ++q) {
+            u[q].x = vw.x > R(0) ? w[q].x : w[q + 1].x;
+            u[q].y = vw.y > R(0) ? w[q].y : w[q + 1].y;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 7; ++q) u[q] = w[q];
+        }
+        const bool px = vw.x > R(0), py = vw.y > R(0);
+        const P cA = mk2(px ? R(1.0 / 6.0) : R(5.0 / 6.0), py ? R(1.0 / 6.0) : R(5.0 / 6.0));
+        const P cB = mk2(px ? R(5.0 / 6.0) : R(1.0 / 6.0), py ? R(5.0 / 6.0) : R(1.0 / 6.0));
+        const P sgnh = mk2(px ? R(0.5) : R(-0.5), py ? R(0.5) : R(-0.5));
+        walk_line<P, R>(u, eps2, c3, cA, cB, sgnh, mk2(vw.x * wscale, vw.y * wscale), (xwalk ? Lx : Ly) + wout,
+                        wstride);
+      }
+      __syncthreads();
+      // --- cell phase: lanes take pairs lane and lane + 32 of the chunk
+      if (cvalid) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pl = lane + 32 * h, pr = ch * kTilePairs + pl;
+          if (pr >= npairs) continue;
+          const unsigned k = 2u * pr;
+          const P L = padd(Lx[warp * kTilePairs + pl], Ly[warp * kTilePairs + pl]);
+          const P base = cb[h][0];
+          const P F = pfma(cL2, L, base);
+          const uint32_t kb = s0 + ((o0 + k) << 3);
+#pragma unroll
+          for (int t = 0; t < nacc; ++t) {
+            const P ai = MT::acc_src ? base : cb[h][1 + t];
+            IO::st(aout[t] + o0 + k, pfma(aL2[t], L, ai), kb + 1 + t);
+          }
+          if (relax)
+            *reinterpret_cast<P*>(fs + k) = F;
+          else
+            IO::st(fout + o0 + k, F, kb);
+          const P v = vt[pr];
+          const R cxa = v.x - u0x;
+          const P cx = mk2(cxa, cxa + dv), cy = psplat(v.y - u0y);
+          const P xf = pmul(cx, F), yf = pmul(cy, F);
+          m2[0] = padd(m2[0], F);
+          m2[1] = padd(m2[1], xf);
+          m2[2] = padd(m2[2], yf);
+          m2[3] = pfma(cx, xf, m2[3]);
+          m2[4] = pfma(cy, xf, m2[4]);
+          m2[5] = pfma(cy, yf, m2[5]);
+        }
+        if constexpr (COMP && F32) {
+          // the paired runs of 4 chunks (16 nodes per lane) into a Neumaier accumulator
+          if ((ch & 3) == 3 || ch == nchunks - 1) {
+#pragma unroll
+            for (int n = 0; n < 6; ++n) {
+              comp_add(mc_s[n], mc_c[n], m2[n].x + m2[n].y);
+              m2[n] = psplat(R(0));
+            }
+          }
+        }
+      }
+      ++gch;
+    };
+    load_walk(0, wA, vwA, okA);
+    for (int ch = 0; ch < nchunks; ch += 2) {
+      if (ch + 1 < nchunks) load_walk(ch + 1, wB, vwB, okB);
+      chunk(ch, wA, vwA, okA);
+      if (ch + 1 < nchunks) {
+        if (ch + 2 < nchunks) load_walk(ch + 2, wA, vwA, okA);
+        chunk(ch + 1, wB, vwB, okB);
+      }
+    }
+    // --- the cell: moments, ES parameters, projection, relaxation
+    if (cvalid) {
+      R m[6];
+      if constexpr (COMP && F32) {
+#pragma unroll
+        for (int n = 0; n < 6; ++n) m[n] = group_sum_comp<32>(mc_s[n], mc_c[n], 0xffffffffu);
+      } else {
+#pragma unroll
+        for (int n = 0; n < 6; ++n) m[n] = warp_sum(m2[n].x + m2[n].y);
+      }
+      if (lane == 0) {
+        double Uc[4];
+        cons_from_sums(m, u0x, u0y, g.w, Uc);
+        const size_t nc = g.nc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) A.U_out[q * nc + ccell] = A.kin_u_moments ? Uc[q] : A.Un[q * nc + ccell];
+      }
+      if (A.f_src) ++mine;
+      if (relax) {
+        __syncwarp();
+        const R tau = pick<R>(V.m.tau, V.m.ftau) * (V.m.tau_rho ? pick<R>(g.w, g.fw) * m[0] : R(1));
+        const R nu = tau / R(V.eps[ccell]), hh = pick<R>(A.h_coef, A.f_h_coef) * nu;
+        CellPar<R> Pp;
+        bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), hh, true, Pp);
+        if constexpr (F32 && !SX) {
+          if (ok) ok = project_rows(g, lane, Pp);
+        } else {
+          if (ok) ok = project<R, W3, 32>(g, lane, Pp);
+        }
+        if (!ok && lane == 0) report_error(V.err, kErrNonRealizable, ccell);
+        const R inv1h = R(1) / (R(1) + hh);
+        const P h2 = psplat(hh), i2 = psplat(inv1h), nq = psplat(nu * inv1h);
+        P aQ2[nacc > 0 ? nacc : 1];
+#pragma unroll
+        for (int t = 0; t < nacc; ++t) aQ2[t] = psplat(aQ[t]);
+        const int ngroups = nvv / W3;
+        // accumulator partials of the next group loaded one iteration ahead
+        P pan[W3 / 2][nacc > 0 ? nacc : 1];
+        auto load_pa = [&](int gi) {
+#pragma unroll
+          for (int j = 0; j < W3 / 2; ++j)
+#pragma unroll
+            for (int t = 0; t < nacc; ++t) pan[j][t] = IO::ldc(aout[t] + o0 + (unsigned)gi * W3 + 2 * j);
+        };
+        if (lane < ngroups) load_pa(lane);
+        for (int gi = lane; gi < ngroups; gi += 32) {
+          P pa[W3 / 2][nacc > 0 ? nacc : 1];
+#pragma unroll
+          for (int j = 0; j < W3 / 2; ++j)
+#pragma unroll
+            for (int t = 0; t < nacc; ++t) pa[j][t] = pan[j][t];
+          if (gi + 32 < ngroups) load_pa(gi + 32);
+          const unsigned kg = (unsigned)gi * W3;
+          const P v = vt[kg / 2];
+          // v_x - u_x of the group's first node and v_y - u_y, as the projection forms them
+          const R cxg = v.x - Pp.ux, cy = v.y - Pp.uy;
+          const auto row = ghat_row2(Pp, cy);
+#pragma unroll
+          for (int j = 0; j < W3; j += 2) {
+            const unsigned k = kg + j;
+            const P F = *reinterpret_cast<const P*>(fs + k);
+            P Fn = F, Q = psplat(R(0));
+            if (ok) {
+              const R cxa = cxg + R(j) * dv;
+              const P Gh = ghat2(Pp, row, mk2(cxa, cxa + dv));
+              // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f*)/(1 + h)
+              Fn = pmul(pfma(h2, Gh, F), i2);
+              Q = pmul(nq, mk2(Gh.x - F.x, Gh.y - F.y));
+            }
+            const uint32_t kb = s0 + ((o0 + k) << 3);
+            IO::st(fout + o0 + k, Fn, kb);
+#pragma unroll
+            for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, pfma(aQ2[t], Q, pa[j / 2][t]), kb + 4 + t);
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0 && A.ctr && mine) atomicAdd((unsigned long long*)A.ctr, (unsigned long long)mine);
+}
+
+}  // namespace esbgk
