@@ -118,31 +118,44 @@ ESBGK_DEV float rcp_(float x) {
 }
 ESBGK_DEV double rcp_(double x) { return 1.0 / x; }
 
+// Constant pairs of walk_line (register pairs, formed once per kernel):
+// m1 = (-1, -1), eps2 = eps_w, C1 = 55/(12 sqrt 2), C2 = -49/(6 sqrt 2),
+// c3 = eps_w (1 - 55/6)/sqrt 2.
+template <typename P>
+struct WalkConst {
+  P m1, eps2, C1, C2, c3;
+};
+template <typename P, typename R>
+ESBGK_DEV WalkConst<P> walk_const(R epsw) {
+  return WalkConst<P>{psplat(R(-1)), psplat(epsw), psplat(R(55.0 / 12.0 / 1.4142135623730951)),
+                      psplat(R(-49.0 / 6.0 / 1.4142135623730951)),
+                      psplat(epsw * R((1.0 - 55.0 / 6.0) / 1.4142135623730951))};
+}
+
 // Upwind CWENO3 faces along one line of the tile and the transport of its 4
 // cells.  u[0..6]: the pair's values in 7 consecutive cells, shifted so that
 // u[q+1] is the upwind cell of face q, the face between tile cells q-1 and q
 // (q = 0..4): cells -2..4 of the line for velocities toward increasing cell
 // index, -1..5 otherwise.  Per node of the pair: (cA, cB) = (1/6, 5/6) toward
-// increasing index, (5/6, 1/6) the other way, sgnh = +1/2 / -1/2;
-// eps2 = (eps_w, eps_w), c3 = eps_w (1 - 55/6)/sqrt(2), vs = v / h.  Writes
+// increasing index, (5/6, 1/6) the other way, sgnh = +1/2 / -1/2; K the
+// constant pairs (walk_const); vs = v / h.  Writes
 // v (face_{q+1} - face_q) / h of tile cell q to out[q * stride].  The faces
 // are formed in order, each from the difference behind and the difference
 // ahead of its upwind cell, so only two differences are live at a time.
 template <typename P, typename R>
-ESBGK_DEV void walk_line(const P (&u)[7], P eps2, R c3, P cA, P cB, P sgnh, P vs, P* out, int stride) {
-  constexpr R C1 = R(55.0 / 12.0 / 1.4142135623730951), C2 = R(-49.0 / 6.0 / 1.4142135623730951);
-  P dl = mk2(u[1].x - u[0].x, u[1].y - u[0].y);
-  P tl = pfma(dl, dl, eps2);
+ESBGK_DEV void walk_line(const P (&u)[7], const WalkConst<P>& K, P cA, P cB, P sgnh, P vs, P* out, int stride) {
+  P dl = pfma(u[0], K.m1, u[1]);
+  P tl = pfma(dl, dl, K.eps2);
   P sl = pmul(tl, tl);
   P prev = psplat(R(0));
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const P dr = mk2(u[q + 2].x - u[q + 1].x, u[q + 2].y - u[q + 1].y);
-    const P tr = pfma(dr, dr, eps2);
+    const P dr = pfma(u[q + 1], K.m1, u[q + 2]);
+    const P tr = pfma(dr, dr, K.eps2);
     const P sr = pmul(tr, tr);
     const P T = padd(tl, tr), Pd = pmul(dl, dr);
     // sqrt(z/2), then z/2
-    const P z0 = mk2(fma(T.x, C1, fma(Pd.x, C2, c3)), fma(T.y, C1, fma(Pd.y, C2, c3)));
+    const P z0 = pfma(T, K.C1, pfma(Pd, K.C2, K.c3));
     const P zh = pmul(z0, z0);
     const P xy = pmul(sl, sr);
     const P p = pfma(cA, dl, pmul(cB, dr));         // (5 d_r + d_l)/6, upwind orientation
@@ -150,7 +163,7 @@ ESBGK_DEV void walk_line(const P (&u)[7], P eps2, R c3, P cA, P cB, P sgnh, P vs
     const P num = pfma(xy, p, pmul(zh, tt));
     const P den = pfma(zh, padd(sl, sr), xy);
     const P face = pfma(sgnh, pmul(num, mk2(rcp_(den.x), rcp_(den.y))), u[q + 1]);
-    if (q > 0) out[(q - 1) * stride] = pmul(vs, mk2(face.x - prev.x, face.y - prev.y));
+    if (q > 0) out[(q - 1) * stride] = pmul(vs, pfma(prev, K.m1, face));
     prev = face;
     dl = dr;
     tl = tr;
@@ -158,45 +171,79 @@ ESBGK_DEV void walk_line(const P (&u)[7], P eps2, R c3, P cA, P cB, P sgnh, P vs
   }
 }
 
+// The discrete Gaussian of a cell at node pairs, for the projection sums and
+// the relaxation pass of the tiled kernel (float arithmetic).  Both passes
+// must see the same G at every node, or the projected Gaussian's moments miss
+// their targets by rounding each stage, so both evaluate it through these
+// functions, from the same per-cell pairs and the same velocity-table entries.
+// The per-cell parameters are splatted into register pairs once per cell
+// (paired instructions take register pairs only).
+struct Gauss2 {
+  float2 qxx, qxy, qyy, pref, isT, u;  // u = (u_x, u_y)
+};
+ESBGK_DEV Gauss2 gauss2(const CellPar<float>& P) {
+  return Gauss2{splat2(P.qxx), splat2(P.qxy), splat2(P.qyy), splat2(P.pref), splat2(P.isT), make_float2(P.ux, P.uy)};
+}
+// Row terms of a group of 4 nodes whose first node has velocity v = (v_x, v_y)
+// (a velocity-table entry): c0 = v_x - u_x of the group's pairs (nodes 0, 1)
+// and c1 (nodes 2, 3), cyy = (v_y - u_y, v_y - u_y), and the exponent's
+// row parts qy = qyy cy^2, qc = qxy cy.  m1 = (-1, -1), off = (0, dv),
+// two = (2 dv, 2 dv).
+struct Row2 {
+  float2 c0, c1, cyy, qy, qc;
+};
+ESBGK_DEV Row2 row2(const Gauss2& Q, float2 v, float2 m1, float2 off, float2 two) {
+  const float2 cg = __ffma2_rn(Q.u, m1, v);
+  Row2 r;
+  r.c0 = __fadd2_rn(splat2(cg.x), off);
+  r.c1 = __fadd2_rn(r.c0, two);
+  r.cyy = splat2(cg.y);
+  r.qy = __fmul2_rn(Q.qyy, __fmul2_rn(r.cyy, r.cyy));
+  r.qc = __fmul2_rn(Q.qxy, r.cyy);
+  return r;
+}
+// G and x = (v_x - u_x)/sqrt(T) at the pair cx of a row.
+ESBGK_DEV void gauss_pair(const Gauss2& Q, const Row2& r, float2 cx, float2& G, float2& x) {
+  const float2 e = __ffma2_rn(Q.qxx, __fmul2_rn(cx, cx), __ffma2_rn(r.qc, cx, r.qy));
+  G = __fmul2_rn(Q.pref, make_float2(exp2r(e.x), exp2r(e.y)));
+  x = __fmul2_rn(cx, Q.isT);
+}
+
 // Projection sums of the discrete Gaussian (the 15 sums of project), factored
-// by velocity rows: along a row segment v_y is fixed, so the lane sums
-// G x^p (p = 0..4) over the segment's node pairs and then adds them times
-// y^q into the 15 sums once per segment.  Segments are half rows (N_v a
-// multiple of 4: the tiled kernel's per-cell groups of 4 nodes).  The
-// relaxation pass must see the same G at every node, or the projected
-// Gaussian's moments miss their targets by rounding each stage: each node's
-// v_x - u_x and exponent are formed exactly as the relaxation pass forms
-// them (group start from the velocity table's expression, then + j dv).
-// The sums are then solved as in project.
-ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P) {
-  const float v0 = g.fv0, dv = g.fdv;
+// by velocity rows: along a half row v_y is fixed, so the lane sums G x^p
+// (p = 0..4) over the half row's node pairs and then adds them times y^q into
+// the 15 sums once per half row (N_v a multiple of 4).  The sums are then
+// solved as in project.
+ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P, const float2* vt) {
   const int seg = g.nv / 2, nseg = g.nvv / seg;
-  const float2 qxx2 = splat2(P.qxx), isT2 = splat2(P.isT), pref2 = splat2(P.pref);
+  const Gauss2 Q = gauss2(P);
+  const float2 m1 = splat2(-1.0f), off = make_float2(0.0f, g.fdv), two = splat2(2.0f * g.fdv);
   float s[15];
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = 0.0f;
 #pragma unroll 1
   for (int sg = lane; sg < nseg; sg += 32) {
-    const int ky = sg >> 1, kx0 = (sg & 1) * seg;
-    const float cy = (v0 + float(ky) * dv) - P.uy, y = cy * P.isT;
-    const float2 qy2 = splat2(P.qyy * cy * cy), qc2 = splat2(P.qxy * cy);
+    const int k0 = (sg >> 1) * g.nv + (sg & 1) * seg;  // first node of the half row
     float2 R0 = splat2(0.0f), R1 = R0, R2 = R0, R3 = R0, R4 = R0;
+    float cy = 0.0f;
 #pragma unroll 2
-    for (int j = 0; j < seg; j += 2) {
-      const int kg = kx0 + (j & ~3);  // first node of the relaxation pass's group
-      const float cxa = ((v0 + float(kg) * dv) - P.ux) + float(j & 3) * dv;
-      const float2 cx = make_float2(cxa, cxa + dv);
-      const float2 e = __ffma2_rn(qxx2, __fmul2_rn(cx, cx), __ffma2_rn(qc2, cx, qy2));
-      const float2 G = __fmul2_rn(pref2, make_float2(exp2r(e.x), exp2r(e.y)));
-      const float2 x = __fmul2_rn(cx, isT2);
-      const float2 t1 = __fmul2_rn(G, x), t2 = __fmul2_rn(t1, x), t3 = __fmul2_rn(t2, x);
-      R0 = __fadd2_rn(R0, G);
-      R1 = __fadd2_rn(R1, t1);
-      R2 = __fadd2_rn(R2, t2);
-      R3 = __fadd2_rn(R3, t3);
-      R4 = __ffma2_rn(t3, x, R4);
+    for (int m = 0; m < seg; m += 4) {
+      const Row2 r = row2(Q, vt[(k0 + m) >> 1], m1, off, two);
+      cy = r.cyy.x;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2 G, x;
+        gauss_pair(Q, r, h ? r.c1 : r.c0, G, x);
+        const float2 t1 = __fmul2_rn(G, x), t2 = __fmul2_rn(t1, x), t3 = __fmul2_rn(t2, x);
+        R0 = __fadd2_rn(R0, G);
+        R1 = __fadd2_rn(R1, t1);
+        R2 = __fadd2_rn(R2, t2);
+        R3 = __fadd2_rn(R3, t3);
+        R4 = __ffma2_rn(t3, x, R4);
+      }
     }
-    const float r[5] = {R0.x + R0.y, R1.x + R1.y, R2.x + R2.y, R3.x + R3.y, R4.x + R4.y};
+    const float y = cy * P.isT;
+    const float rr[5] = {R0.x + R0.y, R1.x + R1.y, R2.x + R2.y, R3.x + R3.y, R4.x + R4.y};
     float yq[5];
     yq[0] = 1.0f;
 #pragma unroll
@@ -204,7 +251,7 @@ ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P) {
 #pragma unroll
     for (int pp = 0; pp < 5; ++pp)
 #pragma unroll
-      for (int q = 0; q + pp < 5; ++q) s[mono(pp, q)] = fmaf(r[pp], yq[q], s[mono(pp, q)]);
+      for (int q = 0; q + pp < 5; ++q) s[mono(pp, q)] = fmaf(rr[pp], yq[q], s[mono(pp, q)]);
   }
 #pragma unroll
   for (int n = 0; n < 15; ++n) s[n] = warp_sum(s[n]) * g.fw;
@@ -271,9 +318,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
   S* fout = (S*)A.f_out;
   const R idx = pick<R>(1.0 / g.dx, g.fidx), idy = pick<R>(1.0 / g.dy, g.fidy);
   const P cL2 = psplat(pick<R>(A.star_cL, A.f_star_cL));
-  const R epsw = pick<R>(V.m.eps_w, V.m.feps_w);
-  const P eps2 = psplat(epsw);
-  const R c3 = epsw * R((1.0 - 55.0 / 6.0) / 1.4142135623730951);
+  const WalkConst<P> WK = walk_const<P, R>(pick<R>(V.m.eps_w, V.m.feps_w));
   const S* ain[nacc > 0 ? nacc : 1];
   S* aout[nacc > 0 ? nacc : 1];
   P aL2[nacc > 0 ? nacc : 1];
@@ -323,6 +368,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
     const unsigned o0 = cvalid ? (unsigned)ccell * (unsigned)nvv : 0u;
     R u0x = R(0), u0y = R(0);
     if (cvalid) ref_velocity(A.U_prev, g.nc, ccell, u0x, u0y);
+    const P u0p = mk2(u0x, u0y), offp = mk2(R(0), dv);
     P m2[6];
     R mc_s[COMP ? 6 : 1], mc_c[COMP ? 6 : 1];  // compensated sums: running sum and compensation
 #pragma unroll
@@ -386,8 +432,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
         const P cA = mk2(px ? R(1.0 / 6.0) : R(5.0 / 6.0), py ? R(1.0 / 6.0) : R(5.0 / 6.0));
         const P cB = mk2(px ? R(5.0 / 6.0) : R(1.0 / 6.0), py ? R(5.0 / 6.0) : R(1.0 / 6.0));
         const P sgnh = mk2(px ? R(0.5) : R(-0.5), py ? R(0.5) : R(-0.5));
-        walk_line<P, R>(u, eps2, c3, cA, cB, sgnh, mk2(vw.x * wscale, vw.y * wscale), (xwalk ? Lx : Ly) + wout,
-                        wstride);
+        walk_line<P, R>(u, WK, cA, cB, sgnh, mk2(vw.x * wscale, vw.y * wscale), (xwalk ? Lx : Ly) + wout, wstride);
       }
       __syncthreads();
       // --- cell phase: lanes take pairs lane and lane + 32 of the chunk
@@ -411,8 +456,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
           else
             IO::st(fout + o0 + k, F, kb);
           const P v = vt[pr];
-          const R cxa = v.x - u0x;
-          const P cx = mk2(cxa, cxa + dv), cy = psplat(v.y - u0y);
+          P cx, cy;
+          if constexpr (F32) {
+            const float2 cg = __ffma2_rn(u0p, WK.m1, v);  // (v_x - u0_x, v_y - u0_y)
+            cx = __fadd2_rn(splat2(cg.x), offp);
+            cy = splat2(cg.y);
+          } else {
+            const R cxa = v.x - u0x;
+            cx = mk2(cxa, cxa + dv);
+            cy = psplat(v.y - u0y);
+          }
           const P xf = pmul(cx, F), yf = pmul(cy, F);
           m2[0] = padd(m2[0], F);
           m2[1] = padd(m2[1], xf);
@@ -468,7 +521,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
         CellPar<R> Pp;
         bool ok = es_params<R>(m, u0x, u0y, pick<R>(g.w, g.fw), pick<R>(V.m.beta, V.m.fbeta), hh, true, Pp);
         if constexpr (F32 && !SX) {
-          if (ok) ok = project_rows(g, lane, Pp);
+          if (ok) ok = project_rows(g, lane, Pp, vt);
         } else {
           if (ok) ok = project<R, W3, 32>(g, lane, Pp);
         }
@@ -479,6 +532,57 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
 #pragma unroll
         for (int t = 0; t < nacc; ++t) aQ2[t] = psplat(aQ[t]);
         const int ngroups = nvv / W3;
+        if constexpr (F32 && !SX) {
+          // float: the Gaussian through the projection's own pair functions
+          // (bit-identical G), two register sets of the partial accumulators
+          // loaded one group ahead
+          const Gauss2 Q2 = gauss2(Pp);
+          const float2 m1 = splat2(-1.0f), off = make_float2(0.0f, dv), two = splat2(2.0f * dv);
+          const float2 a3 = splat2(Pp.a[3]), a1 = splat2(Pp.a[1]), a4 = splat2(Pp.a[4]);
+          const float2 a2 = splat2(Pp.a[2]), a5 = splat2(Pp.a[5]), a0p1 = splat2(1.0f + Pp.a[0]);
+          P paA[2][nacc > 0 ? nacc : 1], paB[2][nacc > 0 ? nacc : 1];
+          auto load_g = [&](int gi, P (&pa)[2][nacc > 0 ? nacc : 1]) {
+            const unsigned kg = (unsigned)gi * 4u;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+              for (int t = 0; t < nacc; ++t) pa[j][t] = IO::ldc(aout[t] + o0 + kg + 2 * j);
+          };
+          auto relax_g = [&](int gi, const P (&pa)[2][nacc > 0 ? nacc : 1]) {
+            const unsigned kg = (unsigned)gi * 4u;
+            const Row2 r = row2(Q2, vt[kg / 2], m1, off, two);
+            const float2 y = __fmul2_rn(r.cyy, Q2.isT);
+            const float2 c0 = __ffma2_rn(__ffma2_rn(a5, y, a2), y, a0p1), c1 = __ffma2_rn(a4, y, a1);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const unsigned k = kg + 2 * j;
+              const float2 F = *reinterpret_cast<const float2*>(fs + k);
+              float2 Fn = F, Q = splat2(0.0f);
+              if (ok) {
+                float2 G, x;
+                gauss_pair(Q2, r, j ? r.c1 : r.c0, G, x);
+                const float2 Gh = __fmul2_rn(G, __ffma2_rn(__ffma2_rn(a3, x, c1), x, c0));
+                // f = (f* + h G_hat)/(1 + h); Q = nu (G_hat - f*)/(1 + h)
+                Fn = __fmul2_rn(__ffma2_rn(h2, Gh, F), i2);
+                Q = __fmul2_rn(nq, __ffma2_rn(F, m1, Gh));
+              }
+              const uint32_t kb = s0 + ((o0 + k) << 3);
+              IO::st(fout + o0 + k, Fn, kb);
+#pragma unroll
+              for (int t = 0; t < nacc; ++t) IO::st(aout[t] + o0 + k, __ffma2_rn(aQ2[t], Q, pa[j][t]), kb + 4 + t);
+            }
+          };
+          if (lane < ngroups) load_g(lane, paA);
+          for (int gi = lane; gi < ngroups; gi += 64) {
+            if (gi + 32 < ngroups) load_g(gi + 32, paB);
+            relax_g(gi, paA);
+            if (gi + 32 < ngroups) {
+              if (gi + 64 < ngroups) load_g(gi + 64, paA);
+              relax_g(gi + 32, paB);
+            }
+          }
+          continue;
+        }
         // accumulator partials of the next group loaded one iteration ahead
         P pan[W3 / 2][nacc > 0 ? nacc : 1];
         auto load_pa = [&](int gi) {

@@ -74,6 +74,7 @@ def test_riemann_full_size_200_steps_against_oracle_record(prec):
     assert int(rec["kin_count"][-1]) == int(s.flags().sum())
 
 
+@pytest.mark.skipif(not os.path.exists(BLOB), reason="the oracle's record of the precision-form run is not written")
 @pytest.mark.parametrize("prec,sums", [("fp64", "plain"), ("fp32", "plain"), ("fp32", "compensated"),
                                        ("bf16", "plain")])
 def test_blob_full_size_100_steps_against_oracle_record(prec, sums):

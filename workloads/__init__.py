@@ -211,3 +211,30 @@ def batched_cases(n_cases=64, seed0=0, sizes=None, nvs=None, steps=100):
             fields=dict(rho=rho, ux=z.copy(), uy=z.copy(), T=T, eps=np.full_like(rho, eps),
                         kin=np.ones(rho.shape, bool))))
     return cases
+
+
+def obstacle_flow(kind="cylinder", n=78, nv=32, vmax=8.0, eps=1e-6, eta_factor=10.0, t_end=0.15, cfl=0.5,
+                  initial="fluid", switch="plain"):
+    """Tests 5 and 6 (Sec. 4.2.3-4.2.4): flow u = (2, 0), rho = 1, p = 1 on
+    [0,1]^2 (n x n cells, outflow edges) toward a solid cylinder of radius 1/12
+    (kind='cylinder') or a rectangle of 10 x 4 cells (kind='rectangle')
+    centred at (2/5, 1/2); eps = 1e-6, eta = 10 eps, delta = 1e-3, 32^2
+    velocities on [-8, 8]^2, dt = 0.5 min(dx, dy)/8 to t_end = 0.15.
+    'solid' in the result is the obstacle mask (cell centres inside it)."""
+    X, Y = _centres(n, n, 0, 1, 0, 1)
+    xc, yc = 0.4, 0.5
+    if kind == "cylinder":
+        solid = (X - xc) ** 2 + (Y - yc) ** 2 < (1.0 / 12.0) ** 2
+    else:
+        solid = (np.abs(X - xc) < 5.0 / n) & (np.abs(Y - yc) < 2.0 / n)
+    rho = np.ones_like(X)
+    dt0 = _dt(cfl, n, n, 0, 1, 0, 1, vmax)
+    steps = int(np.ceil(t_end / dt0))
+    kin = np.zeros(X.shape, bool) if initial == "fluid" else np.ones(X.shape, bool)
+    return dict(
+        grid=dict(nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="outflow", bc_y="outflow"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS, switch=switch, eta_factor=eta_factor), scheme="ars233",
+        dt=t_end / steps, steps=steps,
+        fields=dict(rho=rho, ux=np.full_like(rho, 2.0), uy=np.zeros_like(rho), T=np.ones_like(rho),
+                    eps=np.full_like(rho, eps), kin=kin),
+        solid=solid)
