@@ -34,27 +34,14 @@ void launch_init_state(const double* prim, const uint8_t* kin_in, double* Un, do
   init_state_kernel<<<(nc + 255) / 256, 256, 0, s>>>(prim, kin_in, Un, eps, flags, flags_prev, nc);
 }
 
-// 1/x and sqrt(x) in float64 for positive normal x: a float estimate refined
-// by two Newton-Raphson steps (the error squares at each step, so 2^-24
-// becomes far below float64 rounding); cheaper than the float64 divide and
-// square-root sequences on GB300's narrow FP64 pipe.
-__device__ __forceinline__ double rcp_nr(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = r * fma(-x, r, 2.0);
-  return r * fma(-x, r, 2.0);
-}
-__device__ __forceinline__ double sqrt_nr(double x) {
-  if (!(x > 0.0)) return 0.0;
-  double y = (double)rsqrtf((float)x);  // y ~ 1/sqrt(x)
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  return x * y;
-}
-
 // Reciprocal and square root in the criterion's arithmetic type.
-__device__ __forceinline__ double crit_rcp(double x) { return rcp_nr(x); }
+// In float64 these are the correctly rounded IEEE operations: the criterion
+// meets arguments far outside float's range (lambda_A^2 ~ 1e-52 where the
+// flow is uniform), where a float seed refined by Newton steps would start at
+// 0 or infinity.  One cell's criterion costs a few of them per step.
+__device__ __forceinline__ double crit_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float crit_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double crit_sqrt(double x) { return sqrt_nr(x); }
+__device__ __forceinline__ double crit_sqrt(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
 __device__ __forceinline__ float crit_sqrt(float x) { return x > 0.0f ? sqrtf(x) : 0.0f; }
 
 // Regime criteria of Sec. 3.1.2 for one cell.  X = I - S_1 with

@@ -175,6 +175,29 @@ def test_riemann_plain_switch_fp32():
     assert worst.max() <= TOL["fp32"], worst
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_criterion_in_nearly_uniform_flow(prec):
+    """Sec. 3.1.2's lambda_A where the flow is uniform up to rounding: with
+    eps = 1e-12 and density ripples of 1e-14, (X_xx - X_yy)^2/4 + X_xy^2 is
+    ~1e-49, below float's range; the criterion must stay finite and equal the
+    oracle's, and no cell turns kinetic."""
+    wl = W.obstacle_flow("cylinder", n=30, nv=16)
+    rng = np.random.default_rng(7)
+    f = wl["fields"]
+    f["rho"] = f["rho"] * (1.0 + 1e-14 * rng.standard_normal(f["rho"].shape))
+    f["eps"] = np.full_like(f["eps"], 1e-12)
+    g = gpu_solver(wl, prec)
+    P, st = oracle_pair(wl)
+    g.regime_update()
+    lam_g, _ = g.indicators()
+    lam_o, _ = O.regime_indicators(P, st)
+    eta = P.eta_factor * st.eps
+    assert np.isfinite(lam_g).all()
+    assert lam_o.max() < 1e-20
+    assert np.all(np.abs(lam_g - lam_o) <= 1e-9 * np.maximum(lam_o, eta))
+    assert not g.flags().any()
+
+
 def test_riemann_full_size_first_steps():
     """Coupled configuration at its full size (128^2 cells, 32^2 velocities on
     [-8,8]^2, dynamic switch, ARS(2,3,3)) in FP64: two steps against the
