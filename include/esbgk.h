@@ -246,13 +246,15 @@ int esbgk_kinetic_form(const esbgk_ctx* ctx, int32_t* nodes_per_group, int32_t* 
  * is kinetic (the last esbgk_set_state or esbgk_set_flags map) and the regime
  * is frozen (ESBGK_SWITCH_FROZEN), the specialised stage launches run on
  * tiles of 4 x 4 cells whose threads compute each CWENO3 face once and share
- * it between the two cells it separates (the per-cell kernel computes every
- * face twice).  Needs an even N_v and f* of 16 cells in shared memory
- * (on GB300: N_v <= 54 in FP32/BF16 storage, N_v <= 34 in FP64); other
- * problems keep the per-cell kernel.  Results agree with the per-cell kernel
- * to rounding (a different but equivalent order of the face arithmetic).
- * esbgk_tiles enables it (default) or disables it; host only, no launch.
- * esbgk_tiled reports whether the next step's stages take it. */
+ * it between the two cells it separates (2.5 faces per cell and node; the
+ * per-cell kernel computes 4).  Needs an even N_v and f* of 16 cells in
+ * shared memory (on GB300: N_v <= 54 in FP32/BF16 storage, N_v <= 34 in
+ * FP64); other problems keep the per-cell kernel.  Results agree with the
+ * per-cell kernel to rounding (a different but equivalent order of the face
+ * arithmetic).  esbgk_tiles enables (enable != 0) or disables it (the
+ * default: on GB300 the per-cell kernel is as fast at the sizes measured);
+ * host only, no launch.  esbgk_tiled reports whether the next step's stages
+ * take it. */
 int esbgk_tiles(esbgk_ctx* ctx, int32_t enable);
 int esbgk_tiled(const esbgk_ctx* ctx, int32_t* tiled);
 

@@ -154,7 +154,10 @@ def flux_moments(F, v, w):
 
 def euler_flux(U, d):
     """Physical Euler flux F_x (d=0) or F_y (d=1) of Eq. Euler_Compact, with
-    P = (gamma - 1)(E - 1/2 rho |u|^2).  U: (4, ...)."""
+    P = (gamma - 1)(E - 1/2 rho |u|^2), and the local wave speed
+    |u_n| + sqrt(gamma P / rho).  U: (4, ...).  Reading R25: a reconstructed
+    face state whose pressure is not positive has no sound speed; its wave
+    speed is |u_n| (the sound speed with P clipped at 0)."""
     rho, mx, my, E = U
     ux, uy = mx / rho, my / rho
     P = (GAMMA - 1.0) * (E - 0.5 * rho * (ux * ux + uy * uy))
@@ -162,7 +165,7 @@ def euler_flux(U, d):
     return np.stack([rho * un,
                      mx * un + (P if d == 0 else 0.0),
                      my * un + (P if d == 1 else 0.0),
-                     un * (E + P)]), np.abs(un) + np.sqrt(GAMMA * P / rho)
+                     un * (E + P)]), np.abs(un) + np.sqrt(GAMMA * np.maximum(P, 0.0) / rho)
 
 
 def euler_phi(U, dx, dy, bc_x, bc_y, eps_w, override=None, walls=None):

@@ -255,7 +255,7 @@ class Solver:
 
     def tiles(self, enable=True):
         """Enable or disable the tiled stage kernel (every cell kinetic,
-        regime frozen)."""
+        regime frozen); off by default."""
         self._check(self._abi.esbgk_tiles(self._ctx, int(bool(enable))), "tiles")
 
     def tiled(self):

@@ -192,7 +192,7 @@ struct esbgk_ctx {
   // every cell kinetic as far as the host knows (the last set_state or
   // set_flags map); with the regime frozen the stages may use the tiled kernel
   bool all_kin = false;
-  bool tiles_on = true;
+  bool tiles_on = false;
   bool tiled() const { return tiles_on && all_kin && sw == ESBGK_SWITCH_FROZEN; }
   void drop_graphs() {
     for (auto& e : graphs) {

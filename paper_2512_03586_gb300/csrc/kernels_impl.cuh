@@ -450,7 +450,8 @@ ESBGK_DEV void stencil_offsets(const Geo& g, int c, unsigned (&o)[8]) {
 // Euler part (fluid cells), one lane per cell.
 
 // Physical flux of Eq. Euler_Compact along d (0 = x, 1 = y), gamma = 2, and the
-// local wave speed |u_d| + sqrt(gamma P/rho).
+// local wave speed |u_d| + sqrt(gamma P/rho); a reconstructed face state whose
+// pressure is not positive has no sound speed (P clipped at 0 in the speed).
 template <typename R>
 ESBGK_DEV void euler_phys(const R (&U)[4], int d, R (&F)[4], R& a) {
   const R rho = U[0], ux = U[1] / rho, uy = U[2] / rho;
@@ -460,7 +461,7 @@ ESBGK_DEV void euler_phys(const R (&U)[4], int d, R (&F)[4], R& a) {
   F[1] = U[1] * un + (d == 0 ? P : R(0));
   F[2] = U[2] * un + (d == 1 ? P : R(0));
   F[3] = un * (U[3] + P);
-  a = rabs(un) + rsqrt_(R(2) * P / rho);
+  a = rabs(un) + rsqrt_(R(2) * rmax(P, R(0)) / rho);
 }
 
 // Phi(U)(c): CWENO3 face states per component, local Lax-Friedrichs flux at
@@ -1762,27 +1763,31 @@ struct Launch {
   // modes, an even N_v, the per-pair arrays aligned, no fused L1 deviation,
   // and f* of a whole tile in shared memory.
   using TileFn = void (*)(StageArgs, View);
-  template <int M>
+  template <int M, int E>
   static TileFn tile_variant(bool sx, bool comp) {
-    if (comp) return sx ? tile_stage_kernel<S, M, true, true> : tile_stage_kernel<S, M, false, true>;
-    return sx ? tile_stage_kernel<S, M, true, false> : tile_stage_kernel<S, M, false, false>;
+    if (comp) return sx ? tile_stage_kernel<S, M, true, true, E> : tile_stage_kernel<S, M, false, true, E>;
+    return sx ? tile_stage_kernel<S, M, true, false, E> : tile_stage_kernel<S, M, false, false, E>;
+  }
+  template <int E>
+  static TileFn tile_edge_fn(int m, bool sx, bool comp) {
+    switch (m) {
+      case kFirstRelax2: return tile_variant<kFirstRelax2, E>(sx, comp);
+      case kLoadedRelax1: return tile_variant<kLoadedRelax1, E>(sx, comp);
+      case kFinal: return tile_variant<kFinal, E>(sx, comp);
+      case kFirstRelax0: return tile_variant<kFirstRelax0, E>(sx, comp);
+      default: return nullptr;
+    }
   }
   // compensated sums only change the float arithmetic
   static TileFn tile_fn(int m, bool sx, bool comp) {
     comp = comp && std::is_same<R, float>::value;
-    switch (m) {
-      case kFirstRelax2: return tile_variant<kFirstRelax2>(sx, comp);
-      case kLoadedRelax1: return tile_variant<kLoadedRelax1>(sx, comp);
-      case kFinal: return tile_variant<kFinal>(sx, comp);
-      case kFirstRelax0: return tile_variant<kFirstRelax0>(sx, comp);
-      default: return nullptr;
-    }
+    return tile_edge_fn<kTileEdge>(m, sx, comp);
   }
   static bool aligned_pair(const void* p) { return ((uintptr_t)p % (2 * sizeof(S))) == 0; }
   static int tile_ok(const StageArgs& A, const Geo& g) {
     const int mode = stage_mode(A);
     if (mode == kGeneric || g.nv % 2 != 0 || A.l1_out || A.iface) return 0;
-    if (TileSmem<R>::bytes(g) > (size_t)max_smem()) return 0;
+    if (TileSmem<R, kTileEdge>::bytes(g) > (size_t)max_smem()) return 0;
     if (!aligned_pair(A.f_src) || !aligned_pair(A.star_base) || !aligned_pair(A.f_out)) return 0;
     for (int t = 0; t < A.nacc; ++t)
       if (!aligned_pair(A.acc_in[t]) || !aligned_pair(A.acc_out[t])) return 0;
@@ -1791,22 +1796,23 @@ struct Launch {
   static void stage_tile(const StageArgs& A, const View& V, int grid, cudaStream_t s) {
     const Geo& g = V.g;
     const TileFn fn = tile_fn(stage_mode(A), (g.nv / 2) % 2 != 0, V.m.comp_moments != 0);
-    const size_t smem = TileSmem<R>::bytes(g);
-    const int ntiles = ((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY);
-    int gr = rescale(g, grid, (const void*)fn, kTileThreads, smem);
+    const size_t smem = TileSmem<R, kTileEdge>::bytes(g);
+    constexpr int E = kTileEdge, threads = TileShape<E>::kThreads;
+    const int ntiles = ((g.nx + E - 1) / E) * ((g.ny + E - 1) / E);
+    int gr = rescale(g, grid, (const void*)fn, threads, smem);
     if (gr > ntiles) gr = ntiles;
-    fn<<<gr, kTileThreads, smem, s>>>(A, V);
+    fn<<<gr, threads, smem, s>>>(A, V);
   }
   static cudaError_t setup(const Geo& g) {
     if ((size_t)g.nvv * sizeof(R) > (size_t)max_smem()) return cudaErrorInvalidValue;
     cudaError_t e;
     const int mx = max_smem();
     for (int m = 0; m < kNumModes; ++m)
-      for (int v = 0; v < 4; ++v)
-        if (tile_fn(m, v & 1, v & 2) &&
-            (e = cudaFuncSetAttribute(tile_fn(m, v & 1, v & 2), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
-                cudaSuccess)
+      for (int v = 0; v < 4; ++v) {
+        const TileFn fn = tile_fn(m, v & 1, v & 2);
+        if (fn && (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
           return e;
+      }
     for (int m = 0; m < kNumModes; ++m)
       for (int v = 0; v < kNumVariants; ++v)
         if ((e = cudaFuncSetAttribute(stage_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=

@@ -1,19 +1,19 @@
 // tile_impl.cuh -- the tiled stage kernel for regions where every cell is kinetic.
 //
-// Included by kernels_impl.cuh.  A CTA owns a tile of kTileX x kTileY cells,
-// one warp per cell (as in stage_kernel), and walks the velocity nodes in
-// chunks of kTilePairs node pairs.  Per chunk:
+// Included by kernels_impl.cuh.  A CTA owns a tile of E x E cells (E = 2 or
+// 4), one warp per cell (as in stage_kernel), and walks the velocity nodes in
+// chunks of 16 E node pairs.  Per chunk:
 //
 //   walk phase   -- the transport of Sec. 3.2 computed per face, not per cell:
 //                   a thread takes one node pair and one tile row (x walk) or
-//                   column (y walk), loads the 7 upwind-relevant values of the
-//                   line (two ghost cells each side), forms the 5 CWENO3 face
-//                   values between its 4 cells once each, and writes
-//                   v (F_{i+1/2} - F_{i-1/2}) / dx of its 4 cells to shared
+//                   column (y walk), loads the E + 3 upwind-relevant values
+//                   of the line (two ghost cells each side), forms the E + 1
+//                   CWENO3 face values of its E cells once each, and writes
+//                   v (F_{i+1/2} - F_{i-1/2}) / dx of its E cells to shared
 //                   memory.  A cell's 4 faces are shared with its neighbours,
-//                   so the tile computes 2.5 faces per cell and node instead
-//                   of 4; neighbouring faces also share one difference and its
-//                   smoothness term.
+//                   so the tile computes 2 (E + 1) / E faces per cell and node
+//                   instead of 4; neighbouring faces also share one
+//                   difference and its smoothness term.
 //   cell phase   -- the warp of each cell adds its x and y parts, forms
 //                   f* = base + c_L L and the partial accumulators, keeps f*
 //                   in shared memory and sums the moments of f* (Eq. RKEI1).
@@ -40,12 +40,24 @@
 
 namespace esbgk {
 
-constexpr int kTileX = 4, kTileY = 4;
-constexpr int kTileCells = kTileX * kTileY;
-constexpr int kTileThreads = 32 * kTileCells;  // one warp per cell
-constexpr int kTilePairs = 64;                 // node pairs per chunk: (kTileX + kTileY) * kTilePairs walks
-static_assert((kTileX + kTileY) * kTilePairs == kTileThreads, "one walk per thread and chunk");
-static_assert(kTilePairs == 64, "the cell phase gives each lane two pairs");
+// A tile of E x E cells, one warp per cell.  A chunk holds 16 E node pairs,
+// so that the 2 E lines (E rows, E columns) of a chunk give every thread one
+// walk, and every lane of the cell phase E / 2 pairs.  E = 4: one CTA of 16
+// warps per SM, 2.5 faces per cell and node.  E = 2 (four CTAs of 4 warps per
+// SM, whose load and compute phases interleave, 3 faces per cell and node)
+// took 4.38 ms per step of the 256^2 x 48^2 all-kinetic run against 3.24 ms
+// for E = 4: twice the chunks per cell and 5 instead of 3.5 line loads per
+// value; the library builds E = 4 only.
+template <int E>
+struct TileShape {
+  static constexpr int kCells = E * E;
+  static constexpr int kThreads = 32 * kCells;
+  static constexpr int kPairs = 16 * E;
+  static constexpr int kHalves = kPairs / 32;
+  static constexpr int kMinBlocks = E == 4 ? 1 : 4;
+  static_assert(2 * E * kPairs == kThreads && kPairs % 32 == 0, "one walk per thread and chunk");
+};
+constexpr int kTileEdge = 4;
 
 // Two lanes of arithmetic: paired FP32 instructions for float, component-wise
 // for double.
@@ -132,24 +144,24 @@ ESBGK_DEV WalkConst<P> walk_const(R epsw) {
                       psplat(epsw * R((1.0 - 55.0 / 6.0) / 1.4142135623730951))};
 }
 
-// Upwind CWENO3 faces along one line of the tile and the transport of its 4
-// cells.  u[0..6]: the pair's values in 7 consecutive cells, shifted so that
-// u[q+1] is the upwind cell of face q, the face between tile cells q-1 and q
-// (q = 0..4): cells -2..4 of the line for velocities toward increasing cell
-// index, -1..5 otherwise.  Per node of the pair: (cA, cB) = (1/6, 5/6) toward
+// Upwind CWENO3 faces along one line of the tile and the transport of its NL
+// cells.  u[0..NL+2]: the pair's values in NL+3 consecutive cells, shifted so
+// that u[q+1] is the upwind cell of face q, the face between tile cells q-1
+// and q (q = 0..NL): cells -2..NL of the line for velocities toward
+// increasing cell index, -1..NL+1 otherwise.  Per node of the pair: (cA, cB) = (1/6, 5/6) toward
 // increasing index, (5/6, 1/6) the other way, sgnh = +1/2 / -1/2; K the
 // constant pairs (walk_const); vs = v / h.  Writes
 // v (face_{q+1} - face_q) / h of tile cell q to out[q * stride].  The faces
 // are formed in order, each from the difference behind and the difference
 // ahead of its upwind cell, so only two differences are live at a time.
-template <typename P, typename R>
-ESBGK_DEV void walk_line(const P (&u)[7], const WalkConst<P>& K, P cA, P cB, P sgnh, P vs, P* out, int stride) {
+template <typename P, typename R, int NL>
+ESBGK_DEV void walk_line(const P (&u)[NL + 3], const WalkConst<P>& K, P cA, P cB, P sgnh, P vs, P* out, int stride) {
   P dl = pfma(u[0], K.m1, u[1]);
   P tl = pfma(dl, dl, K.eps2);
   P sl = pmul(tl, tl);
   P prev = psplat(R(0));
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q <= NL; ++q) {
     const P dr = pfma(u[q + 1], K.m1, u[q + 2]);
     const P tr = pfma(dr, dr, K.eps2);
     const P sr = pmul(tr, tr);
@@ -210,12 +222,14 @@ ESBGK_DEV void gauss_pair(const Gauss2& Q, const Row2& r, float2 cx, float2& G, 
 }
 
 // Projection sums of the discrete Gaussian (the 15 sums of project), factored
-// by velocity rows: along a half row v_y is fixed, so the lane sums G x^p
-// (p = 0..4) over the half row's node pairs and then adds them times y^q into
-// the 15 sums once per half row (N_v a multiple of 4).  The sums are then
-// solved as in project.
+// by velocity rows: along a row segment v_y is fixed, so the lane sums G x^p
+// (p = 0..4) over the segment's node pairs and then adds them times y^q into
+// the 15 sums once per segment.  A segment is a run of whole groups of 4
+// nodes (the relaxation pass's groups): a half row when N_v/2 is a multiple
+// of 4, else a whole row (N_v a multiple of 4).  The sums are then solved as
+// in project.
 ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P, const float2* vt) {
-  const int seg = g.nv / 2, nseg = g.nvv / seg;
+  const int seg = (g.nv / 2) % 4 == 0 ? g.nv / 2 : g.nv, nseg = g.nvv / seg;
   const Gauss2 Q = gauss2(P);
   const float2 m1 = splat2(-1.0f), off = make_float2(0.0f, g.fdv), two = splat2(2.0f * g.fdv);
   float s[15];
@@ -223,7 +237,7 @@ ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P, const flo
   for (int n = 0; n < 15; ++n) s[n] = 0.0f;
 #pragma unroll 1
   for (int sg = lane; sg < nseg; sg += 32) {
-    const int k0 = (sg >> 1) * g.nv + (sg & 1) * seg;  // first node of the half row
+    const int k0 = sg * seg;  // first node of the segment (segments tile the rows in order)
     float2 R0 = splat2(0.0f), R1 = R0, R2 = R0, R3 = R0, R4 = R0;
     float cy = 0.0f;
 #pragma unroll 2
@@ -260,20 +274,22 @@ ESBGK_DEV bool project_rows(const Geo& g, int lane, CellPar<float>& P, const flo
 
 // Shared-memory layout of the tiled kernel (dynamic): f* of each cell, the
 // x and y transport parts of two chunks, and the per-pair velocities.
-template <typename R>
+template <typename R, int E>
 struct TileSmem {
   static size_t bytes(const Geo& g) {
     using P = typename PairT<R>::T;
-    return (size_t)kTileCells * g.nvv * sizeof(R) + 2 * 2 * kTileCells * kTilePairs * sizeof(P) +
+    using T = TileShape<E>;
+    return (size_t)T::kCells * g.nvv * sizeof(R) + 2 * 2 * T::kCells * T::kPairs * sizeof(P) +
            (size_t)(g.nvv / 2) * sizeof(P);
   }
 };
 
-// Tile t of the grid: its first cell (i0, j0).
+// Tile t of the grid (tiles of E x E cells): its first cell (i0, j0).
+template <int E>
 ESBGK_DEV void tile_origin(const Geo& g, int t, int& i0, int& j0) {
-  const int tx = (g.nx + kTileX - 1) / kTileX;
-  i0 = (t % tx) * kTileX;
-  j0 = (t / tx) * kTileY;
+  const int tx = (g.nx + E - 1) / E;
+  i0 = (t % tx) * E;
+  j0 = (t / tx) * E;
 }
 
 // SX: some node pair straddles v_x = 0 (N_v/2 odd): its two nodes take
@@ -285,15 +301,19 @@ ESBGK_DEV void tile_origin(const Geo& g, int t, int& i0, int& j0) {
 // of two register sets, so they are in flight while the previous chunk
 // computes; the cell phase's base and accumulator values are loaded at the
 // start of their chunk, before its walk.
-template <typename S, int M, bool SX, bool COMP>
-__global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A, View V) {
+template <typename S, int M, bool SX, bool COMP, int E>
+__global__ void __launch_bounds__(TileShape<E>::kThreads, TileShape<E>::kMinBlocks)
+    tile_stage_kernel(StageArgs A, View V) {
+  using TS = TileShape<E>;
+  constexpr int kTileCells = TS::kCells, kTileThreads = TS::kThreads, kTilePairs = TS::kPairs;
+  constexpr int NH = TS::kHalves;
   using R = typename Real<S>::T;
   using P = typename PairT<R>::T;
   using IO = PairIO<S>;
   using MT = ModeT<M>;
   constexpr bool relax = MT::relax;
   constexpr int nacc = MT::nacc;
-  constexpr int NW = SX ? 8 : 7;                    // line values a walk loads
+  constexpr int NW = SX ? E + 4 : E + 3;            // line values a walk loads
   constexpr int NB = 1 + (MT::acc_src ? 0 : nacc);  // base and accumulator inputs of a cell pair
   constexpr bool F32 = std::is_same<R, float>::value;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -333,18 +353,18 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
   const uint32_t s0 = A.seed ? mix32(*A.seed * 0x632be5abu + A.sid) : 0u;
 
   // walk of this thread: x walks (one per tile row) then y walks (one per column)
-  const bool xwalk = tid < kTileY * kTilePairs;
-  const int wline = xwalk ? tid / kTilePairs : (tid - kTileY * kTilePairs) / kTilePairs;
+  const bool xwalk = tid < E * kTilePairs;
+  const int wline = xwalk ? tid / kTilePairs : (tid - E * kTilePairs) / kTilePairs;
   const int wpair = tid % kTilePairs;
   const R wscale = xwalk ? idx : idy;
-  const int wstride = xwalk ? kTilePairs : kTileX * kTilePairs;
-  const int wout = xwalk ? (wline * kTileX) * kTilePairs + wpair : wline * kTilePairs + wpair;
+  const int wstride = xwalk ? kTilePairs : E * kTilePairs;
+  const int wout = xwalk ? (wline * E) * kTilePairs + wpair : wline * kTilePairs + wpair;
   // cell of this warp in the cell phase
-  const int ci = warp % kTileX, cj = warp / kTileX;
+  const int ci = warp % E, cj = warp / E;
   R* fs = fs_all + (size_t)warp * nvv;
 
   constexpr int W3 = SX ? 2 : 4;  // nodes per group of the per-cell passes
-  const int ntiles = ((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY);
+  const int ntiles = ((g.nx + E - 1) / E) * ((g.ny + E - 1) / E);
   const int nchunks = (npairs + kTilePairs - 1) / kTilePairs;
   long long mine = 0;
   // chunks walked so far: the parity picks the transport buffer, so a buffer
@@ -352,12 +372,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
   int gch = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int i0, j0;
-    tile_origin(g, tile, i0, j0);
-    // the walk's line: cells -2..5 of it (boundary conditions applied)
+    tile_origin<E>(g, tile, i0, j0);
+    // the walk's line: cells -2..E+1 of it (boundary conditions applied)
     const bool wvalid = xwalk ? (j0 + wline < g.ny) : (i0 + wline < g.nx);
-    unsigned wb[8];
+    unsigned wb[E + 4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < E + 4; ++q) {
       const int c = xwalk ? (j0 + wline) * g.nx + nb(i0 - 2 + q, g.nx, g.bcx)
                           : nb(j0 - 2 + q, g.ny, g.bcy) * g.nx + (i0 + wline);
       wb[q] = wvalid ? (unsigned)c * (unsigned)nvv : 0u;
@@ -377,7 +397,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
     for (int n = 0; n < (COMP ? 6 : 1); ++n) mc_s[n] = mc_c[n] = R(0);
 
     // two register sets of the walk's loads; chunk c uses set c & 1
-    P wA[NW], wB[NW], cb[2][NB];
+    P wA[NW], wB[NW], cb[NH][NB];
     P vwA = psplat(R(0)), vwB = psplat(R(0));
     bool okA = false, okB = false;
     auto load_walk = [&](int ch, P (&w)[NW], P& vw, bool& ok) {
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
     };
     auto load_cell = [&](int ch) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < NH; ++h) {
         const int prc = ch * kTilePairs + lane + 32 * h;
         if (cvalid && prc < npairs) {
           const unsigned k = 2u * prc;
@@ -416,29 +436,29 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
       P* Ly = Lx + kTileCells * kTilePairs;
       // --- walk phase
       if (ok) {
-        P u[7];
+        P u[E + 3];
         if (SX) {
           // per node: the window of its own direction
 #pragma unroll
-          for (int q = 0; q < 7; ++q) {
+          for (int q = 0; q < E + 3; ++q) {
             u[q].x = vw.x > R(0) ? w[q].x : w[q + 1].x;
             u[q].y = vw.y > R(0) ? w[q].y : w[q + 1].y;
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < 7; ++q) u[q] = w[q];
+          for (int q = 0; q < E + 3; ++q) u[q] = w[q];
         }
         const bool px = vw.x > R(0), py = vw.y > R(0);
         const P cA = mk2(px ? R(1.0 / 6.0) : R(5.0 / 6.0), py ? R(1.0 / 6.0) : R(5.0 / 6.0));
         const P cB = mk2(px ? R(5.0 / 6.0) : R(1.0 / 6.0), py ? R(5.0 / 6.0) : R(1.0 / 6.0));
         const P sgnh = mk2(px ? R(0.5) : R(-0.5), py ? R(0.5) : R(-0.5));
-        walk_line<P, R>(u, WK, cA, cB, sgnh, mk2(vw.x * wscale, vw.y * wscale), (xwalk ? Lx : Ly) + wout, wstride);
+        walk_line<P, R, E>(u, WK, cA, cB, sgnh, mk2(vw.x * wscale, vw.y * wscale), (xwalk ? Lx : Ly) + wout, wstride);
       }
       __syncthreads();
-      // --- cell phase: lanes take pairs lane and lane + 32 of the chunk
+      // --- cell phase: lanes take pairs lane + 32 h of the chunk
       if (cvalid) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < NH; ++h) {
           const int pl = lane + 32 * h, pr = ch * kTilePairs + pl;
           if (pr >= npairs) continue;
           const unsigned k = 2u * pr;
@@ -475,8 +495,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_stage_kernel(StageArgs A
           m2[5] = pfma(cy, yf, m2[5]);
         }
         if constexpr (COMP && F32) {
-          // the paired runs of 4 chunks (16 nodes per lane) into a Neumaier accumulator
-          if ((ch & 3) == 3 || ch == nchunks - 1) {
+          // the paired runs of 16 nodes per lane into a Neumaier accumulator
+          constexpr int kFlush = 8 / NH;  // chunks
+          if ((ch & (kFlush - 1)) == kFlush - 1 || ch == nchunks - 1) {
 #pragma unroll
             for (int n = 0; n < 6; ++n) {
               comp_add(mc_s[n], mc_c[n], m2[n].x + m2[n].y);

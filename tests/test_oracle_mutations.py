@@ -40,8 +40,11 @@ MUTATIONS = [
      "conservative_interface", "interface energy flux missing the v_y^2 part"),
     ("transport.py", "a = np.maximum(am, ap)", "a = 0.5 * np.maximum(am, ap)", "test_oracle_transport.py",
      "dissipation", "Euler flux with half the Lax-Friedrichs speed"),
-    ("transport.py", "np.abs(un) + np.sqrt(GAMMA * P / rho)", "np.sqrt(GAMMA * P / rho)", "test_oracle_transport.py",
+    ("transport.py", "np.abs(un) + np.sqrt(GAMMA * np.maximum(P, 0.0) / rho)",
+     "np.sqrt(GAMMA * np.maximum(P, 0.0) / rho)", "test_oracle_transport.py",
      "dissipation", "Euler flux speed without the flow speed |u_n|"),
+    ("transport.py", "np.sqrt(GAMMA * np.maximum(P, 0.0) / rho)", "np.sqrt(GAMMA * np.abs(P) / rho)",
+     "test_oracle_transport.py", "without_pressure", "sound speed of a face state with negative pressure from |P|"),
     ("walls.py", "return g[..., ::-1] if axis == 0 else g[..., ::-1, :]", "return g", "test_oracle_walls.py",
      "symmetry", "wall mirror images of f without the specular reflection"),
     ("walls.py", "pm = 2 * a + sg - p", "pm = 2 * a - p", "test_oracle_walls.py", "symmetry",

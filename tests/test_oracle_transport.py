@@ -273,3 +273,20 @@ def test_euler_flux_dissipation_matches_linearisation(d, mode):
          - (-np.exp(-1j * theta) + 5.0 + 2.0 * np.exp(1j * theta)) / 6.0) * np.eye(4)
     other = delta * np.real((M_half @ r)[:, None] * np.exp(1j * (theta * jj + 0.3))[None])
     assert np.abs(other - want).max() > 1e-3 * scale
+
+
+def test_euler_wave_speed_of_a_face_state_without_pressure():
+    """Reading R25: a reconstructed face state whose pressure is not positive
+    (component-wise reconstruction of the conserved variables can give one
+    next to a strong expansion) has no sound speed, so its local
+    Lax-Friedrichs speed is |u_n|; a positive pressure gives
+    |u_n| + sqrt(gamma P/rho).  The flux itself is the physical flux."""
+    from oracle import transport as T
+    rho, ux, uy = 0.8, -1.5, 0.6
+    for P, want in ((-0.05, None), (0.0, None), (0.3, np.sqrt(GAMMA_TEST * 0.3 / rho))):
+        E = P / (GAMMA_TEST - 1.0) + 0.5 * rho * (ux * ux + uy * uy)
+        U = np.array([rho, rho * ux, rho * uy, E])
+        for d, un in ((0, ux), (1, uy)):
+            F, a = T.euler_flux(U, d)
+            assert np.isfinite(a) and a == pytest.approx(abs(un) + (want or 0.0), rel=1e-14)
+            assert np.allclose(F, _textbook_flux(U, d), rtol=1e-12, atol=1e-14)
