@@ -79,7 +79,10 @@ def run_parity(wl, steps, prec="fp64", check_f=True, **over):
             eta = P.eta_factor * st.eps
             assert np.all(np.abs(lam_g - lam_o) <= tol_ind * np.maximum(np.abs(lam_o), eta)), "lambda_A"
             dl1 = np.abs(l1_g - l1_o)[st.kin]
-            assert np.all(dl1 <= tol_ind * np.maximum(l1_o[st.kin], P.delta)), "L1"
+            # FP64: f itself agrees to 1e-10 relative L1 (the field bar), so
+            # the L1 norm of f - M may move by 1e-10 of the cell's density
+            slack = 1e-10 * np.abs(st.U[0][st.kin]) if prec == "fp64" else 0.0
+            assert np.all(dl1 <= tol_ind * np.maximum(l1_o[st.kin], P.delta) + slack), "L1"
             bad = flags_g != new_o
             near = (np.abs(lam_o - eta) <= 1e-6 * np.maximum(eta, 1e-300)) | \
                    (st.kin & (np.abs(l1_o - P.delta) <= 1e-6 * P.delta))
