@@ -527,6 +527,7 @@ def batch_arm(args):
     dts = np.array([c["dt"] for c in cases])
     tab = G.make_tableau("ars233")
     threads, ctas = b.autotune(dts, tab)
+    sched = b.schedule()
     for _ in range(args.warmup):
         b.step(dts, tab)
     b.sync()
@@ -608,7 +609,8 @@ def batch_arm(args):
            "cases": len(cases), "cells": ncells, "elements": elems, "prec": args.prec,
            "l2": "flushed (256 MB write) before every timed step; f arrays far exceed L2",
            "parallelism": "replicas" if world > 1 else "single GPU",
-           "autotuned": {"threads": threads, "ctas_per_sm": ctas}, "cuda_graph": True,
+           "autotuned": {"threads": threads, "ctas_per_sm": ctas,
+                                     "per_cell_form_by_nv": {str(k): v for k, v in sched["forms"].items()}}, "cuda_graph": True,
            "kinetic_fraction_end": c1["kinetic_cells"] / ncells}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -665,10 +667,14 @@ def learned_arm(args):
     X, Y = torch.cat([X, Xf]), torch.cat([Y, Yf])
     del Xf, Yf
     t_collect = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    theta, hist = T.train(X, Y, T.init_params(0), epochs=30, batch=32, lr=3e-3, device=dev)
-    torch.cuda.synchronize(dev)
-    t_train = time.perf_counter() - t0
+    # one network per initialisation seed, same data; seed 0's is timed below
+    nets = []
+    for seed in range(args.init_seeds):
+        t0 = time.perf_counter()
+        th, hi = T.train(X, Y, T.init_params(seed), epochs=30, batch=32, lr=3e-3, device=dev)
+        torch.cuda.synchronize(dev)
+        nets.append((th, hi, time.perf_counter() - t0))
+    theta, hist, t_train = nets[0]
     del X, Y
 
     wl = W.learned_switch_case(seed=rank)
@@ -677,11 +683,11 @@ def learned_arm(args):
     tab = G.make_tableau(wl["scheme"])
     nvv = wl["vmesh"]["nv"] ** 2
 
-    def make(switch, prec, kin=None):
+    def make(switch, prec, kin=None, params=None):
         s = G.Solver(wl["grid"], wl["vmesh"], dict(wl["params"], switch=switch), prec=prec, device=dev)
         s.set_state(f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"] if kin is None else kin)
         if switch == "learned":
-            s.set_switch_params(theta)
+            s.set_switch_params(theta if params is None else params)
         return s
 
     def run(s, n):
@@ -727,6 +733,22 @@ def learned_arm(args):
             learned = s
         else:
             s.close()
+    # the networks of the other initialisation seeds, against plain FP32 (same precision)
+    p32 = res["plain_fp32"]
+    seeds = []
+    for seed, (th, hi, tt) in enumerate(nets):
+        if seed == 0:
+            r = res["learned_fp32"]
+        else:
+            s = make("learned", "fp32", params=th)
+            ms, upd = run(s, nsim)
+            r = {"ms_per_sim_time": ms / (nsim * dt), "error_vs_all_kinetic": err(s.cons()),
+                 "kinetic_cell_steps": upd // nvv // 3}
+            s.close()
+        seeds.append({"init_seed": seed, "final_loss": hi[-1], "train_s": tt,
+                      "wall_per_sim_time_vs_plain_fp32": r["ms_per_sim_time"] / p32["ms_per_sim_time"],
+                      "error_vs_plain_fp32": r["error_vs_all_kinetic"] / p32["error_vs_all_kinetic"],
+                      "kinetic_work_vs_plain_fp32": r["kinetic_cell_steps"] / max(p32["kinetic_cell_steps"], 1)})
 
     # timed region of the line: K steps of the learned FP32 form, L2 flushed between steps
     for _ in range(args.warmup):
@@ -762,6 +784,10 @@ def learned_arm(args):
            "comparison": res,
            "learned_fp32_vs_plain_fp64": {"wall_per_sim_time_ratio": l32["ms_per_sim_time"] / p64["ms_per_sim_time"],
                                           "error_ratio": l32["error_vs_all_kinetic"] / p64["error_vs_all_kinetic"]},
+           "learned_fp32_vs_plain_fp32_by_init_seed": seeds,
+           "learned_fp32_vs_plain_fp32_spread": {
+               k: [min(x[k] for x in seeds), max(x[k] for x in seeds)]
+               for k in ("wall_per_sim_time_vs_plain_fp32", "error_vs_plain_fp32", "kinetic_work_vs_plain_fp32")},
            "clocks": clk.summary(), "gpu_launches": int(round(launches_per_step * args.steps))}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline("learned", args.cpu_steps)
@@ -863,6 +889,7 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=48)
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--sim-steps", type=int, default=100, help="steps of the learned-switch comparison runs")
+    ap.add_argument("--init-seeds", type=int, default=3, help="networks trained from these many initialisations")
     ap.add_argument("--cases", type=int, default=64, help="cases of the batched workload")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-steps", type=int, default=8)

@@ -331,6 +331,11 @@ int esbgk_relax_cells(const void* fstar, const double* h, int32_t n, int32_t nv,
  * launches of a step are captured once into a CUDA graph and replayed.
  * All cases share the storage precision.  Cases are addressed by index
  * 0..n-1; per-case host arrays follow the single-problem conventions.
+ * Cases with the learned switch take the criterion in the batched launches
+ * and their network (features, forward pass, judge) in per-case launches of
+ * the same step (captured in the step's graph); each needs its parameters
+ * (esbgk_batch_set_switch_params) before the first step, else the step
+ * fails with ESBGK_E_STATE.
  * Errors: ESBGK_E_ARG (bad argument, mixed precisions, case index out of
  * range), ESBGK_E_WORKSPACE (workspace too small or not 256-byte aligned),
  * ESBGK_E_CUDA, ESBGK_E_NONREALIZABLE (reported by esbgk_batch_sync for the
@@ -354,6 +359,12 @@ int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vm
  * stays the caller's, and work already queued on the stream still uses it
  * (synchronise first, e.g. esbgk_batch_sync).  NULL is ignored. */
 void esbgk_batch_destroy(esbgk_batch* b);
+
+/* esbgk_set_switch_params and esbgk_switch_stats for case i (a learned-switch
+ * case; ESBGK_E_STATE for another switch). */
+int esbgk_batch_set_switch_params(esbgk_batch* b, int32_t i, const float* theta);
+int esbgk_batch_switch_stats(esbgk_batch* b, int32_t i, long long* judged_cells, long long* predicted,
+                             long long* missed, long long* extra);
 
 /* esbgk_set_state for case i. */
 int esbgk_batch_set_state(esbgk_batch* b, int32_t i, const double* rho, const double* ux,
@@ -379,14 +390,36 @@ int esbgk_batch_get_flags(esbgk_batch* b, int32_t i, uint8_t* kinetic);
 int esbgk_batch_counters(esbgk_batch* b, long long* kinetic_cell_updates, long long* element_updates,
                          long long* steps, long long* kinetic_cells);
 
-/* Autotuner of the batched stage launch.  For each candidate launch shape
- * (32, 64 or 128 threads per CTA, within the shared-memory limit, x 0, 2, 4
- * or 8 CTAs per SM, 0 meaning as many as fit) it runs one untimed and two
- * timed steps (dt, tab) on the current state -- so it advances the batch by
- * three steps per candidate -- and keeps the fastest shape for later steps.
- * Reports the choice (either pointer may be NULL). */
+/* Autotuner of the batched stage launch (it advances the batch: three steps
+ * (dt, tab) per candidate schedule, one untimed and two timed, on the
+ * current state).  First the launch shape: 32, 64 or 128 threads per CTA
+ * (within the shared-memory limit) x 0, 2, 4 or 8 CTAs per SM (0: as many as
+ * fit).  Then, one velocity grid at a time with the others held, the
+ * per-cell form of its cases: the library's default form for that N_v
+ * (esbgk_kinetic_form), the same with one cell per warp where the default
+ * puts two, or the scalar form; a form replaces the current one only if it is
+ * at least 2 % faster.  The chosen forms are kept for the process per (N_v,
+ * storage precision), and the launch shape per (storage precision, set of
+ * N_v): batches created later start from them.  Reports the launch shape
+ * (either pointer may be NULL); esbgk_batch_schedule reports the forms. */
 int esbgk_batch_autotune(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, int32_t* threads,
                          int32_t* ctas_per_sm);
+
+/* The batch's current schedule: the launch shape (threads per CTA, CTAs per
+ * SM; NULL to skip) and, for each distinct N_v of its cases in ascending
+ * order, the per-cell form: 0 the default form, 1 one cell per warp, 2 the
+ * scalar form.  Writes min(cap, count) entries to nv[] and form[] (caller's
+ * host arrays; NULL allowed when cap = 0) and the number of distinct N_v to
+ * *count (NULL to skip).  Host only, no device work; ESBGK_E_ARG for a null
+ * batch or cap < 0. */
+int esbgk_batch_schedule(const esbgk_batch* b, int32_t* threads, int32_t* ctas_per_sm, int32_t* nv, int32_t* form,
+                         int32_t cap, int32_t* count);
+
+/* Set the per-cell form (0, 1 or 2 as in esbgk_batch_schedule) of the cases
+ * whose velocity grid has nv nodes per direction, for the following steps;
+ * results agree with every form to rounding.  Host only; ESBGK_E_ARG for a
+ * null batch, nv outside 0..64 or an unknown form. */
+int esbgk_batch_set_form(esbgk_batch* b, int32_t nv, int32_t form);
 
 /* Wait for the stream; report a pending device error of any case. */
 int esbgk_batch_sync(esbgk_batch* b);

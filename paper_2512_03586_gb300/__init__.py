@@ -466,13 +466,48 @@ class BatchSolver:
         self._check(self._abi.esbgk_batch_step(self._b, _dptr(d), ctypes.byref(t), int(bool(graph))), "step")
 
     def autotune(self, dt, tableau="ars233"):
-        """Pick the stage launch shape (advances the batch); returns (threads, ctas_per_sm)."""
+        """Pick the stage launch shape, then each velocity grid's per-cell
+        form (advances the batch); returns (threads, ctas_per_sm).  The full
+        schedule: schedule()."""
         t = tableau if isinstance(tableau, self._abi.Tableau) else make_tableau(tableau)
         d = self._dt(dt)
         th, ct = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._abi.esbgk_batch_autotune(self._b, _dptr(d), ctypes.byref(t), ctypes.byref(th),
                                                    ctypes.byref(ct)), "autotune")
         return th.value, ct.value
+
+    FORMS = ("default", "one_cell_per_warp", "scalar")
+
+    def schedule(self):
+        """The current schedule: {'threads', 'ctas_per_sm', 'forms': {N_v: form name}}."""
+        th, ct, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._abi.esbgk_batch_schedule(self._b, ctypes.byref(th), ctypes.byref(ct), None, None, 0,
+                                                   ctypes.byref(n)), "schedule")
+        nv = (ctypes.c_int32 * max(n.value, 1))()
+        fm = (ctypes.c_int32 * max(n.value, 1))()
+        self._check(self._abi.esbgk_batch_schedule(self._b, None, None, nv, fm, n.value, None), "schedule")
+        return {"threads": th.value, "ctas_per_sm": ct.value,
+                "forms": {int(nv[i]): self.FORMS[fm[i]] for i in range(n.value)}}
+
+    def set_switch_params(self, i, theta):
+        """Network parameters (CNN_PARAMS float32) of learned-switch case i."""
+        th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(-1))
+        assert th.size == CNN_PARAMS
+        self._check(self._abi.esbgk_batch_set_switch_params(self._b, int(i),
+                                                            th.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                    "set_switch_params")
+
+    def switch_stats(self, i):
+        j, p, m, e = (ctypes.c_longlong() for _ in range(4))
+        self._check(self._abi.esbgk_batch_switch_stats(self._b, int(i), ctypes.byref(j), ctypes.byref(p),
+                                                       ctypes.byref(m), ctypes.byref(e)), "switch_stats")
+        return dict(judged=j.value, predicted=p.value, missed=m.value, extra=e.value)
+
+    def set_form(self, nv, form):
+        """Per-cell form of the cases with nv velocity nodes per direction
+        ('default', 'one_cell_per_warp', 'scalar' or 0..2)."""
+        f = self.FORMS.index(form) if isinstance(form, str) else int(form)
+        self._check(self._abi.esbgk_batch_set_form(self._b, int(nv), f), "set_form")
 
     def moments(self, i, out=None):
         nx, ny, _ = self.shapes[i]

@@ -115,6 +115,12 @@ _SIGS = {
     "esbgk_batch_counters": (I, [P, LL, LL, LL, LL]),
     "esbgk_batch_autotune": (I, [P, D, ctypes.POINTER(Tableau), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_batch_schedule": (I, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                 ctypes.POINTER(ctypes.c_int32)]),
+    "esbgk_batch_set_form": (I, [P, ctypes.c_int32, ctypes.c_int32]),
+    "esbgk_batch_set_switch_params": (I, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    "esbgk_batch_switch_stats": (I, [P, ctypes.c_int32, LL, LL, LL, LL]),
     "esbgk_batch_sync": (I, [P]),
     "esbgk_batch_timing": (I, [P, ctypes.c_int32]),
     "esbgk_batch_timing_read": (I, [P, D, LL, ctypes.c_int32]),

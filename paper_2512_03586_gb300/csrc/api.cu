@@ -4,7 +4,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -1286,8 +1288,26 @@ struct BatchTabSet {
   }
 };
 
+// Per-cell form of a velocity grid in the batched stage launches (autotuned):
+// the library's default form, the same with one cell per warp instead of two,
+// or the scalar form.
+enum : int { kFormDefault = 0, kFormOneCell = 1, kFormScalar = 2, kNumForms = 3 };
+inline int apply_form(int var, int form) {
+  if (form == kFormScalar) return kVarScalar;
+  if (form == kFormOneCell && variant_pairs(var)) return var - 1;  // the same form, one cell per warp
+  return var;
+}
+
+// Schedules the autotuner chose, kept for the process: the form per (N_v,
+// storage precision), and the launch shape per (storage precision, set of
+// N_v of the batch).  A new batch starts from them.
+static std::mutex g_sched_mu;
+static std::map<std::pair<int, int>, int> g_form_of;
+static std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> g_shape_of;
+
 struct esbgk_batch {
   int n = 0, prec = 0;
+  signed char form[65] = {0};  // per N_v: kForm*
   const Launchers* L = nullptr;
   cudaStream_t stream = nullptr;
   int nsm = 0, total_cells = 0, max_threads = 128;
@@ -1305,6 +1325,14 @@ struct esbgk_batch {
   int status = ESBGK_OK;
   std::string msg;
 
+  // the distinct N_v of the cases, ascending
+  std::vector<int> nv_set() const {
+    std::vector<int> v;
+    for (auto* X : cs)
+      if (std::find(v.begin(), v.end(), X->g.nv) == v.end()) v.push_back(X->g.nv);
+    std::sort(v.begin(), v.end());
+    return v;
+  }
   ~esbgk_batch() {
     for (auto& t : sets) t.drop_graph();
     for (auto* c : cs) delete c;
@@ -1341,9 +1369,7 @@ bool batch_layout(int n, const esbgk_grid* grids, const esbgk_vmesh* vmeshes, co
   long long cells = 0;
   B.case_off.resize(n);
   for (int i = 0; i < n; ++i) {
-    if (!valid_inputs(&grids[i], &vmeshes[i], &params[i]) || params[i].prec != params[0].prec ||
-        params[i].sw == ESBGK_SWITCH_LEARNED)
-      return false;
+    if (!valid_inputs(&grids[i], &vmeshes[i], &params[i]) || params[i].prec != params[0].prec) return false;
     B.case_off[i] = p;
     p += up(esbgk_workspace_bytes(&grids[i], &vmeshes[i], &params[i]));
     cells += (long long)grids[i].nx * grids[i].ny;
@@ -1421,8 +1447,21 @@ void batch_launches(esbgk_batch* b, const BatchTabSet& t, const int* grids) {
       launch_batch_l1_offsets(T, b->stream);
       b->L->batch_l1(t.reg, b->d_off_l1, b->n, b->max_nvv, grid_small, b->stream);
     }
-    Timed tm(X0, ESBGK_K_FLAGS);
-    launch_batch_flags(T, b->stream);
+    {
+      Timed tm(X0, ESBGK_K_FLAGS);
+      launch_batch_flags(T, b->stream);
+    }
+    // learned-switch cases: the network's prediction joins the criterion's
+    // map and the previous prediction is judged, as in a single context
+    Timed tm(X0, ESBGK_K_OTHER);
+    for (int i = 0; i < b->n; ++i) {
+      if (!t.h_reg[i].learned) continue;
+      esbgk_ctx* X = b->cs[i];
+      const double d = X->g.dx < X->g.dy ? X->g.dx : X->g.dy;
+      cnn::launch_features(X->Un, X->eps, X->g.nc, d, X->cx, b->stream);
+      cnn::launch_forward(X->cw, X->cx, 1, X->g.ny, X->g.nx, X->ca1, X->ca2, X->logits, &X->err->code, b->stream);
+      cnn::launch_judge(X->flags, X->pred, X->logits, X->g.nc, t.h_reg[i].learned == 2 ? 1 : 0, X->sctr, b->stream);
+    }
   }
   {
     Timed tm(X0, ESBGK_K_COMPACT);
@@ -1454,9 +1493,12 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
   bool any_plain = false;
   for (int i = 0; i < n; ++i) {
     esbgk_ctx* X = b->cs[i];
-    // the batched regime update runs before the stages of every plain case
-    if (X->sw == ESBGK_SWITCH_PLAIN) X->conv_pending = true;
-    any_plain = any_plain || X->sw == ESBGK_SWITCH_PLAIN;
+    // the batched regime update runs before the stages of every case with
+    // the criterion (plain or learned switch)
+    if (X->sw == ESBGK_SWITCH_LEARNED && !X->have_weights)
+      return bfail(b, ESBGK_E_STATE, "batch step: a learned-switch case has no network parameters");
+    if (X->criterion()) X->conv_pending = true;
+    any_plain = any_plain || X->criterion();
     const int r = plan_step(X, dt[i], tab, plans[i]);
     if (r) return bfail(b, r, X->msg);
   }
@@ -1477,7 +1519,7 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
       memset(&c, 0, sizeof c);
       c.V = V;
       c.A = plans[i].st[j];
-      const int v = b->L->variant(c.A, X->g);
+      const int v = apply_form(b->L->variant(c.A, X->g), b->form[X->g.nv]);
       var = var < 0 || var == v ? v : kVarScalar;
       if (stage_mode(c.A) != modes[j]) return bfail(b, ESBGK_E_STATE, "batched cases disagree on a launch shape");
     }
@@ -1491,6 +1533,7 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
     rg[i].prep_copy = plans[i].prep.copy_to != nullptr;
     rg[i].conv = plans[i].prep.list2 != nullptr;
     rg[i].variant = st[i].variant;
+    rg[i].learned = X->sw == ESBGK_SWITCH_LEARNED ? (X->have_pred ? 2 : 1) : 0;
   }
   // find the table set with these descriptors, else overwrite the least recently used
   BatchTabSet* t = nullptr;
@@ -1557,7 +1600,10 @@ int batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab, bool 
     batch_launches(b, *t, grids);
     if ((r = bcheck(b, cudaGetLastError(), "batched step launch"))) return r;
   }
-  for (int i = 0; i < n; ++i) finish_step(b->cs[i], plans[i]);
+  for (int i = 0; i < n; ++i) {
+    finish_step(b->cs[i], plans[i]);
+    if (b->cs[i]->sw == ESBGK_SWITCH_LEARNED) b->cs[i]->have_pred = true;
+  }
   b->steps += 1;
   return ESBGK_OK;
 }
@@ -1602,6 +1648,14 @@ int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vm
     if (per_warp > b->max_nvv) b->max_nvv = per_warp;
   }
   b->total_cells = cell_off[n];
+  {
+    // schedules chosen for these velocity grids earlier in the process
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    for (auto* X : b->cs) {
+      const auto it = g_form_of.find({X->g.nv, b->prec});
+      if (it != g_form_of.end()) b->form[X->g.nv] = (signed char)it->second;
+    }
+  }
   for (int t = 0; t < kTabSets; ++t) {
     b->sets[t].reg = (CaseRegime*)(w + B.reg[t]);
     b->sets[t].stage = (CaseStage*)(w + B.stage[t]);
@@ -1623,6 +1677,12 @@ int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vm
     int w = 4;
     while (w > 1 && per_warp * w + kBatchStaticSmem > (size_t)optin) w >>= 1;
     b->max_threads = b->threads = 32 * w;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    const auto it = g_shape_of.find({b->prec, b->nv_set()});
+    if (it != g_shape_of.end() && it->second.first <= b->max_threads) {
+      b->threads = it->second.first;
+      b->ctas = it->second.second;
+    }
   }
   if (!r)
     r = bcheck(b, cudaMemcpyAsync(b->d_cell_off, cell_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
@@ -1659,6 +1719,19 @@ int esbgk_batch_step(esbgk_batch* b, const double* dt, const esbgk_tableau* tab,
     if (b->cs[i]->status) return b->cs[i]->status;
   }
   return batch_step(b, dt, tab, use_graph != 0);
+}
+
+int esbgk_batch_set_switch_params(esbgk_batch* b, int32_t i, const float* theta) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  const int r = esbgk_set_switch_params(b->cs[i], theta);
+  b->drop_graphs();  // the case's judge state restarts
+  return r;
+}
+
+int esbgk_batch_switch_stats(esbgk_batch* b, int32_t i, long long* judged_cells, long long* predicted,
+                             long long* missed, long long* extra) {
+  if (!b || i < 0 || i >= b->n) return ESBGK_E_ARG;
+  return esbgk_switch_stats(b->cs[i], judged_cells, predicted, missed, extra);
 }
 
 int esbgk_batch_get_moments(esbgk_batch* b, int32_t i, double* rho, double* ux, double* uy, double* T) {
@@ -1699,42 +1772,92 @@ int esbgk_batch_autotune(esbgk_batch* b, const double* dt, const esbgk_tableau* 
                          int32_t* ctas_per_sm) {
   if (!b || !dt) return ESBGK_E_ARG;
   if (b->status) return b->status;
-  // candidates: warps per CTA x CTAs per SM (0 = as many as fit); each is
-  // timed over two steps after one untimed step
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int r = bcheck(b, cudaEventCreate(&e0), "autotune event");
+  if (!r) r = bcheck(b, cudaEventCreate(&e1), "autotune event");
+  // one untimed and two timed steps of the current schedule (ms; < 0: error)
+  auto time_steps = [&]() -> float {
+    b->drop_graphs();
+    if ((r = esbgk_batch_step(b, dt, tab, 0))) return -1.f;
+    if ((r = bcheck(b, cudaEventRecord(e0, b->stream), "autotune record"))) return -1.f;
+    for (int k = 0; k < 2 && !r; ++k) r = esbgk_batch_step(b, dt, tab, 0);
+    if (r || (r = bcheck(b, cudaEventRecord(e1, b->stream), "autotune record"))) return -1.f;
+    if ((r = bcheck(b, cudaEventSynchronize(e1), "autotune sync"))) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  // 1. launch shape: warps per CTA x CTAs per SM (0 = as many as fit)
   const int cand_threads[3] = {32, 64, 128};
   const int cand_ctas[4] = {0, 2, 4, 8};
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int r = bcheck(b, cudaEventCreate(&e0), "autotune event");
-  if (!r) r = bcheck(b, cudaEventCreate(&e1), "autotune event");
   for (int t : cand_threads) {
     for (int c : cand_ctas) {
       if (r || t > b->max_threads) break;
       b->threads = t;
       b->ctas = c;
-      if ((r = esbgk_batch_step(b, dt, tab, 0))) break;
-      if ((r = bcheck(b, cudaEventRecord(e0, b->stream), "autotune record"))) break;
-      for (int k = 0; k < 2 && !r; ++k) r = esbgk_batch_step(b, dt, tab, 0);
-      if (r || (r = bcheck(b, cudaEventRecord(e1, b->stream), "autotune record"))) break;
-      if ((r = bcheck(b, cudaEventSynchronize(e1), "autotune sync"))) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
+      const float ms = time_steps();
+      if (ms >= 0.f && ms < best) {
         best = ms;
         bt = t;
         bc = c;
       }
     }
   }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
   b->threads = bt;
   b->ctas = bc;
+  // 2. per velocity grid, the per-cell form (coordinate search, one grid at a
+  // time, the others held): a change must gain 2 % to be taken over timing noise
+  const std::vector<int> nvs = b->nv_set();
+  for (int nv : nvs) {
+    if (r) break;
+    const int keep = b->form[nv];
+    int bf = keep;
+    float bms = time_steps();
+    for (int f = 0; f < kNumForms && !r; ++f) {
+      if (f == keep || (f == kFormOneCell && nv * nv > kPairMaxNodes)) continue;  // no two-cell form to undo
+      b->form[nv] = (signed char)f;
+      const float ms = time_steps();
+      if (ms >= 0.f && ms < 0.98f * bms) {
+        bms = ms;
+        bf = f;
+      }
+    }
+    b->form[nv] = (signed char)bf;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   b->drop_graphs();
-  if (threads) *threads = bt;
-  if (ctas_per_sm) *ctas_per_sm = bc;
+  if (!r) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    for (int nv : nvs) g_form_of[{nv, b->prec}] = b->form[nv];
+    g_shape_of[{b->prec, nvs}] = {b->threads, b->ctas};
+  }
+  if (threads) *threads = b->threads;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas;
   return r;
+}
+
+int esbgk_batch_set_form(esbgk_batch* b, int32_t nv, int32_t form) {
+  if (!b || nv < 0 || nv > 64 || form < 0 || form >= kNumForms) return ESBGK_E_ARG;
+  b->form[nv] = (signed char)form;
+  b->drop_graphs();
+  return ESBGK_OK;
+}
+
+int esbgk_batch_schedule(const esbgk_batch* b, int32_t* threads, int32_t* ctas_per_sm, int32_t* nv, int32_t* form,
+                         int32_t cap, int32_t* count) {
+  if (!b || cap < 0 || (cap > 0 && (!nv || !form))) return ESBGK_E_ARG;
+  if (threads) *threads = b->threads;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas;
+  const std::vector<int> nvs = b->nv_set();
+  if (count) *count = (int32_t)nvs.size();
+  for (int i = 0; i < (int)nvs.size() && i < cap; ++i) {
+    nv[i] = nvs[i];
+    form[i] = b->form[nvs[i]];
+  }
+  return ESBGK_OK;
 }
 
 int esbgk_batch_sync(esbgk_batch* b) {

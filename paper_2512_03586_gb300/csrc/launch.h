@@ -182,7 +182,7 @@ struct CaseRegime {
   int prep_copy;          // the start-of-step launch copies U^n and flags (units of 32 cells)
   int conv;               // the start-of-step launch fills converted cells
   int variant;            // StageVariant of the case's stage launches
-  int pad;
+  int learned;            // learned switch: 1, 2 when the previous prediction is judged; else 0
 };
 
 // Device tables of a batch.

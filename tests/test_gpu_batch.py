@@ -139,6 +139,10 @@ def test_batch_autotune_keeps_results():
         dts = np.array([c["dt"] for c in cases])
         threads, ctas = b.autotune(dts)
         assert threads in (32, 64, 128) and ctas in (0, 2, 4, 8)
+        sch = b.schedule()
+        assert (sch["threads"], sch["ctas_per_sm"]) == (threads, ctas)
+        assert sorted(sch["forms"]) == [16, 20, 24]
+        assert set(sch["forms"].values()) <= set(b.FORMS)
         n_tuned = b.counters()["steps"]
         assert n_tuned > 0
         b.step(dts)
@@ -146,7 +150,35 @@ def test_batch_autotune_keeps_results():
         for s, c in zip(singles, cases):
             for _ in range(n_tuned + 1):
                 s.step(c["dt"], "ars233")
+        # whatever forms were chosen, the results are the single runs'
         _compare(b, singles, "fp32")
+        # a later batch of the same velocity grids starts from the chosen schedule
+        b2 = _batch(cases, "fp32", stream=stream)
+        assert b2.schedule() == sch
+
+
+@pytest.mark.parametrize("form", ["default", "one_cell_per_warp", "scalar"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_every_per_cell_form_keeps_results(form, prec):
+    """Each per-cell form the autotuner may choose gives the single-problem
+    results (N_v = 12: two cells per warp by default; N_v = 26 and 18: the
+    straddling forms)."""
+    import torch
+    cases = W.batched_cases(n_cases=3, seed0=40, sizes=[16, 24], nvs=[12, 18, 26])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, prec, stream=stream)
+        for nv in sorted({c["vmesh"]["nv"] for c in cases}):
+            b.set_form(nv, form)
+        assert set(b.schedule()["forms"].values()) == {form}
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(3):
+            b.step(dts)
+        singles = [_single(c, prec) for c in cases]
+        for s, c in zip(singles, cases):
+            for _ in range(3):
+                s.step(c["dt"], "ars233")
+        _compare(b, singles, prec)
 
 
 def test_batch_matches_oracle_small():
@@ -186,3 +218,49 @@ def test_batch_rejects_bad_input():
     out = np.empty(4 * 16)
     assert b._abi.esbgk_batch_get_cons(b._b, 5, out.ctypes.data_as(b._abi.D)) == b._abi.E_ARG
     assert b._abi.esbgk_batch_get_cons(b._b, -1, out.ctypes.data_as(b._abi.D)) == b._abi.E_ARG
+
+
+def test_batch_learned_switch_equals_single_contexts():
+    """Learned-switch cases in a batch (with a plain-switch case beside them):
+    the criterion runs batched, each network in its own launches of the same
+    step; flags, judge statistics and fields equal the single contexts' runs
+    with the same network (FP64 storage: fields to 1e-12)."""
+    import torch
+    from paper_2512_03586_gb300 import switch_train as T
+    theta = T.init_params(5)
+    theta[-1] = -0.5  # head bias: part of the cells predicted kinetic
+    cases = [W.riemann_quadrants(nx=24, ny=20, nv=16, seed=3), W.riemann_quadrants(nx=32, ny=16, nv=12, seed=4),
+             W.riemann_quadrants(nx=20, ny=20, nv=16, seed=5)]
+    for c in cases[:2]:
+        c["params"] = dict(c["params"], switch="learned")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, "fp64", stream=stream)
+        for i in range(2):
+            b.set_switch_params(i, theta)
+        singles = [_single(c, "fp64") for c in cases]
+        for s in singles[:2]:
+            s.set_switch_params(theta)
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(5):
+            b.step(dts)
+            for s, c in zip(singles, cases):
+                s.step(c["dt"], "ars233")
+            for i, s in enumerate(singles):
+                np.testing.assert_array_equal(b.flags(i), s.flags())
+        _compare(b, singles, "fp64")
+        for i in range(2):
+            assert b.switch_stats(i) == singles[i].switch_stats()
+        assert b.switch_stats(0)["predicted"] > 0
+
+
+def test_batch_learned_case_without_parameters_is_refused():
+    import torch
+    import paper_2512_03586_gb300 as G
+    c = W.riemann_quadrants(nx=8, ny=8, nv=8, seed=1)
+    c["params"] = dict(c["params"], switch="learned")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch([c], "fp64", stream=stream)
+        with pytest.raises(G.Error):
+            b.step(np.array([c["dt"]]))

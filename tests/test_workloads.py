@@ -73,3 +73,21 @@ def test_blob_sine_and_learned_recipes():
     iy, ix = np.unravel_index(np.argmax(ratio), ratio.shape)
     assert abs((ix + 0.5) / 64 - 0.3) < 0.02 and abs((iy + 0.5) / 64 - 0.7) < 0.02
     assert lw["params"]["switch"] == "learned"
+
+
+def test_tests_3_and_4_recipes_match_the_paper_setup():
+    """Sizes, time steps, boundary conditions and thresholds of Tests 3-4 as
+    printed in Sec. 4.2.1-4.2.2, and the initial states' jumps."""
+    kh, sb = W.kelvin_helmholtz(), W.shock_bubble()
+    assert (kh["grid"]["nx"], kh["grid"]["ny"], sb["grid"]["nx"], sb["grid"]["ny"]) == (150, 75, 150, 50)
+    assert (kh["grid"]["bc_x"], kh["grid"]["bc_y"]) == ("periodic", "outflow")
+    assert kh["steps"] == 4080 and sb["steps"] == 1200
+    assert abs(kh["dt"] - 0.5 / 150 / 8) < 1e-15 and abs(sb["dt"] - 0.5 / 50 / 8) < 1e-15
+    assert kh["params"]["eta_factor"] == 4.0 and sb["params"]["eta_factor"] == 0.5
+    f = kh["fields"]
+    assert set(np.unique(f["rho"])) == {1.0, 2.0} and np.allclose(f["rho"] * f["T"], 1.0)
+    assert np.abs(f["uy"]).max() <= 0.01 and kh["fields"]["kin"].all()
+    g = sb["fields"]
+    left = g["ux"] > 0
+    assert np.allclose(g["rho"][left], 16 / 7) and np.allclose((g["rho"] * g["T"])[left], 4.75)
+    assert 2.4 < g["rho"].max() < 2.5  # the bubble's peak 1 + 1.5 exp(-16 d^2) near its centre

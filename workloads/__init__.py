@@ -238,3 +238,50 @@ def obstacle_flow(kind="cylinder", n=78, nv=32, vmax=8.0, eps=1e-6, eta_factor=1
         fields=dict(rho=rho, ux=np.full_like(rho, 2.0), uy=np.zeros_like(rho), T=np.ones_like(rho),
                     eps=np.full_like(rho, eps), kin=kin),
         solid=solid)
+
+
+def kelvin_helmholtz(nx=150, ny=75, nv=32, vmax=8.0, eps=1e-6, t_end=1.7, cfl=0.5, steps=None,
+                     initial="kinetic", switch="plain"):
+    """Test 3 (Sec. 4.2.1): shear layer on [0, 1] x [0, 0.5] (periodic in x,
+    outflow in y), (rho, u_x, p) = (2, -0.5, 1) for y <= 1/4 and (1, 0.5, 1)
+    above, u_y = 0.01 sin(4 pi x), T = p / rho; eps = 1e-6, plain switch with
+    eta = 4 eps, delta = 1e-3; every cell starts kinetic with f the Maxwellian
+    of its state ('fluid': all macroscopic).  dt = 0.5 min(dx, dy) / 8 to
+    t_end = 1.7 (steps: fewer, for a shortened run)."""
+    X, Y = _centres(nx, ny, 0, 1, 0, 0.5)
+    low = Y <= 0.25
+    rho = np.where(low, 2.0, 1.0)
+    ux = np.where(low, -0.5, 0.5)
+    uy = 0.01 * np.sin(4 * np.pi * X)
+    dt = _dt(cfl, nx, ny, 0, 1, 0, 0.5, vmax)
+    n = int(np.ceil(t_end / dt - 1e-9)) if steps is None else steps
+    kin = np.full(X.shape, initial == "kinetic")
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=0.5, bc_x="periodic", bc_y="outflow"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS, switch=switch, eta_factor=4.0), scheme="ars233",
+        dt=dt, steps=n,
+        fields=dict(rho=rho, ux=ux, uy=uy, T=1.0 / rho, eps=np.full_like(rho, eps), kin=kin))
+
+
+def shock_bubble(nx=150, ny=50, nv=32, vmax=8.0, eps=1e-6, t_end=1.5, cfl=0.5, steps=None,
+                 initial="kinetic", switch="plain"):
+    """Test 4 (Sec. 4.2.2): on [-2, 3] x [-0.5, 0.5] (outflow edges) a shock
+    state (rho, u_x, p) = (16/7, sqrt(5/3) 7/16, 4.75) for x <= -1 runs into
+    (1 + 1.5 exp(-16 d^2), 0, 1), d the distance to (0.5, 0); u_y = 0,
+    T = p / rho; eps = 1e-6, plain switch with eta = eps/2, delta = 1e-3;
+    every cell starts kinetic with f the Maxwellian of its state.
+    dt = 0.5 min(dx, dy) / 8 to t_end = 1.5."""
+    X, Y = _centres(nx, ny, -2, 3, -0.5, 0.5)
+    left = X <= -1.0
+    d2 = (X - 0.5) ** 2 + Y ** 2
+    rho = np.where(left, 16.0 / 7.0, 1.0 + 1.5 * np.exp(-16.0 * d2))
+    ux = np.where(left, np.sqrt(5.0 / 3.0) * 7.0 / 16.0, 0.0)
+    p = np.where(left, 4.75, 1.0)
+    dt = _dt(cfl, nx, ny, -2, 3, -0.5, 0.5, vmax)
+    n = int(np.ceil(t_end / dt - 1e-9)) if steps is None else steps
+    kin = np.full(X.shape, initial == "kinetic")
+    return dict(
+        grid=dict(nx=nx, ny=ny, x0=-2.0, x1=3.0, y0=-0.5, y1=0.5, bc_x="outflow", bc_y="outflow"),
+        vmesh=dict(nv=nv, vmax=vmax), params=dict(PARAMS, switch=switch, eta_factor=0.5), scheme="ars233",
+        dt=dt, steps=n,
+        fields=dict(rho=rho, ux=ux, uy=np.zeros_like(rho), T=p / rho, eps=np.full_like(rho, eps), kin=kin))
