@@ -244,6 +244,40 @@ ESBGK_DEV float2 cweno_face2(float2 a, float2 b, float2 c, float2 epsw) {
   return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
 }
 
+// F(b, c, d) - F(a, b, c) for two node pairs: the difference of the upwind
+// CWENO3 face values at the two faces of the middle cells b | c, each face
+// from the cell behind it and its two neighbours (the same weights as
+// cweno_face2).  The three differences d1 = b - a, d2 = c - b, d3 = d - c and
+// their squares t = d^2 + eps, s = t^2 serve both faces: with dl, dr the
+// differences behind and ahead of a face's upwind cell,
+//   F = u + 1/2 [s_l s_r (dl + 5 dr)/6 + (z/2)(s_r dl + s_l dr)] / [s_l s_r + (z/2)(s_l + s_r)],
+//   z/2 = (55/(12 sqrt 2) (t_l + t_r) - 49/(6 sqrt 2) dl dr + eps (1 - 55/6)/sqrt 2)^2
+// (z = (eps + 13/3 (dr - dl)^2 + 1/4 (dl + dr)^2)^2 rewritten through the
+// squares already formed).
+ESBGK_DEV float2 cweno_dface2(float2 a, float2 b, float2 c, float2 d, float2 epsw) {
+  const float2 m1 = splat2(-1.0f);
+  const float2 d1 = __ffma2_rn(a, m1, b), d2 = __ffma2_rn(b, m1, c), d3 = __ffma2_rn(c, m1, d);
+  const float2 t1 = __ffma2_rn(d1, d1, epsw), t2 = __ffma2_rn(d2, d2, epsw), t3 = __ffma2_rn(d3, d3, epsw);
+  const float2 s1 = __fmul2_rn(t1, t1), s2 = __fmul2_rn(t2, t2), s3 = __fmul2_rn(t3, t3);
+  const float2 C1 = splat2((float)(55.0 / 12.0 / 1.4142135623730951));
+  const float2 C2 = splat2((float)(-49.0 / 6.0 / 1.4142135623730951));
+  const float2 c3 = __fmul2_rn(epsw, splat2((float)((1.0 - 55.0 / 6.0) / 1.4142135623730951)));
+  const float2 c16 = splat2(1.0f / 6.0f), c56 = splat2(5.0f / 6.0f);
+  auto face = [&](float2 u, float2 dl, float2 dr, float2 tl, float2 tr, float2 sl, float2 sr) {
+    const float2 z0 = __ffma2_rn(__fadd2_rn(tl, tr), C1, __ffma2_rn(__fmul2_rn(dl, dr), C2, c3));
+    const float2 zh = __fmul2_rn(z0, z0), xy = __fmul2_rn(sl, sr);
+    const float2 p = __ffma2_rn(c16, dl, __fmul2_rn(c56, dr));
+    const float2 tt = __ffma2_rn(sr, dl, __fmul2_rn(sl, dr));
+    const float2 num = __ffma2_rn(xy, p, __fmul2_rn(zh, tt));
+    const float2 den = __ffma2_rn(zh, __fadd2_rn(sl, sr), xy);
+    float rx, ry;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(den.y));
+    return __ffma2_rn(splat2(0.5f), __fmul2_rn(num, make_float2(rx, ry)), u);
+  };
+  return __ffma2_rn(face(b, d1, d2, t1, t2, s1, s2), m1, face(c, d2, d3, t2, t3, s2, s3));
+}
+
 // Case of global work unit u: the largest c with off[c] <= u (off ascending,
 // off[0] = 0, n >= 1).
 ESBGK_DEV int find_case(const int* off, int n, int u) {

@@ -1058,10 +1058,8 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
       for (int j = 0; j < W; j += 2) {
         const float2 Q = make_float2(q0[j], q0[j + 1]);
         const float2 Ux = make_float2(ux[j], ux[j + 1]), Uy = make_float2(uy[j], uy[j + 1]);
-        const float2 dFx = __ffma2_rn(cweno_face2(make_float2(fx[j], fx[j + 1]), Ux, Q, e2), m1,
-                                      cweno_face2(Ux, Q, make_float2(dx[j], dx[j + 1]), e2));
-        const float2 dFy = __ffma2_rn(cweno_face2(make_float2(fy[j], fy[j + 1]), Uy, Q, e2), m1,
-                                      cweno_face2(Uy, Q, make_float2(dy[j], dy[j + 1]), e2));
+        const float2 dFx = cweno_dface2(make_float2(fx[j], fx[j + 1]), Ux, Q, make_float2(dx[j], dx[j + 1]), e2);
+        const float2 dFy = cweno_dface2(make_float2(fy[j], fy[j + 1]), Uy, Q, make_float2(dy[j], dy[j + 1]), e2);
         const float vxa = vx0 + R(j) * dv, vxb = vxa + dv;
         const float2 Lf = __ffma2_rn(make_float2(rabs(vxa) * idx, rabs(vxb) * idx), dFx, __fmul2_rn(splat2(ay), dFy));
         const float2 F = __ffma2_rn(splat2(cL), Lf, make_float2(bs[j], bs[j + 1]));
