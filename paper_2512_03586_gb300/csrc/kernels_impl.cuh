@@ -289,43 +289,52 @@ ESBGK_DEV bool project(const Geo& g, int lane, CellPar<R>& P, unsigned mask = 0x
   for (int n = 0; n < 15; ++n) s[n] = R(0);
   NodeIter<R> it(lane * W, g.nv, v0, dv, L * W);
   if constexpr (std::is_same<R, float>::value && W % 2 == 0) {
-    // pairs of nodes on the paired FP32 instructions (the pair shares v_y)
-    float2 s2[15];
-#pragma unroll
-    for (int n = 0; n < 15; ++n) s2[n] = splat2(0.0f);
+    // Row segments: a lane takes runs of whole node groups of one velocity
+    // row (v_y fixed), sums G x^p (p = 0..4) along the run on the paired
+    // FP32 instructions and adds them times y^q into the 15 sums once per run.
+    // A segment is half a row when the row has an even number of groups and
+    // that still leaves every lane a segment, else a whole row.  G is formed
+    // from the same operands as in the relaxation pass (cx = (v_x - u_x) +
+    // j dv of the group's first node), so both passes see the same G.
+    const int gpr = g.nv / W, nrows = g.nv;
+    const int segg = (gpr % 2 == 0 && nrows * 2 >= L) ? gpr / 2 : gpr;
+    const int nseg = nrows * (gpr / segg);
+    const float2 qxx2 = splat2(P.qxx), pref2 = splat2(P.pref), isT2 = splat2(P.isT);
 #pragma unroll 1
-    for (; it.k < g.nvv; it.next()) {
-      const float cy = it.vy() - P.uy, y = cy * P.isT;
-      const float2 y2 = splat2(y), qy = splat2(P.qyy * cy * cy), qc = splat2(P.qxy * cy);
+    for (int sg = lane; sg < nseg; sg += L) {
+      const int k0 = sg * segg * W;  // first node of the segment
+      const int ky = k0 / g.nv, kx0 = k0 - ky * g.nv;
+      const float cy = (v0 + R(ky) * dv) - P.uy, y = cy * P.isT;
+      const float2 qy = splat2(P.qyy * cy * cy), qc = splat2(P.qxy * cy);
+      float2 R0 = splat2(0.0f), R1 = R0, R2 = R0, R3 = R0, R4 = R0;
+#pragma unroll 1
+      for (int gg = 0; gg < segg; ++gg) {
+        const float cx0 = (v0 + R(kx0 + gg * W) * dv) - P.ux;
 #pragma unroll
-      for (int j = 0; j < W; j += 2) {
-        const float cxa = it.vx() + R(j) * dv - P.ux;
-        const float2 cx = make_float2(cxa, cxa + dv);
-        const float2 e = __ffma2_rn(splat2(P.qxx), __fmul2_rn(cx, cx), __ffma2_rn(qc, cx, qy));
-        const float2 G = __fmul2_rn(splat2(P.pref), make_float2(exp2r(e.x), exp2r(e.y)));
-        const float2 x = __fmul2_rn(cx, splat2(P.isT));
-        const float2 Gx = __fmul2_rn(G, x), Gy = __fmul2_rn(G, y2);
-        const float2 Gxx = __fmul2_rn(Gx, x), Gxy = __fmul2_rn(Gx, y2), Gyy = __fmul2_rn(Gy, y2);
-        s2[0] = __fadd2_rn(s2[0], G);
-        s2[1] = __fadd2_rn(s2[1], Gx);
-        s2[2] = __fadd2_rn(s2[2], Gy);
-        s2[3] = __fadd2_rn(s2[3], Gxx);
-        s2[4] = __fadd2_rn(s2[4], Gxy);
-        s2[5] = __fadd2_rn(s2[5], Gyy);
-        s2[6] = __ffma2_rn(Gxx, x, s2[6]);
-        s2[7] = __ffma2_rn(Gxx, y2, s2[7]);
-        s2[8] = __ffma2_rn(Gxy, y2, s2[8]);
-        s2[9] = __ffma2_rn(Gyy, y2, s2[9]);
-        const float2 Gxxx = __fmul2_rn(Gxx, x), Gxxy = __fmul2_rn(Gxx, y2);
-        s2[10] = __ffma2_rn(Gxxx, x, s2[10]);
-        s2[11] = __ffma2_rn(Gxxx, y2, s2[11]);
-        s2[12] = __ffma2_rn(Gxxy, y2, s2[12]);
-        s2[13] = __ffma2_rn(__fmul2_rn(Gxy, y2), y2, s2[13]);
-        s2[14] = __ffma2_rn(__fmul2_rn(Gyy, y2), y2, s2[14]);
+        for (int j = 0; j < W; j += 2) {
+          const float cxa = cx0 + R(j) * dv;
+          const float2 cx = make_float2(cxa, cxa + dv);
+          const float2 e = __ffma2_rn(qxx2, __fmul2_rn(cx, cx), __ffma2_rn(qc, cx, qy));
+          const float2 G = __fmul2_rn(pref2, make_float2(exp2r(e.x), exp2r(e.y)));
+          const float2 x = __fmul2_rn(cx, isT2);
+          const float2 t1 = __fmul2_rn(G, x), t2 = __fmul2_rn(t1, x), t3 = __fmul2_rn(t2, x);
+          R0 = __fadd2_rn(R0, G);
+          R1 = __fadd2_rn(R1, t1);
+          R2 = __fadd2_rn(R2, t2);
+          R3 = __fadd2_rn(R3, t3);
+          R4 = __ffma2_rn(t3, x, R4);
+        }
       }
-    }
+      const float rr[5] = {R0.x + R0.y, R1.x + R1.y, R2.x + R2.y, R3.x + R3.y, R4.x + R4.y};
+      float yq[5];
+      yq[0] = 1.0f;
 #pragma unroll
-    for (int n = 0; n < 15; ++n) s[n] = s2[n].x + s2[n].y;
+      for (int q = 1; q < 5; ++q) yq[q] = yq[q - 1] * y;
+#pragma unroll
+      for (int pp = 0; pp < 5; ++pp)
+#pragma unroll
+        for (int q = 0; q + pp < 5; ++q) s[mono(pp, q)] = fmaf(rr[pp], yq[q], s[mono(pp, q)]);
+    }
   } else {
 #pragma unroll 1
   for (; it.k < g.nvv; it.next())
