@@ -19,6 +19,9 @@
 // memory; the GEMM depth runs over 9 taps x the input channels.
 #include "cnn.h"
 
+#include <cuda.h>
+
+#include <cstring>
 #include <string>
 
 #include "common.cuh"
@@ -163,7 +166,11 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(const bf* __restrict__ i
 //      offset); a tap is only a different start address.
 //   B: the weights as [k group of 8][32 out][8]: core matrices at +128 B
 //      along N and +512 B along K.
-constexpr int TC_M = 128, TC_HW = TC_M + 2, TC_PLANE = 3 * TC_HW * 16;  // bytes of one 8-channel plane
+constexpr int TC_M = 128, TC_HW = TC_M + 2;
+// bytes of one 8-channel plane (3 x TC_HW cells of 16 B), padded to 128 B:
+// the tensor copies write each plane at a 128-byte aligned address
+constexpr int TC_PLANE = (3 * TC_HW * 16 + 127) / 128 * 128;
+constexpr unsigned kTcHaloBytes = 4u * 3u * TC_HW * 16u;  // the four planes' boxes
 constexpr int TC_WBYTES = kK2 / 8 * 512;                                  // 36 k groups x 512 B
 constexpr size_t kTcSmem = 4 * (size_t)TC_PLANE + TC_WBYTES;
 
@@ -186,13 +193,20 @@ constexpr uint32_t kTcIdesc = (1u << 4)                // D format f32
 // segment within it).  Per segment: stage the halo, one thread issues the
 // MMAs and commits to the mbarrier (phase = the CTA's segment count & 1),
 // every warp reads its 32 cells back.
-__global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ in, const bf* __restrict__ wk,
+// TMA: the halo comes by four tensor copies (one per 8-channel plane, box 8
+// channels x TC_HW cells x 3 rows, zeros outside the image) completing on an
+// mbarrier; the next tile's copies are issued as soon as the current tile's
+// MMAs have read the halo, so they overlap the read-back.  Without a tensor
+// map the threads stage the halo with plain loads.
+template <bool TMA>
+__global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                        const bf* __restrict__ in, const bf* __restrict__ wk,
                                                         const float* __restrict__ bias, int n, int H, int W,
                                                         bf* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sa = tsm;                 // A halo, 4 planes
   unsigned char* sb = tsm + 4 * TC_PLANE;  // B weights
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar, tbar;
   __shared__ uint32_t tmem_base;
   __shared__ float s_b[kHid];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -205,6 +219,7 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
   }
   if (tid == 0) {
     mbar_init(&mbar, 1);
+    mbar_init(&tbar, 1);
     mbar_init_fence();
   }
   if (tid < kHid) s_b[tid] = bias[tid];
@@ -213,25 +228,68 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
     const int o = i / (kK2 / 8), kg = i % (kK2 / 8);
     *reinterpret_cast<uint4*>(sb + kg * 512 + o * 16) = *reinterpret_cast<const uint4*>(wk + (size_t)o * kK2 + kg * 8);
   }
+  // the weights written by the threads are read by the tensor cores (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  // tile t: image t / (H * segs), row and segment within it
+  auto tile_of = [&](int t, int& img, int& y, int& x0) {
+    img = t / (H * segs);
+    const int r0 = t % (H * segs);
+    y = r0 / segs;
+    x0 = (r0 % segs) * TC_M;
+  };
+  // one thread: the tensor copies of tile t's halo (rows y-1..y+1, cells
+  // x0-1..x0+TC_M of every plane; coordinates outside the image read zeros)
+  auto issue = [&](int t) {
+    int img, y, x0;
+    tile_of(t, img, y, x0);
+    const unsigned bar = smem_u32(&tbar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTcHaloBytes) : "memory");
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl)
+      asm volatile(
+          "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+          "%6}], [%7];" ::"r"(smem_u32(sa + pl * TC_PLANE)),
+          "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(pl), "r"(x0 - 1), "r"(y - 1), "r"(img), "r"(bar)
+          : "memory");
+  };
   bool ok = true;
-  unsigned phase = 0;
+  unsigned phase = 0, tphase = 0;
+  if (TMA && tid == 0 && (int)blockIdx.x < total) issue(blockIdx.x);
   for (int t = blockIdx.x; t < total && ok; t += gridDim.x, phase ^= 1u) {
-    const int img = t / (H * segs), r0 = t % (H * segs), y = r0 / segs, x0 = (r0 % segs) * TC_M;
-    // halo rows y-1..y+1, cells x0-1..x0+TC_M, zeros outside the image
-    for (int i = tid; i < 3 * TC_HW * 4; i += blockDim.x) {
-      const int pl = i % 4, cell = i / 4, r = cell / TC_HW, cx = cell % TC_HW;
-      const int gy = y + r - 1, gx = x0 + cx - 1;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-        v = *reinterpret_cast<const uint4*>(in + (((size_t)img * H + gy) * W + gx) * kHid + pl * 8);
-      *reinterpret_cast<uint4*>(sa + pl * TC_PLANE + (r * TC_HW + cx) * 16) = v;
+    int img, y, x0;
+    tile_of(t, img, y, x0);
+    if constexpr (TMA) {
+      // the halo of tile t has landed (bounded wait; the outcome is uniform);
+      // the barrier also orders the previous tile's read-back before this
+      // tile's MMAs overwrite the accumulator
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      ok = __syncthreads_and(mbar_wait(&tbar, tphase));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tphase ^= 1u;
+      if (!ok) {
+        if (tid == 0 && err) atomicCAS(err, 0, kErrTimeout);
+        // the copies may still be in flight: wait for them once more (bounded)
+        __syncthreads_and(mbar_wait(&tbar, tphase ^ 1u));
+        break;
+      }
+    } else {
+      // halo rows y-1..y+1, cells x0-1..x0+TC_M, zeros outside the image
+      for (int i = tid; i < 3 * TC_HW * 4; i += blockDim.x) {
+        const int pl = i % 4, cell = i / 4, r = cell / TC_HW, cx = cell % TC_HW;
+        const int gy = y + r - 1, gx = x0 + cx - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+          v = *reinterpret_cast<const uint4*>(in + (((size_t)img * H + gy) * W + gx) * kHid + pl * 8);
+        *reinterpret_cast<uint4*>(sa + pl * TC_PLANE + (r * TC_HW + cx) * 16) = v;
+      }
+      // operands written by the threads are read by the tensor cores (async
+      // proxy); the previous segment's accumulator reads are complete
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    // operands written by the threads are read by the tensor cores (async
-    // proxy); the previous segment's accumulator reads are complete
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     if (tid == 0) {
       const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
@@ -261,6 +319,8 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       break;
     }
+    // the MMAs have read the halo: the next tile's copies run during the read-back
+    if (TMA && tid == 0 && t + (int)gridDim.x < total) issue(t + gridDim.x);
     // warp w reads tensor-memory lanes 32w..32w+31 (its cells), 32 columns (channels)
     uint32_t v[32];
     asm volatile(
@@ -288,6 +348,40 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const bf* __restrict__ i
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_base));
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of activations [img][H][W][32] bf16 as five dimensions
+// (8 channels, 4 planes, W, H, img) with a box of one plane x TC_HW cells x
+// 3 rows; false if it cannot be built (the threads then stage the halo).
+static bool halo_map(CUtensorMap* m, const bf* in, int n, int H, int W) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || ((uintptr_t)in & 15u)) return false;
+  const cuuint64_t dims[5] = {8, 4, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+  const cuuint64_t strides[4] = {16, 64, 64ull * W, 64ull * W * H};  // bytes, dimensions 1..4
+  const cuuint32_t box[5] = {8, 1, TC_HW, 3, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf*>(in), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int H, int W, bf* out, int* err,
                       cudaStream_t s) {
   static int nsm = 0;  // SMs of the device (queried once)
@@ -299,7 +393,13 @@ void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int 
   }
   const int total = n * H * ((W + TC_M - 1) / TC_M);
   const int cap = nsm * 5;  // resident CTAs at 43 KB of shared memory each
-  conv32_tc_kernel<<<total < cap ? total : cap, 128, kTcSmem, s>>>(in, wk, bias, n, H, W, out, err);
+  const int grid = total < cap ? total : cap;
+  alignas(64) CUtensorMap m;
+  memset(&m, 0, sizeof m);
+  if (halo_map(&m, in, n, H, W))
+    conv32_tc_kernel<true><<<grid, 128, kTcSmem, s>>>(m, in, wk, bias, n, H, W, out, err);
+  else
+    conv32_tc_kernel<false><<<grid, 128, kTcSmem, s>>>(m, in, wk, bias, n, H, W, out, err);
 }
 
 // Weight gradient of a 3 x 3 convolution, per CTA partial sums over the
