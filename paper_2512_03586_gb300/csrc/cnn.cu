@@ -198,11 +198,16 @@ constexpr uint32_t kTcIdesc = (1u << 4)                // D format f32
 // mbarrier; the next tile's copies are issued as soon as the current tile's
 // MMAs have read the halo, so they overlap the read-back.  Without a tensor
 // map the threads stage the halo with plain loads.
-template <bool TMA>
+// MODE kFwd: out = relu(acc + bias) (the forward 32 -> 32 layer, weights
+// w2f); kDgrad: out = acc masked by (mask > 0), the input gradient of that
+// layer (weights w2d: transposed channels, flipped taps; mask = its input
+// activations, the ReLU derivative of the layer below).
+template <bool TMA, int MODE>
 __global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                         const bf* __restrict__ in, const bf* __restrict__ wk,
                                                         const float* __restrict__ bias, int n, int H, int W,
-                                                        bf* __restrict__ out, int* __restrict__ err) {
+                                                        bf* __restrict__ out, const bf* __restrict__ mask,
+                                                        int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sa = tsm;                 // A halo, 4 planes
   unsigned char* sb = tsm + 4 * TC_PLANE;  // B weights
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ 
     mbar_init(&tbar, 1);
     mbar_init_fence();
   }
-  if (tid < kHid) s_b[tid] = bias[tid];
+  if (MODE == kFwd && tid < kHid) s_b[tid] = bias[tid];
   // weights W2f[o][k] (k = tap*32 + c) -> [k/8][o][k%8], 16-byte pieces
   for (int i = tid; i < kHid * kK2 / 8; i += blockDim.x) {
     const int o = i / (kK2 / 8), kg = i % (kK2 / 8);
@@ -334,12 +339,30 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ 
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const int gx = x0 + 32 * warp + lane;
     if (gx < W) {
-      uint32_t* dst = reinterpret_cast<uint32_t*>(out + (((size_t)img * H + y) * W + gx) * kHid);
+      const size_t cell = ((size_t)img * H + y) * W + gx;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + cell * kHid);
+      if constexpr (MODE == kFwd) {
 #pragma unroll
-      for (int o = 0; o < kHid; o += 2) {
-        const float a = fmaxf(__uint_as_float(v[o]) + s_b[o], 0.f);
-        const float b = fmaxf(__uint_as_float(v[o + 1]) + s_b[o + 1], 0.f);
-        dst[o / 2] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+        for (int o = 0; o < kHid; o += 2) {
+          const float a = fmaxf(__uint_as_float(v[o]) + s_b[o], 0.f);
+          const float b = fmaxf(__uint_as_float(v[o + 1]) + s_b[o + 1], 0.f);
+          dst[o / 2] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+        }
+      } else {
+        const uint4* mk = reinterpret_cast<const uint4*>(mask + cell * kHid);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // 8 channels per 16-byte piece of the mask
+          const uint4 m4 = mk[q];
+          const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int o = 8 * q + 2 * h;
+            const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[h]);
+            const float a = __bfloat162float(m2.x) > 0.f ? __uint_as_float(v[o]) : 0.f;
+            const float b = __bfloat162float(m2.y) > 0.f ? __uint_as_float(v[o + 1]) : 0.f;
+            dst[o / 2] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+          }
+        }
       }
     }
   }
@@ -382,8 +405,10 @@ static bool halo_map(CUtensorMap* m, const bf* in, int n, int H, int W) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// mask: null for the forward layer (bias + ReLU), else the input gradient
+// masked by mask > 0.
 void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int H, int W, bf* out, int* err,
-                      cudaStream_t s) {
+                      cudaStream_t s, const bf* mask = nullptr) {
   static int nsm = 0;  // SMs of the device (queried once)
   if (nsm == 0) {
     int dev = 0;
@@ -396,10 +421,13 @@ void launch_conv32_tc(const bf* in, const bf* wk, const float* bias, int n, int 
   const int grid = total < cap ? total : cap;
   alignas(64) CUtensorMap m;
   memset(&m, 0, sizeof m);
-  if (halo_map(&m, in, n, H, W))
-    conv32_tc_kernel<true><<<grid, 128, kTcSmem, s>>>(m, in, wk, bias, n, H, W, out, err);
+  const bool tma = halo_map(&m, in, n, H, W);
+  if (mask)
+    (tma ? conv32_tc_kernel<true, kDgrad> : conv32_tc_kernel<false, kDgrad>)<<<grid, 128, kTcSmem, s>>>(
+        m, in, wk, nullptr, n, H, W, out, mask, err);
   else
-    conv32_tc_kernel<false><<<grid, 128, kTcSmem, s>>>(m, in, wk, bias, n, H, W, out, err);
+    (tma ? conv32_tc_kernel<true, kFwd> : conv32_tc_kernel<false, kFwd>)<<<grid, 128, kTcSmem, s>>>(
+        m, in, wk, bias, n, H, W, out, nullptr, err);
 }
 
 // Weight gradient of a 3 x 3 convolution, per CTA partial sums over the
@@ -812,7 +840,7 @@ void backward_launches(esbgk_cnn* c, const __nv_bfloat16* x, const uint8_t* y, i
   wgrad_kernel<kHid><<<c->nparts, kThreads, 0, s>>>(c->dz2, c->a1, n, H, W, c->part);
   reduce_wgrad_kernel<kHid><<<(kHid * kK2 + kHid + 255) / 256, 256, 0, s>>>(c->part, c->nparts, c->grad, kOffW2,
                                                                             kOffB2, kHid);
-  conv_kernel<kHid, kDgrad><<<grid, kThreads, 0, s>>>(c->dz2, c->w.w2d, nullptr, H, W, c->dz1, c->a1);
+  launch_conv32_tc(c->dz2, c->w.w2d, nullptr, n, H, W, c->dz1, c->err, s, c->a1);
   wgrad_kernel<kCinPad><<<c->nparts, kThreads, 0, s>>>(c->dz1, x, n, H, W, c->part);
   reduce_wgrad_kernel<kCinPad><<<(kHid * kK1 + kHid + 255) / 256, 256, 0, s>>>(c->part, c->nparts, c->grad, kOffW1,
                                                                               kOffB1, kCin);
