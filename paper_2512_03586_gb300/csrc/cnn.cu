@@ -7,9 +7,12 @@
 // mma.sync.m16n8k16); the 1 x 1 head, the loss and the optimizer are float32
 // on the CUDA cores.
 //
-// The forward 32 -> 32 convolution runs on the 5th-generation tensor cores
-// (tcgen05.mma with a tensor-memory accumulator, conv32_tc_kernel); the other
-// convolutions use mma.sync.
+// The 32 -> 32 convolution of the forward pass and its input gradient run on
+// the 5th-generation tensor cores (tcgen05.mma with a tensor-memory
+// accumulator, halo staged by TMA tensor copies: conv32_tc_kernel); the
+// 5 -> 32 forward convolution and the weight gradients use mma.sync (the
+// 5 -> 32 layer on the tcgen05 kernel, nine MMAs per tile, took 51.2 us per
+// training batch against 37.9 us).
 //
 // Tiling (mma.sync kernels): a CTA owns 8 x 16 output cells of one image; its 4 warps own two
 // rows of 16 cells each (one m16 tile per row) and all 32 output channels
