@@ -756,6 +756,36 @@ def learned_arm(args):
                       "error_vs_plain_fp32": r["error_vs_all_kinetic"] / p32["error_vs_all_kinetic"],
                       "kinetic_work_vs_plain_fp32": r["kinetic_cell_steps"] / max(p32["kinetic_cell_steps"], 1)})
 
+    # the combined form: learned switch + FP32 storage + batched form, four
+    # copies of the deployment case in one batch (a batch equals its single
+    # runs to rounding, so case 0's error is the learned run's)
+    nb = args.batch_cases
+    bstream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(bstream):
+        bs = G.BatchSolver([(wl["grid"], wl["vmesh"], dict(wl["params"], switch="learned"))] * nb, prec="fp32",
+                           device=dev, stream=bstream)
+        for i in range(nb):
+            bs.set_state(i, f["rho"], f["ux"], f["uy"], f["T"], f["eps"], f["kin"])
+            bs.set_switch_params(i, theta)
+        dts = np.full(nb, dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(bstream)
+        for _ in range(nsim):
+            bs.step(dts, tab)
+        e1.record(bstream)
+        torch.cuda.synchronize(dev)
+        bs.sync()
+        bms = e0.elapsed_time(e1)
+        berr = err(bs.cons(0))
+        del bs
+    per_case = bms / nb / (nsim * dt)
+    combined = {"cases": nb, "ms_per_step": bms / nsim, "ms_per_sim_time_per_case": per_case,
+                "error_vs_all_kinetic_case0": berr,
+                "wall_per_sim_time_vs_plain_fp64": per_case / res["plain_fp64"]["ms_per_sim_time"],
+                "error_vs_plain_fp64": berr / res["plain_fp64"]["error_vs_all_kinetic"],
+                "wall_per_sim_time_vs_learned_fp32_single": per_case / res["learned_fp32"]["ms_per_sim_time"]}
+
     # timed region of the line: K steps of the learned FP32 form, L2 flushed between steps
     for _ in range(args.warmup):
         learned.step(dt, tab)
@@ -791,6 +821,7 @@ def learned_arm(args):
            "learned_fp32_vs_plain_fp64": {"wall_per_sim_time_ratio": l32["ms_per_sim_time"] / p64["ms_per_sim_time"],
                                           "error_ratio": l32["error_vs_all_kinetic"] / p64["error_vs_all_kinetic"]},
            "learned_fp32_vs_plain_fp32_by_init_seed": seeds,
+           "learned_fp32_batched_vs_plain_fp64": combined,
            "learned_fp32_vs_plain_fp32_spread": {
                k: [min(x[k] for x in seeds), max(x[k] for x in seeds)]
                for k in ("wall_per_sim_time_vs_plain_fp32", "error_vs_plain_fp32", "kinetic_work_vs_plain_fp32")},
@@ -896,6 +927,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--sim-steps", type=int, default=100, help="steps of the learned-switch comparison runs")
     ap.add_argument("--init-seeds", type=int, default=3, help="networks trained from these many initialisations")
+    ap.add_argument("--batch-cases", type=int, default=4, help="cases of the batched learned-switch comparison")
     ap.add_argument("--cases", type=int, default=64, help="cases of the batched workload")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-steps", type=int, default=8)
