@@ -68,6 +68,13 @@ def test_host_only_entry_points(libpath):
     assert _abi.esbgk_step(None, 1e-3, None) == _abi.E_ARG
     assert _abi.esbgk_relax_cells(None, None, 1, 8, 1.0, -0.5, 0, None, None, None) == _abi.E_ARG
     _abi.esbgk_destroy(None)
+    # the batch's schedule, form and learned-switch entry points on a null batch
+    i32 = ctypes.c_int32()
+    assert _abi.esbgk_batch_schedule(None, None, None, None, None, 0, ctypes.byref(i32)) == _abi.E_ARG
+    assert _abi.esbgk_batch_set_form(None, 16, 0) == _abi.E_ARG
+    assert _abi.esbgk_batch_set_switch_params(None, 0, None) == _abi.E_ARG
+    assert _abi.esbgk_batch_switch_stats(None, 0, None, None, None, None) == _abi.E_ARG
+    assert _abi.esbgk_tiles(None, 1) == _abi.E_ARG
 
 
 def test_oracle_and_library_share_no_code():
