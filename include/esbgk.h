@@ -533,7 +533,7 @@ int esbgk_cnn_sync(esbgk_cnn* c);
  *   the 3 KiB hold the counters, the error word and the rounding key);
  * larger problems are rejected with ESBGK_E_TOO_LARGE before any device work.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture begins.
+ * device current).
  * All calls share the one array, which keeps the last call's contents (the
  * call clears what must start at zero): calls that may overlap on the GPU --
  * on different streams, or from several host threads -- race and must be
