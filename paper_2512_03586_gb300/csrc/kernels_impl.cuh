@@ -959,9 +959,11 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
 // fourth x-neighbour too and takes each node's upwind stencil.
 // L lanes per cell: 32 (the warp) or 16 (a half-warp; mask: its lanes; lane:
 // the index within the half) -- two cells per warp for small velocity grids.
-template <typename S, int M, int W, int L = 32, bool SX = false>
+// WALLS: solid obstacles (the stencil maps of View; no group straddles v_x = 0).
+template <typename S, int M, int W, int L = 32, bool SX = false, bool WALLS = false>
 ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs,
                                 unsigned mask = 0xffffffffu) {
+  static_assert(!(WALLS && SX), "the wall form has no straddling group");
   using R = typename Real<S>::T;
   using IO = VecIO<S, W>;
   using SM = SmemVec<R, W>;
@@ -969,7 +971,11 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   const Geo& g = V.g;
   const unsigned o0 = (unsigned)c * (unsigned)g.nvv;
   unsigned o[8];
-  stencil_offsets(g, c, o);
+  unsigned rb = 0u;  // reflection bits of the stencil positions (solid obstacles)
+  if constexpr (WALLS)
+    stencil_walls(V, c, o, rb);
+  else
+    stencil_offsets(g, c, o);
   const S* fsrc = (const S*)A.f_src;
   const S* sbase = (const S*)A.star_base;
   const R v0 = pick<R>(g.v0, g.fv0), dv = pick<R>(g.dv, g.fdv);
@@ -1022,10 +1028,33 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
     const R vx0 = it.vx(), vy = it.vy();
     const bool px = vx0 > R(0), py = vy > R(0);
     R q0[W], ux[W], dx[W], fx[W], uy[W], dy[W], fy[W], bs[W], ai[nacc > 0 ? nacc : 1][W];
+    // the group's values at stencil position e; a mirror image across a wall
+    // face (reflection bit set) is read at the mirrored nodes: along x the
+    // node order reversed within the row (the mirrored group starts at
+    // N_v - W - k_x, aligned because W divides N_v), along y the mirrored row
+    // (oe: the position's cell offset, re: its reflection bit, xa: along x)
+    auto ldn = [&](unsigned oe, bool re, bool xa, R (&v)[W]) {
+      if constexpr (WALLS) {
+        if (re) {
+          const unsigned kxg = (unsigned)it.kx, kyg = (unsigned)it.fy, nvu = (unsigned)g.nv;
+          if (xa) {
+            R t[W];
+            IO::ld(fsrc + oe + kyg * nvu + (nvu - (unsigned)W - kxg), t);
+#pragma unroll
+            for (int j = 0; j < W; ++j) v[j] = t[W - 1 - j];
+          } else {
+            IO::ld(fsrc + oe + (nvu - 1u - kyg) * nvu + kxg, v);
+          }
+          return;
+        }
+      }
+      IO::ld(fsrc + oe + k, v);
+    };
+    auto bit = [&](int e) { return WALLS && ((rb >> e) & 1u); };
     IO::ld(fsrc + o0 + k, q0);
-    IO::ld(fsrc + (px ? o[1] : o[2]) + k, ux);
-    IO::ld(fsrc + (px ? o[2] : o[1]) + k, dx);
-    IO::ld(fsrc + (px ? o[0] : o[3]) + k, fx);
+    ldn(px ? o[1] : o[2], px ? bit(1) : bit(2), true, ux);
+    ldn(px ? o[2] : o[1], px ? bit(2) : bit(1), true, dx);
+    ldn(px ? o[0] : o[3], px ? bit(0) : bit(3), true, fx);
     if (SX && it.kx == kz) {
       // first node v_x < 0 (loaded above), the last ones v_x > 0: upwind is
       // the left neighbour, downwind the right one, far side two to the left
@@ -1040,9 +1069,9 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
           fx[j] = l2[j];
         }
     }
-    IO::ld(fsrc + (py ? o[5] : o[6]) + k, uy);
-    IO::ld(fsrc + (py ? o[6] : o[5]) + k, dy);
-    IO::ld(fsrc + (py ? o[4] : o[7]) + k, fy);
+    ldn(py ? o[5] : o[6], py ? bit(5) : bit(6), false, uy);
+    ldn(py ? o[6] : o[5], py ? bit(6) : bit(5), false, dy);
+    ldn(py ? o[4] : o[7], py ? bit(4) : bit(7), false, fy);
     if (MT::base_src) {
 #pragma unroll
       for (int j = 0; j < W; ++j) bs[j] = q0[j];
@@ -1330,7 +1359,7 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
           ++mine;
         }
       } else if constexpr (W > 1) {
-        kinetic_cell_vec<S, M, W, 32, SX>(A, V, V.klist[u], lane, sfs);
+        kinetic_cell_vec<S, M, W, 32, SX, WALLS>(A, V, V.klist[u], lane, sfs);
         ++mine;
       } else {
         kinetic_cell<S, M, WALLS>(A, V, V.klist[u], lane, sfs);
@@ -1727,6 +1756,21 @@ struct Launch {
       default: return stage_kernel<S, kGeneric, 1>;
     }
   }
+  // With solid obstacles: the wide vector form with the wall stencils (one
+  // cell per warp) where the specialised modes would take a wide form, else
+  // the generic scalar form.
+  static StageFn wall_fn(int m, int var) {
+    if (var == kVarWide || var == kVarWidePair) {
+      switch (m) {
+        case kFirstRelax2: return stage_kernel<S, kFirstRelax2, kW, false, false, true>;
+        case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1, kW, false, false, true>;
+        case kFinal: return stage_kernel<S, kFinal, kW, false, false, true>;
+        case kFirstRelax0: return stage_kernel<S, kFirstRelax0, kW, false, false, true>;
+        default: break;
+      }
+    }
+    return stage_kernel<S, kGeneric, 1, false, false, true>;
+  }
   static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
   // Per-cell code of a stage launch: the vector form (specialised modes,
   // every f-sized array 16-byte aligned, N_v divisible by the group size)
@@ -1827,9 +1871,10 @@ struct Launch {
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(stage_kernel<S, kGeneric, 1, false, false, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
-      return e;
+    for (int m = 0; m < kNumModes; ++m)
+      if ((e = cudaFuncSetAttribute(wall_fn(m, kVarWide), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+          cudaSuccess)
+        return e;
     // batched kernels: set here so that their launches can be graph-captured
     const int mb = mx - kBatchStaticSmem;
     for (int m = 0; m < kNumModes; ++m)
@@ -1857,8 +1902,8 @@ struct Launch {
     const int arrays = V.wsrc || !variant_pairs(var) ? 1 : 2;  // f* arrays per warp
     const int threads = 32 * warps_for(V.g, arrays);
     const size_t smem = proj ? smem_for(V.g, arrays) : 0;
-    // solid obstacles: the generic scalar form with the wall stencils
-    const StageFn fn = V.wsrc ? stage_kernel<S, kGeneric, 1, false, false, true> : stage_fn(mode, var);
+    // solid obstacles: the forms with the wall stencils
+    const StageFn fn = V.wsrc ? wall_fn(mode, var) : stage_fn(mode, var);
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {

@@ -71,8 +71,12 @@ def _box(n=20, nv=12):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("all_kinetic", [True, False])
-def test_walls_frozen_map_match_oracle(prec, all_kinetic):
-    wl, solid = _box()
+@pytest.mark.parametrize("nv", [10, 16])
+def test_walls_frozen_map_match_oracle(prec, all_kinetic, nv):
+    """N_v = 10 takes the scalar wall form (N_v/2 is not a multiple of the
+    node group, 2 nodes in FP64 and 4 in FP32); N_v = 16 the vector form
+    with mirrored group reads."""
+    wl, solid = _box(nv=nv)
     wl["fields"]["kin"] = np.full(solid.shape, all_kinetic)
     g, P, st = _pair(wl, solid, prec)
     g.tiles(True)
