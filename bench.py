@@ -270,7 +270,7 @@ class ClockSampler:
 # the sources that define the stage kernels (the network, the host runtime and
 # the criterion's kernels do not change their traffic)
 STAGE_SOURCES = ("common.cuh", "kernels_impl.cuh", "tile_impl.cuh", "launch.h", "kernels_f32.cu", "kernels_f64.cu",
-                 "kernels_bf16.cu")
+                 "kernels_bf16.cu", "kernels_f32_sums.cu", "kernels_bf16_sums.cu")
 
 
 def source_hash():

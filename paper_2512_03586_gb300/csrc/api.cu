@@ -1312,6 +1312,7 @@ struct esbgk_batch {
   cudaStream_t stream = nullptr;
   int nsm = 0, total_cells = 0, max_threads = 128;
   int max_nvv = 0;  // shared f nodes per warp of the batched kernels
+  bool comp = false;  // some case sums the moments with compensation
   std::vector<esbgk_ctx*> cs;
   BatchTabSet sets[kTabSets];
   int* d_cell_off = nullptr;
@@ -1429,7 +1430,7 @@ CaseRegime regime_of(esbgk_batch* b, int i) {
 
 // CTAs of a batched stage launch.
 int batch_stage_grid(esbgk_batch* b, int mode, int var) {
-  const int occ = b->L->batch_stage_occupancy(mode, var, b->max_nvv, b->threads);
+  const int occ = b->L->batch_stage_occupancy(mode, var, b->comp, b->max_nvv, b->threads);
   const int per_sm = b->ctas > 0 && b->ctas < occ ? b->ctas : occ;
   return b->nsm * per_sm;
 }
@@ -1481,7 +1482,7 @@ void batch_launches(esbgk_batch* b, const BatchTabSet& t, const int* grids) {
     for (int v = 0; v < kNumVariants; ++v)
       if (t.has_var[v])
         b->L->batch_stage(t.stage + (size_t)j * b->n, b->d_off_stage + v * (b->n + 1), b->n, t.modes[j], v,
-                          b->max_nvv, b->threads, grids[j * kNumVariants + v], b->stream);
+                          b->comp, b->max_nvv, b->threads, grids[j * kNumVariants + v], b->stream);
   }
 }
 
@@ -1642,6 +1643,7 @@ int esbgk_batch_create(int32_t n, const esbgk_grid* grids, const esbgk_vmesh* vm
       return r;
     }
     b->cs.push_back(X);
+    b->comp = b->comp || X->m.comp_moments;
     cell_off[i + 1] = cell_off[i] + X->g.nc;
     // shared f nodes per warp: two cells' worth where pairs may run
     const int per_warp = X->g.nvv <= kPairMaxNodes ? 2 * X->g.nvv : X->g.nvv;

@@ -951,6 +951,10 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
   }
 }
 
+// Moment sums of the paired FP32 vector forms: compensation compiled out, or
+// chosen at run time by Model::comp_moments.
+enum : int { kSumsPlain = 0, kSumsRunTime = 1 };
+
 // Vector form of kinetic_cell for a specialised launch mode: each lane takes W
 // consecutive nodes of one velocity row per iteration (one vector load per
 // stencil array instead of W), which needs N_v divisible by W (a group never
@@ -960,7 +964,10 @@ ESBGK_DEV void kinetic_cell(const StageArgs& A, const View& V, int c, int lane, 
 // L lanes per cell: 32 (the warp) or 16 (a half-warp; mask: its lanes; lane:
 // the index within the half) -- two cells per warp for small velocity grids.
 // WALLS: solid obstacles (the stencil maps of View; no group straddles v_x = 0).
-template <typename S, int M, int W, int L = 32, bool SX = false, bool WALLS = false>
+// SUMS: how the paired FP32 forms sum the moments -- kSumsPlain compiles the
+// compensation out (no compensation state live in the node loop),
+// kSumsRunTime follows Model::comp_moments.
+template <typename S, int M, int W, int L = 32, bool SX = false, bool WALLS = false, int SUMS = kSumsRunTime>
 ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int lane, typename Real<S>::T* sfs,
                                 unsigned mask = 0xffffffffu) {
   static_assert(!(WALLS && SX), "the wall form has no straddling group");
@@ -1009,7 +1016,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   // go every kFlush groups into a Neumaier-compensated accumulator per lane
   // (m, mc) and the lanes are added with error-free two-sums.
   constexpr bool kPacked = std::is_same<R, float>::value && W % 2 == 0;
-  const bool kComp = kPacked && V.m.comp_moments;
+  const bool kComp = kPacked && SUMS == kSumsRunTime && V.m.comp_moments;
   constexpr int kFlush = 4;
   R m[6];
   float2 m2[6];
@@ -1327,11 +1334,14 @@ ESBGK_DEV void buffer_cell(const StageArgs& A, const View& V, int c, int lane) {
 #ifndef ESBGK_STAGE_MIN_BLOCKS
 #define ESBGK_STAGE_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
 #endif
+
 // PAIR (vector form, small velocity grids): a kinetic unit is two cells, one
 // per half-warp, so that twice as many cells are in flight when a cell has
 // only a few node groups per lane.
-// WALLS: solid obstacles (View::wsrc); only the generic scalar form is compiled with them.
-template <typename S, int M, int W, bool PAIR = false, bool SX = false, bool WALLS = false>
+// WALLS: solid obstacles (View::wsrc): the generic scalar form and the wide
+// vector form are compiled with them.
+// SUMS: the moment sums of the vector forms (kinetic_cell_vec).
+template <typename S, int M, int W, bool PAIR = false, bool SX = false, bool WALLS = false, int SUMS = kSumsPlain>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_kernel(StageArgs A, View V) {
   using R = typename Real<S>::T;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1355,11 +1365,12 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS) stage_ke
       if constexpr (PAIR) {
         const int ci = 2 * u + half;  // this half's cell
         if (ci < nK) {
-          kinetic_cell_vec<S, M, W, 16, SX>(A, V, V.klist[ci], lane & 15, sfs, half ? 0xffff0000u : 0x0000ffffu);
+          kinetic_cell_vec<S, M, W, 16, SX, false, SUMS>(A, V, V.klist[ci], lane & 15, sfs,
+                                                         half ? 0xffff0000u : 0x0000ffffu);
           ++mine;
         }
       } else if constexpr (W > 1) {
-        kinetic_cell_vec<S, M, W, 32, SX, WALLS>(A, V, V.klist[u], lane, sfs);
+        kinetic_cell_vec<S, M, W, 32, SX, WALLS, SUMS>(A, V, V.klist[u], lane, sfs);
         ++mine;
       } else {
         kinetic_cell<S, M, WALLS>(A, V, V.klist[u], lane, sfs);
@@ -1564,7 +1575,7 @@ static_assert(kCellWarps * sizeof(CasePrep) <= kBatchStaticSmem && sizeof(CasePr
 
 // One variant of the per-cell code (W, PAIR, SX as in stage_kernel); `off` is the
 // unit prefix of this variant, in which cases of other variants are empty.
-template <typename S, int M, int W, bool PAIR, bool SX>
+template <typename S, int M, int W, bool PAIR, bool SX, int SUMS = kSumsPlain>
 __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
     batch_stage_kernel(const CaseStage* __restrict__ cases, const int* __restrict__ off, int n, int max_nvv) {
   using R = typename Real<S>::T;
@@ -1589,14 +1600,14 @@ __global__ void __launch_bounds__(kCellThreads, ESBGK_STAGE_MIN_BLOCKS)
         // two cells, one per half-warp, each with its own f* array
         const int ci = 2 * local + half;
         if (ci < nK) {
-          kinetic_cell_vec<S, M, W, 16, SX>(A, V, V.klist[ci], lane & 15, sfs + half * V.g.nvv,
-                                            half ? 0xffff0000u : 0x0000ffffu);
+          kinetic_cell_vec<S, M, W, 16, SX, false, SUMS>(A, V, V.klist[ci], lane & 15, sfs + half * V.g.nvv,
+                                                         half ? 0xffff0000u : 0x0000ffffu);
           if ((lane & 15) == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
         }
         __syncwarp();
       } else {
         if constexpr (W > 1)
-          kinetic_cell_vec<S, M, W, 32, SX>(A, V, V.klist[local], lane, sfs);
+          kinetic_cell_vec<S, M, W, 32, SX, false, SUMS>(A, V, V.klist[local], lane, sfs);
         else
           kinetic_cell<S, M>(A, V, V.klist[local], lane, sfs);
         if (lane == 0 && A.ctr && A.f_src) atomicAdd((unsigned long long*)A.ctr, 1ull);
@@ -1686,6 +1697,17 @@ namespace esbgk {
 
 // ---------------------------------------------------------------------------
 // Host-side launchers for storage type S.
+// The stage kernels with run-time moment sums (compensated sums requested;
+// FP32 arithmetic only), compiled in translation units of their own
+// (kernels_f32_sums.cu, kernels_bf16_sums.cu) so that the main ones build in
+// parallel with them.  The first argument selects the storage type.
+using StageFnT = void (*)(StageArgs, View);
+using BatchFnT = void (*)(const CaseStage*, const int*, int, int);
+StageFnT stage_fn_runtime_sums(const float*, int m, int var);
+StageFnT stage_fn_runtime_sums(const __nv_bfloat16*, int m, int var);
+BatchFnT batch_fn_runtime_sums(const float*, int m, int var);
+BatchFnT batch_fn_runtime_sums(const __nv_bfloat16*, int m, int var);
+
 template <typename S>
 struct Launch {
   using R = typename Real<S>::T;
@@ -1730,31 +1752,39 @@ struct Launch {
     return nb;
   }
 
-  using StageFn = void (*)(StageArgs, View);
+  using StageFn = StageFnT;
   static constexpr int kW = VecW<S>::value;
   // node groups of the variants: kW, or 2 (fewer nodes per group than kW
   // when N_v is not a multiple of kW)
   static constexpr int narrow_w() { return kW > 2 ? 2 : kW; }
-  template <int M>
+  template <int M, int SUMS>
   static StageFn stage_variant(int var) {
     switch (var) {
-      case kVarWide: return stage_kernel<S, M, kW>;
-      case kVarWidePair: return stage_kernel<S, M, kW, true>;
-      case kVarWideSx: return stage_kernel<S, M, kW, false, true>;
-      case kVarWideSxPair: return stage_kernel<S, M, kW, true, true>;
-      case kVarNarrowSx: return stage_kernel<S, M, narrow_w(), false, true>;
-      case kVarNarrowSxPair: return stage_kernel<S, M, narrow_w(), true, true>;
-      default: return stage_kernel<S, M, 1>;
+      case kVarWide: return stage_kernel<S, M, kW, false, false, false, SUMS>;
+      case kVarWidePair: return stage_kernel<S, M, kW, true, false, false, SUMS>;
+      case kVarWideSx: return stage_kernel<S, M, kW, false, true, false, SUMS>;
+      case kVarWideSxPair: return stage_kernel<S, M, kW, true, true, false, SUMS>;
+      case kVarNarrowSx: return stage_kernel<S, M, narrow_w(), false, true, false, SUMS>;
+      case kVarNarrowSxPair: return stage_kernel<S, M, narrow_w(), true, true, false, SUMS>;
+      default: return stage_kernel<S, M, 1>;  // the scalar form sums plainly
     }
   }
-  static StageFn stage_fn(int m, int var = kVarScalar) {
+  template <int SUMS>
+  static StageFn stage_fn_sums(int m, int var) {
     switch (m) {
-      case kFirstRelax2: return stage_variant<kFirstRelax2>(var);
-      case kLoadedRelax1: return stage_variant<kLoadedRelax1>(var);
-      case kFinal: return stage_variant<kFinal>(var);
-      case kFirstRelax0: return stage_variant<kFirstRelax0>(var);
+      case kFirstRelax2: return stage_variant<kFirstRelax2, SUMS>(var);
+      case kLoadedRelax1: return stage_variant<kLoadedRelax1, SUMS>(var);
+      case kFinal: return stage_variant<kFinal, SUMS>(var);
+      case kFirstRelax0: return stage_variant<kFirstRelax0, SUMS>(var);
       default: return stage_kernel<S, kGeneric, 1>;
     }
+  }
+  // comp: compensated moment sums requested (only the FP32-arithmetic vector
+  // forms have them; the others always sum plainly)
+  static StageFn stage_fn(int m, int var = kVarScalar, bool comp = false) {
+    if constexpr (std::is_same<R, float>::value)
+      if (comp) return stage_fn_runtime_sums((const S*)nullptr, m, var);
+    return stage_fn_sums<kSumsPlain>(m, var);
   }
   // With solid obstacles: the wide vector form with the wall stencils (one
   // cell per warp) where the specialised modes would take a wide form, else
@@ -1762,10 +1792,10 @@ struct Launch {
   static StageFn wall_fn(int m, int var) {
     if (var == kVarWide || var == kVarWidePair) {
       switch (m) {
-        case kFirstRelax2: return stage_kernel<S, kFirstRelax2, kW, false, false, true>;
-        case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1, kW, false, false, true>;
-        case kFinal: return stage_kernel<S, kFinal, kW, false, false, true>;
-        case kFirstRelax0: return stage_kernel<S, kFirstRelax0, kW, false, false, true>;
+        case kFirstRelax2: return stage_kernel<S, kFirstRelax2, kW, false, false, true, kSumsRunTime>;
+        case kLoadedRelax1: return stage_kernel<S, kLoadedRelax1, kW, false, false, true, kSumsRunTime>;
+        case kFinal: return stage_kernel<S, kFinal, kW, false, false, true, kSumsRunTime>;
+        case kFirstRelax0: return stage_kernel<S, kFirstRelax0, kW, false, false, true, kSumsRunTime>;
         default: break;
       }
     }
@@ -1788,27 +1818,34 @@ struct Launch {
     if (g.nv % 2 == 0) return kVarNarrowSx + pair;  // N_v/2 odd when kW = 2
     return kVarScalar;
   }
-  using BatchFn = void (*)(const CaseStage*, const int*, int, int);
-  template <int M>
+  using BatchFn = BatchFnT;
+  template <int M, int SUMS>
   static BatchFn batch_variant(int var) {
     switch (var) {
-      case kVarWide: return batch_stage_kernel<S, M, kW, false, false>;
-      case kVarWidePair: return batch_stage_kernel<S, M, kW, true, false>;
-      case kVarWideSx: return batch_stage_kernel<S, M, kW, false, true>;
-      case kVarWideSxPair: return batch_stage_kernel<S, M, kW, true, true>;
-      case kVarNarrowSx: return batch_stage_kernel<S, M, narrow_w(), false, true>;
-      case kVarNarrowSxPair: return batch_stage_kernel<S, M, narrow_w(), true, true>;
-      default: return batch_stage_kernel<S, M, 1, false, false>;
+      case kVarWide: return batch_stage_kernel<S, M, kW, false, false, SUMS>;
+      case kVarWidePair: return batch_stage_kernel<S, M, kW, true, false, SUMS>;
+      case kVarWideSx: return batch_stage_kernel<S, M, kW, false, true, SUMS>;
+      case kVarWideSxPair: return batch_stage_kernel<S, M, kW, true, true, SUMS>;
+      case kVarNarrowSx: return batch_stage_kernel<S, M, narrow_w(), false, true, SUMS>;
+      case kVarNarrowSxPair: return batch_stage_kernel<S, M, narrow_w(), true, true, SUMS>;
+      default: return batch_stage_kernel<S, M, 1, false, false>;  // the scalar form sums plainly
     }
   }
-  static BatchFn batch_fn(int m, int var) {
+  template <int SUMS>
+  static BatchFn batch_fn_sums(int m, int var) {
     switch (m) {
-      case kFirstRelax2: return batch_variant<kFirstRelax2>(var);
-      case kLoadedRelax1: return batch_variant<kLoadedRelax1>(var);
-      case kFinal: return batch_variant<kFinal>(var);
-      case kFirstRelax0: return batch_variant<kFirstRelax0>(var);
+      case kFirstRelax2: return batch_variant<kFirstRelax2, SUMS>(var);
+      case kLoadedRelax1: return batch_variant<kLoadedRelax1, SUMS>(var);
+      case kFinal: return batch_variant<kFinal, SUMS>(var);
+      case kFirstRelax0: return batch_variant<kFirstRelax0, SUMS>(var);
       default: return batch_stage_kernel<S, kGeneric, 1, false, false>;
     }
+  }
+  // comp: some case of the launch asks for compensated moment sums
+  static BatchFn batch_fn(int m, int var, bool comp) {
+    if constexpr (std::is_same<R, float>::value)
+      if (comp) return batch_fn_runtime_sums((const S*)nullptr, m, var);
+    return batch_fn_sums<kSumsPlain>(m, var);
   }
   // Tiled stage kernel (every cell kinetic, regime frozen): the specialised
   // modes, an even N_v, the per-pair arrays aligned, no fused L1 deviation,
@@ -1865,9 +1902,9 @@ struct Launch {
           return e;
       }
     for (int m = 0; m < kNumModes; ++m)
-      for (int v = 0; v < kNumVariants; ++v)
-        if ((e = cudaFuncSetAttribute(stage_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
-            cudaSuccess)
+      for (int v = 0; v < 2 * kNumVariants; ++v)
+        if ((e = cudaFuncSetAttribute(stage_fn(m, v % kNumVariants, v >= kNumVariants),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
       return e;
@@ -1878,9 +1915,9 @@ struct Launch {
     // batched kernels: set here so that their launches can be graph-captured
     const int mb = mx - kBatchStaticSmem;
     for (int m = 0; m < kNumModes; ++m)
-      for (int v = 0; v < kNumVariants; ++v)
-        if ((e = cudaFuncSetAttribute(batch_fn(m, v), cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) !=
-            cudaSuccess)
+      for (int v = 0; v < 2 * kNumVariants; ++v)
+        if ((e = cudaFuncSetAttribute(batch_fn(m, v % kNumVariants, v >= kNumVariants),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
           return e;
     if ((e = cudaFuncSetAttribute(batch_l1_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb)) != cudaSuccess)
       return e;
@@ -1903,7 +1940,7 @@ struct Launch {
     const int threads = 32 * warps_for(V.g, arrays);
     const size_t smem = proj ? smem_for(V.g, arrays) : 0;
     // solid obstacles: the forms with the wall stencils
-    const StageFn fn = V.wsrc ? wall_fn(mode, var) : stage_fn(mode, var);
+    const StageFn fn = V.wsrc ? wall_fn(mode, var) : stage_fn(mode, var, V.m.comp_moments != 0);
     fn<<<rescale(V.g, grid, (const void*)fn, threads, smem), threads, smem, s>>>(A, V);
   }
   static void prep(const PrepArgs& P, const View& V, int grid, cudaStream_t s) {
@@ -1920,12 +1957,12 @@ struct Launch {
     relax_cells_kernel<S><<<grid, threads, smem_for(g, 1), s>>>((const S*)fs, h, n, g, beta, (S*)fo, (S*)go);
   }
   static size_t batch_smem(int max_nvv, int threads) { return (size_t)(threads / 32) * max_nvv * sizeof(R); }
-  static int batch_stage_occupancy(int mode, int var, int max_nvv, int threads) {
-    return occ((const void*)batch_fn(mode, var), threads, batch_smem(max_nvv, threads));
+  static int batch_stage_occupancy(int mode, int var, bool comp, int max_nvv, int threads) {
+    return occ((const void*)batch_fn(mode, var, comp), threads, batch_smem(max_nvv, threads));
   }
-  static void batch_stage(const CaseStage* cases, const int* off, int n, int mode, int var, int max_nvv, int threads,
-                          int grid, cudaStream_t s) {
-    const BatchFn fn = batch_fn(mode, var);
+  static void batch_stage(const CaseStage* cases, const int* off, int n, int mode, int var, bool comp, int max_nvv,
+                          int threads, int grid, cudaStream_t s) {
+    const BatchFn fn = batch_fn(mode, var, comp);
     fn<<<grid, threads, batch_smem(max_nvv, threads), s>>>(cases, off, n, max_nvv);
   }
   static void batch_prep(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t s) {

@@ -208,12 +208,13 @@ struct Launchers {
   void (*relax_cells)(const void* fs, const double* h, int n, const Geo&, double beta, void* fo, void* go,
                       int grid, cudaStream_t);
   void (*moments)(const void* f, double* U, const View&, int grid, cudaStream_t);
-  // batched form; threads per CTA (multiple of 32, <= 128) and grid chosen by the caller
-  void (*batch_stage)(const CaseStage* cases, const int* off, int n, int mode, int var, int max_nvv, int threads,
-                      int grid, cudaStream_t);
+  // batched form; threads per CTA (multiple of 32, <= 128) and grid chosen by the caller;
+  // comp: some case asks for compensated moment sums
+  void (*batch_stage)(const CaseStage* cases, const int* off, int n, int mode, int var, bool comp, int max_nvv,
+                      int threads, int grid, cudaStream_t);
   void (*batch_prep)(const CasePrep* cases, const int* off, int n, int grid, cudaStream_t);
   void (*batch_l1)(const CaseRegime* cases, const int* off, int n, int max_nvv, int grid, cudaStream_t);
-  int (*batch_stage_occupancy)(int mode, int var, int max_nvv, int threads);
+  int (*batch_stage_occupancy)(int mode, int var, bool comp, int max_nvv, int threads);
   int (*variant)(const StageArgs& A, const Geo& g);
   int wide_nodes;  // nodes per group of the kVarWide variants
   // tiled stage kernel for problems whose every cell is kinetic (regime frozen)

@@ -97,6 +97,30 @@ def test_batch_equals_single_cases(prec, tableau, graph):
         assert cb["steps"] == 5
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_mixed_moment_sums_equal_single_cases(prec):
+    """Cases with compensated and plain moment sums in one batch: the batched
+    launches take the kernels whose sums follow each case's parameter, and
+    every case matches the same problem advanced alone (compensated cases by
+    the single-problem kernels with run-time sums, plain ones by the kernels
+    with the compensation compiled out)."""
+    import torch
+    cases = _mixed_cases()
+    for k, c in enumerate(cases):
+        c["params"] = dict(c["params"], moment_sums="compensated" if k % 2 == 0 else "plain")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = _batch(cases, prec, stream=stream)
+        singles = [_single(c, prec) for c in cases]
+        dts = np.array([c["dt"] for c in cases])
+        for _ in range(5):
+            for s, c in zip(singles, cases):
+                s.step(c["dt"], "ars233")
+            b.step(dts, "ars233", graph=True)
+        b.sync()
+        _compare(b, singles, prec)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_batch_with_largest_velocity_grid(prec):
     """A case at the largest accepted N_v = 64 (4096 nodes: the widest shared
