@@ -990,6 +990,12 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
   const R epsw = pick<R>(V.m.eps_w, V.m.feps_w), cL = pick<R>(A.star_cL, A.f_star_cL);
   constexpr bool relax = MT::relax;
   constexpr int nacc = MT::nacc;
+  // f* and every accumulator start from f_src (the first relaxed stage): the
+  // partial accumulators f_src + aL L are not written in pass 1; pass 3
+  // rebuilds them from f* = f_src + cL L as f_src + (aL / cL)(f* - f_src)
+  // (the same value up to the rounding of f*; cL != 0 by the host's choice
+  // of this mode)
+  constexpr bool kRebuild = relax && MT::base_src && MT::acc_src && nacc > 0;
   S* fout = (S*)A.f_out;
   const S* ain[nacc > 0 ? nacc : 1];
   S* aout[nacc > 0 ? nacc : 1];
@@ -1111,7 +1117,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
         fs[j] = F.x;
         fs[j + 1] = F.y;
 #pragma unroll
-        for (int t = 0; t < nacc; ++t) {
+        for (int t = 0; t < (kRebuild ? 0 : nacc); ++t) {
           const float2 Pa = __ffma2_rn(splat2(aL[t]), Lf, make_float2(ai[t][j], ai[t][j + 1]));
           pa[t][j] = Pa.x;
           pa[t][j + 1] = Pa.y;
@@ -1134,7 +1140,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
         const R Lf = Lx + Ly;
         fs[j] = bs[j] + cL * Lf;
 #pragma unroll
-        for (int t = 0; t < nacc; ++t) pa[t][j] = ai[t][j] + aL[t] * Lf;
+        for (int t = 0; t < (kRebuild ? 0 : nacc); ++t) pa[t][j] = ai[t][j] + aL[t] * Lf;
         const R cx = vx - u0x, cy = vy - u0y;
         m[0] += fs[j];
         m[1] += cx * fs[j];
@@ -1152,7 +1158,7 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
       if (A.l1_out) SM::st(sfs + k, fs);
     }
 #pragma unroll
-    for (int t = 0; t < nacc; ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
+    for (int t = 0; t < (kRebuild ? 0 : nacc); ++t) IO::st_sr(aout[t] + o0 + k, pa[t], kb + 1 + t);
     if constexpr (kPacked) {
       if (kComp && ++blk == kFlush) {
         blk = 0;
@@ -1209,14 +1215,40 @@ ESBGK_DEV void kinetic_cell_vec(const StageArgs& A, const View& V, int c, int la
 
   // pass 3: G_hat, implicit relaxation, Q, accumulators, outputs
   const R inv1h = R(1) / (R(1) + h);
+  R rL[nacc > 0 ? nacc : 1];  // aL / cL of the rebuilt accumulators
+#pragma unroll
+  for (int t = 0; t < nacc; ++t) rL[t] = kRebuild ? aL[t] / cL : R(0);
   NodeIter<R> jt(lane * W, g.nv, v0, dv, L * W);
 #pragma unroll 1
   for (; jt.k < g.nvv; jt.next()) {
     const unsigned k = jt.k;
     R fs[W], pa[nacc > 0 ? nacc : 1][W], fn[W];
     SM::ld(sfs + k, fs);
+    if constexpr (kRebuild) {
+      R q[W];  // f_src, read in pass 1 and still in L2
+      IO::ld(fsrc + o0 + k, q);
+      if constexpr (kPacked) {
 #pragma unroll
-    for (int t = 0; t < nacc; ++t) IO::ldc(aout[t] + o0 + k, pa[t]);
+        for (int j = 0; j < W; j += 2) {
+          const float2 Q0 = make_float2(q[j], q[j + 1]);
+          const float2 D = __ffma2_rn(Q0, splat2(-1.0f), make_float2(fs[j], fs[j + 1]));
+#pragma unroll
+          for (int t = 0; t < nacc; ++t) {
+            const float2 Pa = __ffma2_rn(splat2(rL[t]), D, Q0);
+            pa[t][j] = Pa.x;
+            pa[t][j + 1] = Pa.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < nacc; ++t)
+#pragma unroll
+          for (int j = 0; j < W; ++j) pa[t][j] = q[j] + rL[t] * (fs[j] - q[j]);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < nacc; ++t) IO::ldc(aout[t] + o0 + k, pa[t]);
+    }
     const R cy = jt.vy() - P.uy, cx0 = jt.vx() - P.ux;
     if constexpr (kPacked) {
       // pairs of nodes on the paired FP32 instructions

@@ -128,7 +128,9 @@ inline int stage_mode(const StageArgs& A) {
   const bool relax = A.h_coef > 0.0;
   if (!A.f_src) return kGeneric;
   const bool bsrc = A.star_base == A.f_src;
-  if (bsrc && relax && A.nacc == 2 && A.acc_in[0] == A.f_src && A.acc_in[1] == A.f_src) return kFirstRelax2;
+  // (kFirstRelax2 rebuilds its accumulators from f* and f_src: it needs a transport coefficient)
+  if (bsrc && relax && A.nacc == 2 && A.acc_in[0] == A.f_src && A.acc_in[1] == A.f_src && A.star_cL != 0.0)
+    return kFirstRelax2;
   if (!bsrc && relax && A.nacc == 1 && A.acc_in[0] != A.f_src) return kLoadedRelax1;
   if (!bsrc && !relax && !A.need_q && A.nacc == 0) return kFinal;
   if (bsrc && relax && A.nacc == 0) return kFirstRelax0;
