@@ -51,3 +51,30 @@ def test_pair_is_second_order_on_gpu(scheme):
     orders = np.log2(np.array(err[:-1]) / np.array(err[1:]))
     print("\n%s orders %s" % (scheme, orders))
     assert abs(orders[-1] - 2.0) <= 0.3, orders
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_first_relaxed_stage_without_transport_coefficient(prec):
+    """ARS(2,3,3) with the explicit coefficient of its second stage set to
+    zero (At[1][0] = 0): f* of the first relaxed stage is f^n itself, so the
+    specialised first-stage kernel (which rebuilds its partial accumulators
+    from f* - f^n and the ratio of the coefficients) cannot serve it and the
+    generic stage kernel takes the stage.  The result matches the FP64 oracle
+    with the same tableau."""
+    import oracle as O
+    from test_gpu_parity import field_errors, gpu_solver, oracle_pair
+    At = O.ARS233.At.copy()
+    At[1, 0] = 0.0
+    tab_o = O.Tableau(At=At, bt=O.ARS233.bt, A=O.ARS233.A, b=O.ARS233.b)
+    tab_g = {"At": At, "bt": O.ARS233.bt, "A": O.ARS233.A, "b": O.ARS233.b}
+    wl = W.order_test(n=17, nv=12, eps=1e-2, seed=2)
+    wl["dt"] = 0.2 / 8
+    g = gpu_solver(wl, prec)
+    P, st = oracle_pair(wl)
+    worst = np.zeros(4)
+    for _ in range(3):
+        g.advance(wl["dt"], tab_g)
+        st = O.advance(P, st, wl["dt"], tab_o)
+        worst = np.maximum(worst, field_errors(g.cons(), st.U))
+    assert np.all(np.isfinite(g.cons())), "non-finite state"
+    assert worst.max() <= TOL[prec], worst
