@@ -67,3 +67,16 @@ def test_committed_traffic_belongs_to_the_committed_kernel_sources():
             assert tr is not None and 4.0 < tr < 40.0
         else:
             assert tr is None
+
+
+def test_profile_summaries_name_the_traffic_record_sources():
+    """The ncu summaries the stored traffic comes from name the same stage
+    kernel sources (source hash) as the traffic record."""
+    d = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
+    summaries = {"blob/fp32": "stage_kernel_blob256x48_fp32.md", "riemann/fp32": "stage_kernel_riemann128x32_fp32.md"}
+    for key, e in d["entries"].items():
+        text = open(os.path.join(ROOT, "profiles", summaries[key])).read()
+        assert e["source_hash"] in text, key
+        # the capture command of the record is the one the summary gives
+        log = e["command"].split("--log-file ")[1].split()[0]
+        assert log in text, (key, log)
